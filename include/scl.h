@@ -1,0 +1,222 @@
+/*
+ * scl.h -- C ABI of libscl: GB300 (sm_103a) replay of the memory-profiling
+ * hot path of Scalene (Berger, Stern, Altmayer Pizzorno, arXiv 2212.07597).
+ *
+ * A trace is the stream of allocation, free and memcpy events one profiled
+ * process would have sent through Scalene's allocator shim (Section 3.1).  The
+ * library replays traces through
+ *   - the threshold sampler (Section 3.2): counters A and F of bytes allocated
+ *     and freed; when |A - F| >= T a sample is taken and both are reset;
+ *   - sample records and per-line attribution (Section 3.3): each sample holds
+ *     the window's allocation and free totals, their Python share, the
+ *     footprint at the crossing and the line current when it fired;
+ *   - the leak detector (Section 3.4): a growth sample that sets a new
+ *     footprint high-water mark tracks the sampled block; frees compare their
+ *     pointer with it; at the next mark the site's (frees, mallocs) pair is
+ *     updated; likelihood = 1 - (frees + 1) / (mallocs - frees + 2);
+ *   - the copy-volume sampler (Section 3.5): one sample per T_c bytes copied,
+ *     T_c a multiple of T.
+ *
+ * Every trace has resident state on the device (counter, open-window totals,
+ * footprint, high-water mark, tracked block, per-line tables, copy counter), so
+ * a trace may arrive in any number of segments: replaying the pieces in order
+ * gives exactly the result of replaying the whole.
+ *
+ * Conventions
+ *   - Every int-returning call returns SCL_OK (0) or a negative SCL_E* code;
+ *     scl_last_error() then holds a one-line message.
+ *   - "device pointer": memory the CUDA device can read (cudaMalloc, torch).
+ *     Event arrays stay owned by the caller and must stay valid until the
+ *     stream work of the call has finished.  Each array must be 16-byte
+ *     aligned when its segment holds >= 1024 events (SCL_EINVAL otherwise).
+ *   - Replay calls are asynchronous on the caller's stream; query calls
+ *     synchronise that stream first and report any error a kernel recorded.
+ *   - Query outputs are caller-owned host arrays; when `cap` is too small the
+ *     call stores the needed count in *n_out and returns SCL_ERANGE.
+ *   - All arithmetic is exact 64-bit integer arithmetic; a sum that would
+ *     overflow int64 is reported as SCL_EOVERFLOW.
+ *   - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef SCL_H
+#define SCL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCL_OK 0
+#define SCL_EINVAL (-1)     /* bad argument, descriptor, alignment or trace id */
+#define SCL_ENOMEM (-2)     /* device or pinned host allocation failed */
+#define SCL_ECUDA (-3)      /* a CUDA runtime call failed */
+#define SCL_ETIMEOUT (-4)   /* a bounded device wait gave up (see spin_limit) */
+#define SCL_EOVERFLOW (-5)  /* an int64 sum would overflow, or a record buffer overflowed */
+#define SCL_ERANGE (-6)     /* a line id >= n_lines was seen, or an output cap is too small */
+
+typedef struct scl_ctx scl_ctx;
+
+/* One trace segment of allocation events, structure of arrays (Section 3.1-3.2).
+ * delta[i] > 0 is a malloc of delta[i] bytes, delta[i] < 0 a free of -delta[i]
+ * bytes, 0 is allowed and never samples.  addr[i] is the block address (only
+ * compared for equality, Section 3.4).  line[i] < n_lines is the source line the
+ * shim attributes the call to, is_python[i] = 1 for Python's allocator and 0 for
+ * native code (Section 3.1).  All four are device pointers of length n. */
+typedef struct {
+    const int64_t *delta;
+    const uint64_t *addr;
+    const uint32_t *line;
+    const uint8_t *is_python;
+    uint64_t n;
+} scl_events;
+
+/* memcpy events of the same segment (Section 3.5): bytes copied, line, flag.
+ * Device pointers of length n; n may be 0. */
+typedef struct {
+    const uint64_t *size;
+    const uint32_t *line;
+    const uint8_t *is_python;
+    uint64_t n;
+} scl_copies;
+
+typedef struct {
+    int64_t threshold;            /* T >= 1 (Section 3.2: a prime just above 10 MB, 10485767 by default) */
+    uint32_t copy_multiple;       /* T_c = copy_multiple * T (Section 3.5), >= 1, default 2 */
+    uint32_t n_lines;             /* L: line ids are < L, default 256 */
+    uint64_t copy_phase;          /* copy counter at trace start, in [0, T_c), default 0 */
+    int64_t initial_footprint;    /* F0: footprint and first high-water mark at trace start */
+    uint32_t max_traces;          /* resident trace slots, ids 0 .. max_traces-1, default 1 */
+    uint32_t leak_rule;           /* 0: likelihood as printed in Section 3.4 (default);
+                                     1: Laplace's rule, 1 - (frees+1)/(mallocs+2) */
+    uint64_t spin_limit;          /* iterations before a device wait reports SCL_ETIMEOUT (0: 1<<26) */
+    uint64_t sample_log_capacity; /* samples kept per trace for scl_samples (0: keep none) */
+    uint32_t sample_budget_shift; /* record space per work unit = (events >> shift) + 64; 0 never
+                                     overflows (needed when T is tiny), default 3 */
+    uint32_t unit_events;         /* events per walker work unit (multiple of 1024; 0: tuned default) */
+} scl_config;
+
+/* Fill *cfg with the defaults listed above. */
+int scl_config_default(scl_config *cfg);
+
+/* One segment of trace `trace_id` (< max_traces). */
+typedef struct {
+    uint32_t trace_id;
+    uint32_t reserved;
+    scl_events ev;
+    scl_copies cp;
+} scl_segment;
+
+/* One sample-file entry (Section 3.3): 56 bytes. */
+typedef struct {
+    uint64_t idx;         /* event index within the trace (counted over all its segments) */
+    int64_t A, F;         /* bytes allocated / freed in the window that closed here */
+    int64_t A_py, F_py;   /* the Python part of A and F */
+    int64_t footprint;    /* F0 + all deltas up to and including idx */
+    uint32_t line;        /* line of the event that crossed the threshold */
+    int8_t kind;          /* +1 growth (A - F >= T), -1 shrink (A - F <= -T) */
+    uint8_t is_python;    /* flag of that event */
+    uint8_t is_hwm;       /* 1: this sample set a new high-water mark and started tracking its block */
+    uint8_t reserved;
+} scl_sample;
+
+/* Per-line totals over all samples of a trace (Sections 3.3 and 3.5), row = line id. */
+typedef struct {
+    uint64_t n_growth, n_shrink;        /* samples attributed to the line */
+    int64_t A, F, A_py, F_py;           /* sums of the window totals of those samples */
+    int64_t net;                        /* sum of A - F over those samples */
+    uint64_t copy_samples[2];           /* copy-volume samples, index = is_python */
+    uint64_t copy_bytes[2];             /* copy_samples * T_c */
+} scl_line_stat;
+
+/* Per-line leak score (Section 3.4) as an unreduced fraction num/den. */
+typedef struct {
+    uint32_t line;
+    uint32_t reserved;
+    uint64_t mallocs;   /* tracked blocks sampled at this line (incremented when tracking starts) */
+    uint64_t frees;     /* of those whose trial has closed, the ones freed inside their window */
+    int64_t num, den;   /* likelihood = num / den under the configured leak_rule; den >= 2 */
+} scl_leak_score;
+
+/* Resident sampler state of one trace. */
+typedef struct {
+    uint64_t n_events, n_copies, n_samples;
+    int64_t c;                          /* A - F of the open window */
+    int64_t A, F, A_py, F_py;           /* open-window totals */
+    int64_t footprint, hwm;
+    uint64_t tracked_addr, tracked_idx; /* block tracked since the last high-water crossing */
+    uint32_t tracked_line;
+    uint8_t tracked_valid, tracked_reclaimed, reserved[2];
+    uint64_t copy_counter;              /* bytes copied since the last copy sample, < T_c */
+} scl_trace_state;
+
+/* Create a context: validates *cfg, allocates the resident state of max_traces
+ * traces on the current CUDA device.  The library owns *out until scl_replay_free. */
+int scl_replay_init(scl_ctx **out, const scl_config *cfg);
+void scl_replay_free(scl_ctx *ctx);
+const char *scl_last_error(const scl_ctx *ctx);
+
+/* Append each segment to its trace's resident state (Sections 3.2-3.5).
+ * segs: host array of nsegs descriptors holding device pointers.  Segments of
+ * the same trace are applied in array order.  Asynchronous on cuda_stream
+ * (a cudaStream_t; NULL = legacy default stream).  Returns SCL_EINVAL on a bad
+ * descriptor; errors found by kernels (line id >= L -> SCL_ERANGE, int64
+ * overflow / record space -> SCL_EOVERFLOW, wait limit -> SCL_ETIMEOUT) are
+ * reported by the next query or scl_sync, and the affected results are invalid. */
+int scl_replay_batch(scl_ctx *ctx, const scl_segment *segs, uint32_t nsegs, void *cuda_stream);
+
+/* Same as scl_replay_batch but the event arrays are in HOST memory: the library
+ * copies them to its own device staging buffers on cuda_stream first (pinned
+ * host memory makes those copies asynchronous). */
+int scl_replay_batch_host(scl_ctx *ctx, const scl_segment *segs, uint32_t nsegs, void *cuda_stream);
+
+/* Wait for the work of the last replay call; return the first recorded device error. */
+int scl_sync(scl_ctx *ctx);
+
+/* Queries (synchronise first).  scl_samples returns the trace's retained samples
+ * in order; *n_out = all samples ever taken; if more were taken than
+ * sample_log_capacity, the first sample_log_capacity are returned and the call
+ * returns SCL_EOVERFLOW.  scl_line_stats / scl_leak_scores return n_lines rows. */
+int scl_samples(scl_ctx *ctx, uint32_t trace, scl_sample *out, uint64_t cap, uint64_t *n_out);
+int scl_line_stats(scl_ctx *ctx, uint32_t trace, scl_line_stat *out, uint32_t cap, uint32_t *n_out);
+int scl_leak_scores(scl_ctx *ctx, uint32_t trace, scl_leak_score *out, uint32_t cap, uint32_t *n_out);
+int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_state *out);
+
+/* Checkpoint / resume of one trace's resident state (counter, window totals,
+ * footprint, mark, tracked block, per-line tables, copy counter; not the sample
+ * log).  Export with buf == NULL stores the needed size in *n_out.  Import
+ * replaces the trace's state; a state exported from a context with other
+ * threshold, n_lines, copy_multiple or leak_rule is rejected (SCL_EINVAL). */
+int scl_state_export(scl_ctx *ctx, uint32_t trace, void *buf, uint64_t cap, uint64_t *n_out);
+int scl_state_import(scl_ctx *ctx, uint32_t trace, const void *buf, uint64_t n);
+
+/* Return a trace to its initial state (F0, counters 0, empty tables and log). */
+int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
+
+/* Tuning of the walker: events per work unit, walker warps per block.  scl_autotune
+ * times scl_replay_batch on the given segments for each candidate and keeps the
+ * fastest; it replays into scratch trace slots and leaves the traces' state as it
+ * was.  The chosen values are returned by scl_tuning_get. */
+typedef struct {
+    uint32_t unit_events;    /* events per work unit (multiple of 1024) */
+    uint32_t warps_per_block;/* walker warps per thread block (1..16) */
+    uint32_t ext_events;     /* cap on the lookahead a unit walks into its successor (0 = whole unit) */
+    uint32_t reserved;
+} scl_tuning;
+int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
+int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);
+int scl_autotune(scl_ctx *ctx, const scl_segment *segs, uint32_t nsegs, void *cuda_stream,
+                 scl_tuning *best_out, double *best_ms_out);
+
+/* Per-kernel device time of replay calls, for measurement.  When enabled, each
+ * replay call records CUDA events around its kernels on its stream; scl_kernel_times
+ * synchronises and returns, for each kernel name, the summed milliseconds and the
+ * number of launches since the last reset.  names[i] point to static strings. */
+int scl_profile_enable(scl_ctx *ctx, int on);
+int scl_kernel_times(scl_ctx *ctx, const char **names, double *ms, uint64_t *launches,
+                     uint32_t cap, uint32_t *n_out);
+int scl_profile_reset(scl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCL_H */
