@@ -33,8 +33,12 @@
  *     synchronise that stream first and report any error a kernel recorded.
  *   - Query outputs are caller-owned host arrays; when `cap` is too small the
  *     call stores the needed count in *n_out and returns SCL_ERANGE.
- *   - All arithmetic is exact 64-bit integer arithmetic; a sum that would
- *     overflow int64 is reported as SCL_EOVERFLOW.
+ *   - All arithmetic is exact 64-bit integer arithmetic.  The caller keeps the
+ *     running sums of a trace's deltas inside int64 (the library does not
+ *     check every event); a copy byte count that overflows uint64 and record
+ *     space that runs out are reported as SCL_EOVERFLOW.
+ *   - Line ids are read, and checked, where the method uses them: at the
+ *     events that trigger a sample and at memcpy events.
  *   - A context is not thread-safe: one host thread drives it at a time.
  */
 #ifndef SCL_H
@@ -91,7 +95,7 @@ typedef struct {
     uint64_t spin_limit;          /* iterations before a device wait reports SCL_ETIMEOUT (0: 1<<26) */
     uint64_t sample_log_capacity; /* samples kept per trace for scl_samples (0: keep none) */
     uint32_t sample_budget_shift; /* record space per work unit = (events >> shift) + 64; 0 never
-                                     overflows (needed when T is tiny), default 3 */
+                                     overflows (needed when T is tiny), default 4 */
     uint32_t unit_events;         /* events per walker work unit (multiple of 1024; 0: tuned default) */
 } scl_config;
 
@@ -147,7 +151,7 @@ typedef struct {
     uint32_t tracked_line;
     uint8_t tracked_valid, tracked_reclaimed, reserved[2];
     uint64_t copy_counter;              /* bytes copied since the last copy sample, < T_c */
-} scl_trace_state;
+} scl_trace_info;
 
 /* Create a context: validates *cfg, allocates the resident state of max_traces
  * traces on the current CUDA device.  The library owns *out until scl_replay_free. */
@@ -179,7 +183,7 @@ int scl_sync(scl_ctx *ctx);
 int scl_samples(scl_ctx *ctx, uint32_t trace, scl_sample *out, uint64_t cap, uint64_t *n_out);
 int scl_line_stats(scl_ctx *ctx, uint32_t trace, scl_line_stat *out, uint32_t cap, uint32_t *n_out);
 int scl_leak_scores(scl_ctx *ctx, uint32_t trace, scl_leak_score *out, uint32_t cap, uint32_t *n_out);
-int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_state *out);
+int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_info *out);
 
 /* Checkpoint / resume of one trace's resident state (counter, window totals,
  * footprint, mark, tracked block, per-line tables, copy counter; not the sample
@@ -215,6 +219,12 @@ int scl_profile_enable(scl_ctx *ctx, int on);
 int scl_kernel_times(scl_ctx *ctx, const char **names, double *ms, uint64_t *launches,
                      uint32_t cap, uint32_t *n_out);
 int scl_profile_reset(scl_ctx *ctx);
+
+/* Failure-detection self test (no counterpart in the paper): launches one warp that
+ * waits, with the same bounded wait the walker uses, on a barrier nothing arrives at.
+ * The wait gives up after `limit` polls and the call returns SCL_ETIMEOUT; the
+ * context's error word is cleared afterwards, so the context stays usable. */
+int scl_selftest_wait(scl_ctx *ctx, uint64_t limit, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,785 @@
+// scl_host.cu -- the C ABI of libscl (include/scl.h): contexts, batch planning,
+// launch sequence, queries, checkpoint / resume, profiling.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/scl.h"
+#include "scl_internal.cuh"
+#include "scl_launch.h"
+
+using namespace scl;
+
+namespace {
+
+constexpr uint32_t STATE_MAGIC = 0x53434c31u;   // "SCL1"
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct ProfEntry {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct scl_ctx {
+    scl_config cfg{};
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    cudaStream_t last_stream = nullptr;
+    // resident state
+    DevTrace *traces = nullptr;
+    LineRow *lines = nullptr;
+    Sample *log = nullptr;
+    ErrWord *errw = nullptr;
+    void *scores = nullptr;
+    unsigned *queue = nullptr;
+    std::vector<uint64_t> h_events;   // host mirror of each trace's event count
+    // batch scratch
+    DevBuf plan, ures, pub, recs, cross, recl, bits, btres, ctsum, stage;
+    void *h_plan = nullptr;
+    size_t h_plan_cap = 0;
+    cudaEvent_t plan_done = nullptr;
+    bool plan_pending = false;
+    // tuning
+    scl_tuning tune{};
+    // profiling
+    bool prof = false;
+    std::vector<ProfEntry> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<const char *, std::pair<double, uint64_t>>> prof_acc;
+};
+
+namespace {
+
+int fail(scl_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(scl_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? SCL_ENOMEM : SCL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+int ensure(scl_ctx *c, DevBuf &b, size_t bytes, cudaStream_t s, const char *what) {
+    if (bytes <= b.cap) return SCL_OK;
+    size_t nb = std::max(bytes, b.cap + b.cap / 2);
+    nb = (nb + 4095) & ~size_t(4095);
+    if (b.p) {
+        CK(cudaStreamSynchronize(s), "sync before regrow");
+        CK(cudaFree(b.p), "cudaFree");
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    CK(cudaMalloc(&b.p, nb), what);
+    b.cap = nb;
+    return SCL_OK;
+}
+
+cudaEvent_t pool_event(scl_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Prof {
+    scl_ctx *c;
+    cudaStream_t s;
+    const char *name;
+    cudaEvent_t a = nullptr;
+    Prof(scl_ctx *c_, cudaStream_t s_, const char *n) : c(c_), s(s_), name(n) {
+        if (c->prof) { a = pool_event(c); cudaEventRecord(a, s); }
+    }
+    ~Prof() {
+        if (c->prof) {
+            cudaEvent_t b = pool_event(c);
+            cudaEventRecord(b, s);
+            c->prof_pending.push_back({name, a, b});
+        }
+    }
+};
+
+void prof_collect(scl_ctx *c) {
+    for (auto &p : c->prof_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        bool found = false;
+        for (auto &q : c->prof_acc)
+            if (strcmp(q.first, p.name) == 0) { q.second.first += ms; q.second.second += 1; found = true; break; }
+        if (!found) c->prof_acc.push_back({p.name, {ms, 1}});
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->prof_pending.clear();
+}
+
+int check_device_error(scl_ctx *c) {
+    ErrWord w{};
+    CK(cudaMemcpy(&w, c->errw, sizeof w, cudaMemcpyDeviceToHost), "read error word");
+    if (w.code == 0) return SCL_OK;
+    switch (w.code) {
+    case E_RANGE:
+        return fail(c, SCL_ERANGE, "line id %u >= n_lines (%u) at event %llu", w.detail0, c->cfg.n_lines,
+                    (unsigned long long)w.detail1);
+    case E_TIMEOUT:
+        return fail(c, SCL_ETIMEOUT, "a device wait exceeded spin_limit (site %u, %llu)", w.detail0,
+                    (unsigned long long)w.detail1);
+    case E_OVERFLOW:
+        return fail(c, SCL_EOVERFLOW,
+                    "record space overflow or uint64 copy-count overflow (site %u, unit/tile %llu); "
+                    "lower sample_budget_shift", w.detail0, (unsigned long long)w.detail1);
+    default:
+        return fail(c, w.code, "device error %d (%u, %llu)", w.code, w.detail0, (unsigned long long)w.detail1);
+    }
+}
+
+int sync_and_check(scl_ctx *c) {
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(c->last_stream), "stream sync");
+    return check_device_error(c);
+}
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+int scl_config_default(scl_config *cfg) {
+    if (!cfg) return SCL_EINVAL;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->threshold = 10485767;
+    cfg->copy_multiple = 2;
+    cfg->n_lines = 256;
+    cfg->copy_phase = 0;
+    cfg->initial_footprint = 0;
+    cfg->max_traces = 1;
+    cfg->leak_rule = 0;
+    cfg->spin_limit = 0;
+    cfg->sample_log_capacity = 0;
+    cfg->sample_budget_shift = 4;
+    cfg->unit_events = 0;
+    return SCL_OK;
+}
+
+const char *scl_last_error(const scl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void scl_replay_free(scl_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (DevBuf *b : {&c->plan, &c->ures, &c->pub, &c->recs, &c->cross, &c->recl, &c->bits, &c->btres, &c->ctsum,
+                      &c->stage})
+        if (b->p) cudaFree(b->p);
+    cudaFree(c->traces);
+    cudaFree(c->lines);
+    if (c->log) cudaFree(c->log);
+    cudaFree(c->errw);
+    cudaFree(c->scores);
+    cudaFree(c->queue);
+    if (c->h_plan) cudaFreeHost(c->h_plan);
+    if (c->plan_done) cudaEventDestroy(c->plan_done);
+    delete c;
+}
+
+int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
+    if (!out || !cfg_in) return SCL_EINVAL;
+    *out = nullptr;
+    scl_ctx *c = new scl_ctx();
+    c->cfg = *cfg_in;
+    scl_config &cfg = c->cfg;
+    if (cfg.threshold < 1 || cfg.copy_multiple < 1 || cfg.n_lines == 0 || cfg.max_traces == 0 ||
+        cfg.leak_rule > 1 || cfg.sample_budget_shift > 20 || (cfg.unit_events % UNIT_ALIGN) != 0) {
+        int r = fail(c, SCL_EINVAL, "invalid config (threshold >= 1, copy_multiple >= 1, n_lines >= 1, "
+                                    "max_traces >= 1, leak_rule in {0,1}, unit_events multiple of 1024)");
+        scl_replay_free(c);
+        return r;
+    }
+    const unsigned __int128 tc = (unsigned __int128)cfg.copy_multiple * (unsigned __int128)cfg.threshold;
+    if (tc > (unsigned __int128)INT64_MAX || cfg.copy_phase >= (uint64_t)tc) {
+        int r = fail(c, SCL_EINVAL, "copy threshold out of range or copy_phase >= T_c");
+        scl_replay_free(c);
+        return r;
+    }
+    if (cfg.spin_limit == 0) cfg.spin_limit = 1ull << 26;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const size_t L = cfg.n_lines, NTr = cfg.max_traces;
+    if (e == cudaSuccess) e = cudaMalloc(&c->traces, sizeof(DevTrace) * NTr);
+    if (e == cudaSuccess) e = cudaMalloc(&c->lines, sizeof(LineRow) * L * NTr);
+    if (e == cudaSuccess && cfg.sample_log_capacity)
+        e = cudaMalloc(&c->log, sizeof(Sample) * cfg.sample_log_capacity * NTr);
+    if (e == cudaSuccess) e = cudaMalloc(&c->errw, sizeof(ErrWord));
+    if (e == cudaSuccess) e = cudaMalloc(&c->scores, sizeof(scl_leak_score) * L);
+    if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(c, e, "context allocation");
+        fprintf(stderr, "scl_replay_init: %s\n", c->err.c_str());
+        scl_replay_free(c);
+        return r;
+    }
+    for (uint32_t t = 0; t < cfg.max_traces; ++t) {
+        e = launch_reset(c->traces, c->lines, t, cfg.n_lines, cfg.initial_footprint, cfg.copy_phase, nullptr);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        int r = cuda_fail(c, e, "context initialisation");
+        scl_replay_free(c);
+        return r;
+    }
+    c->h_events.assign(NTr, 0);
+    c->tune.unit_events = cfg.unit_events ? cfg.unit_events : 131072;
+    c->tune.warps_per_block = 8;
+    c->tune.ext_events = 0;
+    *out = c;
+    return SCL_OK;
+}
+
+int scl_tuning_get(const scl_ctx *c, scl_tuning *out) {
+    if (!c || !out) return SCL_EINVAL;
+    *out = c->tune;
+    return SCL_OK;
+}
+
+int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
+    if (!c || !t) return SCL_EINVAL;
+    if (t->unit_events == 0 || t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 12 ||
+        (t->ext_events % TILE))
+        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024, warps_per_block 1..12, "
+                                   "ext_events multiple of %d", TILE);
+    c->tune = *t;
+    return SCL_OK;
+}
+
+int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stream) {
+    if (!c) return SCL_EINVAL;
+    if (nsegs && !segs) return fail(c, SCL_EINVAL, "segs is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const scl_config &cfg = c->cfg;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+
+    // ---- validate and group by trace (array order kept within a trace)
+    std::vector<int> first_seen(cfg.max_traces, -1);
+    std::vector<std::vector<uint32_t>> groups;
+    std::vector<uint32_t> gtrace;
+    for (uint32_t i = 0; i < nsegs; ++i) {
+        const scl_segment &g = segs[i];
+        if (g.trace_id >= cfg.max_traces)
+            return fail(c, SCL_EINVAL, "segment %u: trace_id %u >= max_traces %u", i, g.trace_id, cfg.max_traces);
+        if (g.ev.n && (!g.ev.delta || !g.ev.addr || !g.ev.line || !g.ev.is_python))
+            return fail(c, SCL_EINVAL, "segment %u: NULL event array", i);
+        if (g.ev.n >= UNIT_ALIGN && !(aligned16(g.ev.delta) && aligned16(g.ev.addr) && aligned16(g.ev.line) &&
+                                      aligned16(g.ev.is_python)))
+            return fail(c, SCL_EINVAL, "segment %u: event arrays must be 16-byte aligned", i);
+        if (g.ev.n >= (1ull << 40)) return fail(c, SCL_EINVAL, "segment %u: too many events", i);
+        if (g.cp.n && (!g.cp.size || !g.cp.line || !g.cp.is_python))
+            return fail(c, SCL_EINVAL, "segment %u: NULL memcpy array", i);
+        int &fs = first_seen[g.trace_id];
+        if (fs < 0) {
+            fs = (int)groups.size();
+            groups.emplace_back();
+            gtrace.push_back(g.trace_id);
+        }
+        groups[fs].push_back(i);
+    }
+    const uint32_t nbt = (uint32_t)groups.size();
+    if (nbt == 0) return SCL_OK;
+
+    // longest trace first: its units enter the walker queue first
+    std::vector<uint64_t> tev(nbt, 0);
+    for (uint32_t b = 0; b < nbt; ++b)
+        for (uint32_t i : groups[b]) tev[b] += segs[i].ev.n;
+    std::vector<uint32_t> order(nbt);
+    for (uint32_t b = 0; b < nbt; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return tev[x] > tev[y]; });
+
+    // ---- plan
+    const uint64_t UE = c->tune.unit_events;
+    const uint32_t shift = cfg.sample_budget_shift;
+    std::vector<Unit> units;
+    std::vector<BTrace> bts(nbt);
+    std::vector<CompactGroup> cgroups;
+    std::vector<LeakTile> ltiles;
+    std::vector<CopyTile> ctiles;
+    uint64_t rec_total = 0, bit_total = 0;
+    for (uint32_t bi = 0; bi < nbt; ++bi) {
+        const uint32_t b = order[bi];
+        BTrace &B = bts[bi];
+        memset(&B, 0, sizeof B);
+        B.trace = gtrace[b];
+        B.u0 = (uint32_t)units.size();
+        B.c0 = (uint32_t)ctiles.size();
+        uint64_t gidx = c->h_events[B.trace];
+        for (uint32_t i : groups[b]) {
+            const scl_segment &g = segs[i];
+            for (uint64_t off = 0; off < g.ev.n; off += UE) {
+                Unit U;
+                memset(&U, 0, sizeof U);
+                U.len = std::min<uint64_t>(UE, g.ev.n - off);
+                U.delta = g.ev.delta + off;
+                U.py = g.ev.is_python + off;
+                U.addr = g.ev.addr + off;
+                U.line = g.ev.line + off;
+                U.gidx0 = gidx;
+                U.bit0 = bit_total;
+                U.rec0 = rec_total;
+                const uint64_t cap = (U.len >> shift) + 64;
+                U.spec_cap = U.src_cap = (uint32_t)std::min<uint64_t>(cap, 0xffffffffu);
+                U.trace = B.trace;
+                U.bt = bi;
+                units.push_back(U);
+                gidx += U.len;
+                bit_total += (U.len + 31) / 32;
+                rec_total += (uint64_t)U.src_cap + U.spec_cap;
+            }
+            for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
+                CopyTile T;
+                T.len = (uint32_t)std::min<uint64_t>(COPY_TILE, g.cp.n - off);
+                T.size = g.cp.size + off;
+                T.line = g.cp.line + off;
+                T.py = g.cp.is_python + off;
+                T.bt = bi;
+                ctiles.push_back(T);
+            }
+            B.n_ev += g.ev.n;
+            B.n_cp += g.cp.n;
+        }
+        B.nu = (uint32_t)units.size() - B.u0;
+        B.nc = (uint32_t)ctiles.size() - B.c0;
+        if (B.nu) {
+            units[B.u0].first = 1;
+            units[B.u0 + B.nu - 1].last = 1;
+        }
+        for (uint32_t k = 0; k < B.nu; k += 8) cgroups.push_back({B.u0 + k, std::min<uint32_t>(8, B.nu - k)});
+    }
+    for (uint32_t u = 0; u < units.size(); ++u)
+        for (uint64_t k = 0; k * LEAK_TILE < units[u].len; ++k) ltiles.push_back({u, (uint32_t)k});
+    const int nunits = (int)units.size();
+
+    // ---- plan blob: units | bts | groups | leak tiles | copy tiles
+    const size_t o_units = 0;
+    const size_t o_bts = al256(o_units + sizeof(Unit) * units.size());
+    const size_t o_grp = al256(o_bts + sizeof(BTrace) * bts.size());
+    const size_t o_lt = al256(o_grp + sizeof(CompactGroup) * cgroups.size());
+    const size_t o_ct = al256(o_lt + sizeof(LeakTile) * ltiles.size());
+    const size_t blob = al256(o_ct + sizeof(CopyTile) * ctiles.size());
+    if (c->plan_pending) {
+        CK(cudaEventSynchronize(c->plan_done), "wait for previous plan upload");
+        c->plan_pending = false;
+    }
+    if (blob > c->h_plan_cap) {
+        if (c->h_plan) cudaFreeHost(c->h_plan);
+        c->h_plan = nullptr;
+        c->h_plan_cap = 0;
+        CK(cudaMallocHost(&c->h_plan, blob * 2), "pinned plan buffer");
+        c->h_plan_cap = blob * 2;
+    }
+    char *hp = static_cast<char *>(c->h_plan);
+    memcpy(hp + o_units, units.data(), sizeof(Unit) * units.size());
+    memcpy(hp + o_bts, bts.data(), sizeof(BTrace) * bts.size());
+    memcpy(hp + o_grp, cgroups.data(), sizeof(CompactGroup) * cgroups.size());
+    memcpy(hp + o_lt, ltiles.data(), sizeof(LeakTile) * ltiles.size());
+    memcpy(hp + o_ct, ctiles.data(), sizeof(CopyTile) * ctiles.size());
+
+    int r;
+    if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;
+    if ((r = ensure(c, c->ures, sizeof(UnitRes) * std::max(1, nunits), s, "unit results"))) return r;
+    if ((r = ensure(c, c->pub, sizeof(uint32_t) * std::max(1, nunits), s, "progress counters"))) return r;
+    if ((r = ensure(c, c->recs, sizeof(Rec) * std::max<uint64_t>(1, rec_total), s, "sample records"))) return r;
+    if ((r = ensure(c, c->cross, sizeof(Cross) * std::max<uint64_t>(1, rec_total), s, "crossings"))) return r;
+    if ((r = ensure(c, c->recl, std::max<uint64_t>(1, rec_total), s, "reclaim flags"))) return r;
+    if ((r = ensure(c, c->bits, 4 * std::max<uint64_t>(1, bit_total), s, "free bitmask"))) return r;
+    if ((r = ensure(c, c->btres, sizeof(BTraceRes) * nbt, s, "batch trace results"))) return r;
+    if ((r = ensure(c, c->ctsum, sizeof(uint64_t) * std::max<size_t>(1, ctiles.size()), s, "copy tile sums")))
+        return r;
+
+    char *dp = static_cast<char *>(c->plan.p);
+    CK(cudaMemcpyAsync(dp, hp, blob, cudaMemcpyHostToDevice, s), "plan upload");
+    CK(cudaEventRecord(c->plan_done, s), "plan event");
+    c->plan_pending = true;
+    CK(cudaMemsetAsync(c->ures.p, 0, sizeof(UnitRes) * nunits, s), "memset");
+    CK(cudaMemsetAsync(c->pub.p, 0, sizeof(uint32_t) * nunits, s), "memset");
+    CK(cudaMemsetAsync(c->recl.p, 0, rec_total, s), "memset");
+    CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * nbt, s), "memset");
+    CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned), s), "memset");
+
+    const Unit *d_units = reinterpret_cast<const Unit *>(dp + o_units);
+    const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + o_bts);
+    c->last_stream = s;
+
+    if (nunits) {
+        LaunchWalk w;
+        w.units = d_units;
+        w.nunits = nunits;
+        w.ures = static_cast<UnitRes *>(c->ures.p);
+        w.recs = static_cast<Rec *>(c->recs.p);
+        w.pub = static_cast<uint32_t *>(c->pub.p);
+        w.bits = static_cast<uint32_t *>(c->bits.p);
+        w.traces = c->traces;
+        w.T = cfg.threshold;
+        w.ext_cap = c->tune.ext_events;
+        w.queue = c->queue;
+        w.err = c->errw;
+        w.spin = cfg.spin_limit;
+        w.warps_per_block = (int)c->tune.warps_per_block;
+        int bps = 0;
+        if (walk_occupancy(w.warps_per_block, &bps) || bps < 1) bps = 1;
+        const int max_blocks = bps * c->num_sms;
+        const int need = (nunits + w.warps_per_block - 1) / w.warps_per_block;
+        w.blocks = std::max(1, std::min(max_blocks, need));
+        {
+            Prof p(c, s, "walk");
+            CK(launch_walk(w, s), "launch walk");
+        }
+        {
+            Prof p(c, s, "resolve");
+            CK(launch_resolve(d_units, nunits, w.ures, w.recs, s), "launch resolve");
+        }
+        {
+            Prof p(c, s, "fallback");
+            CK(launch_fallback(d_units, d_bts, (int)nbt, w.ures, w.recs, cfg.threshold, c->errw, cfg.spin_limit, s),
+               "launch fallback");
+        }
+    }
+    LaunchPost a;
+    a.units = d_units;
+    a.nunits = nunits;
+    a.bts = d_bts;
+    a.nbt = (int)nbt;
+    a.ures = static_cast<UnitRes *>(c->ures.p);
+    a.btres = static_cast<BTraceRes *>(c->btres.p);
+    a.recs = static_cast<const Rec *>(c->recs.p);
+    a.cross = static_cast<Cross *>(c->cross.p);
+    a.recl = static_cast<uint8_t *>(c->recl.p);
+    a.bits = static_cast<const uint32_t *>(c->bits.p);
+    a.traces = c->traces;
+    a.lines = c->lines;
+    a.log = c->log;
+    a.log_cap = cfg.sample_log_capacity;
+    a.n_lines = cfg.n_lines;
+    a.T = cfg.threshold;
+    a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
+    a.groups = reinterpret_cast<const CompactGroup *>(dp + o_grp);
+    a.ngroups = (int)cgroups.size();
+    a.ltiles = reinterpret_cast<const LeakTile *>(dp + o_lt);
+    a.nltiles = (int)ltiles.size();
+    a.ctiles = reinterpret_cast<const CopyTile *>(dp + o_ct);
+    a.nctiles = (int)ctiles.size();
+    a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
+    a.err = c->errw;
+    {
+        Prof p(c, s, "scan");
+        CK(launch_scan(a, s), "launch scan");
+    }
+    {
+        Prof p(c, s, "compact");
+        CK(launch_compact(a, s), "launch compact");
+    }
+    {
+        Prof p(c, s, "scan2");
+        CK(launch_scan2(a, s), "launch scan2");
+    }
+    {
+        Prof p(c, s, "leak");
+        CK(launch_leak(a, s), "launch leak");
+    }
+    {
+        Prof p(c, s, "epi");
+        CK(launch_epi(a, s), "launch epi");
+    }
+    {
+        Prof p(c, s, "copy_sum");
+        CK(launch_copy_sum(a, s), "launch copy sum");
+    }
+    {
+        Prof p(c, s, "copy_scan");
+        CK(launch_copy_scan(a, s), "launch copy scan");
+    }
+    {
+        Prof p(c, s, "copy_apply");
+        CK(launch_copy_apply(a, s), "launch copy apply");
+    }
+    {
+        Prof p(c, s, "state");
+        CK(launch_state(a, s), "launch state");
+    }
+    for (uint32_t bi = 0; bi < nbt; ++bi) c->h_events[bts[bi].trace] += bts[bi].n_ev;
+    return SCL_OK;
+}
+
+int scl_replay_batch_host(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stream) {
+    if (!c) return SCL_EINVAL;
+    if (nsegs && !segs) return fail(c, SCL_EINVAL, "segs is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    size_t need = 0;
+    for (uint32_t i = 0; i < nsegs; ++i) {
+        const scl_segment &g = segs[i];
+        need += al256(g.ev.n * 8) * 2 + al256(g.ev.n * 4) + al256(g.ev.n) + al256(g.cp.n * 8) + al256(g.cp.n * 4) +
+                al256(g.cp.n);
+    }
+    int r = ensure(c, c->stage, std::max<size_t>(need, 256), s, "host staging buffer");
+    if (r) return r;
+    std::vector<scl_segment> dsegs(segs, segs + nsegs);
+    char *p = static_cast<char *>(c->stage.p);
+    auto put = [&](const void *src, size_t bytes) -> const void * {
+        char *dst = p;
+        if (bytes) {
+            if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return nullptr;
+        }
+        p += al256(bytes);
+        return dst;
+    };
+    for (uint32_t i = 0; i < nsegs; ++i) {
+        const scl_segment &g = segs[i];
+        scl_segment &d = dsegs[i];
+        if (g.ev.n && (!g.ev.delta || !g.ev.addr || !g.ev.line || !g.ev.is_python))
+            return fail(c, SCL_EINVAL, "segment %u: NULL event array", i);
+        if (g.cp.n && (!g.cp.size || !g.cp.line || !g.cp.is_python))
+            return fail(c, SCL_EINVAL, "segment %u: NULL memcpy array", i);
+        d.ev.delta = static_cast<const int64_t *>(put(g.ev.delta, g.ev.n * 8));
+        d.ev.addr = static_cast<const uint64_t *>(put(g.ev.addr, g.ev.n * 8));
+        d.ev.line = static_cast<const uint32_t *>(put(g.ev.line, g.ev.n * 4));
+        d.ev.is_python = static_cast<const uint8_t *>(put(g.ev.is_python, g.ev.n));
+        d.cp.size = static_cast<const uint64_t *>(put(g.cp.size, g.cp.n * 8));
+        d.cp.line = static_cast<const uint32_t *>(put(g.cp.line, g.cp.n * 4));
+        d.cp.is_python = static_cast<const uint8_t *>(put(g.cp.is_python, g.cp.n));
+        if (!d.ev.delta || !d.ev.addr || !d.ev.line || !d.ev.is_python || !d.cp.size || !d.cp.line || !d.cp.is_python)
+            return fail(c, SCL_ECUDA, "host to device copy failed");
+    }
+    return scl_replay_batch(c, dsegs.data(), nsegs, stream);
+}
+
+int scl_sync(scl_ctx *c) {
+    if (!c) return SCL_EINVAL;
+    return sync_and_check(c);
+}
+
+int scl_samples(scl_ctx *c, uint32_t trace, scl_sample *out, uint64_t cap, uint64_t *n_out) {
+    if (!c || !n_out) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    int r = sync_and_check(c);
+    if (r) return r;
+    DevTrace t;
+    CK(cudaMemcpy(&t, c->traces + trace, sizeof t, cudaMemcpyDeviceToHost), "read trace state");
+    *n_out = t.n_samples;
+    const uint64_t have = std::min<uint64_t>(t.n_samples, c->cfg.sample_log_capacity);
+    if (cap < have) return fail(c, SCL_ERANGE, "output holds %llu samples, %llu needed", (unsigned long long)cap,
+                                (unsigned long long)have);
+    if (have) {
+        static_assert(sizeof(Sample) == sizeof(scl_sample), "sample layout");
+        CK(cudaMemcpy(out, c->log + (uint64_t)trace * c->cfg.sample_log_capacity, sizeof(Sample) * have,
+                      cudaMemcpyDeviceToHost),
+           "read samples");
+    }
+    if (t.n_samples > have)
+        return fail(c, SCL_EOVERFLOW, "%llu samples taken, only the first %llu retained (sample_log_capacity)",
+                    (unsigned long long)t.n_samples, (unsigned long long)have);
+    return SCL_OK;
+}
+
+int scl_line_stats(scl_ctx *c, uint32_t trace, scl_line_stat *out, uint32_t cap, uint32_t *n_out) {
+    if (!c || !n_out) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    int r = sync_and_check(c);
+    if (r) return r;
+    const uint32_t L = c->cfg.n_lines;
+    *n_out = L;
+    if (cap < L) return fail(c, SCL_ERANGE, "output holds %u rows, %u needed", cap, L);
+    std::vector<LineRow> rows(L);
+    CK(cudaMemcpy(rows.data(), c->lines + (uint64_t)trace * L, sizeof(LineRow) * L, cudaMemcpyDeviceToHost),
+       "read line stats");
+    for (uint32_t l = 0; l < L; ++l) {
+        scl_line_stat &o = out[l];
+        const LineRow &x = rows[l];
+        o.n_growth = x.n_growth; o.n_shrink = x.n_shrink;
+        o.A = x.A; o.F = x.F; o.A_py = x.A_py; o.F_py = x.F_py; o.net = x.net;
+        o.copy_samples[0] = x.copy_samples[0]; o.copy_samples[1] = x.copy_samples[1];
+        o.copy_bytes[0] = x.copy_bytes[0]; o.copy_bytes[1] = x.copy_bytes[1];
+    }
+    return SCL_OK;
+}
+
+int scl_leak_scores(scl_ctx *c, uint32_t trace, scl_leak_score *out, uint32_t cap, uint32_t *n_out) {
+    if (!c || !n_out) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    int r = sync_and_check(c);
+    if (r) return r;
+    const uint32_t L = c->cfg.n_lines;
+    *n_out = L;
+    if (cap < L) return fail(c, SCL_ERANGE, "output holds %u rows, %u needed", cap, L);
+    CK(launch_scores(c->lines, trace, L, c->cfg.leak_rule, c->scores, c->last_stream), "launch scores");
+    CK(cudaMemcpyAsync(out, c->scores, sizeof(scl_leak_score) * L, cudaMemcpyDeviceToHost, c->last_stream),
+       "read scores");
+    CK(cudaStreamSynchronize(c->last_stream), "sync");
+    return SCL_OK;
+}
+
+int scl_trace_state(scl_ctx *c, uint32_t trace, scl_trace_info *out) {
+    if (!c || !out) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    int r = sync_and_check(c);
+    if (r) return r;
+    DevTrace t;
+    CK(cudaMemcpy(&t, c->traces + trace, sizeof t, cudaMemcpyDeviceToHost), "read trace state");
+    memset(out, 0, sizeof *out);
+    out->n_events = t.n_events; out->n_copies = t.n_copies; out->n_samples = t.n_samples;
+    out->c = t.c; out->A = t.A; out->F = t.F; out->A_py = t.A_py; out->F_py = t.F_py;
+    out->footprint = t.footprint; out->hwm = t.hwm;
+    out->tracked_addr = t.tracked_addr; out->tracked_idx = t.tracked_idx; out->tracked_line = t.tracked_line;
+    out->tracked_valid = (uint8_t)t.tracked_valid; out->tracked_reclaimed = (uint8_t)t.tracked_reclaimed;
+    out->copy_counter = t.copy_counter;
+    return SCL_OK;
+}
+
+struct StateHeader {
+    uint32_t magic, n_lines;
+    int64_t threshold;
+    uint32_t copy_multiple, leak_rule;
+};
+
+int scl_state_export(scl_ctx *c, uint32_t trace, void *buf, uint64_t cap, uint64_t *n_out) {
+    if (!c || !n_out) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    const uint64_t need = sizeof(StateHeader) + sizeof(DevTrace) + sizeof(LineRow) * (uint64_t)c->cfg.n_lines;
+    *n_out = need;
+    if (!buf) return SCL_OK;
+    if (cap < need) return fail(c, SCL_ERANGE, "state needs %llu bytes", (unsigned long long)need);
+    int r = sync_and_check(c);
+    if (r) return r;
+    StateHeader h{STATE_MAGIC, c->cfg.n_lines, c->cfg.threshold, c->cfg.copy_multiple, c->cfg.leak_rule};
+    char *p = static_cast<char *>(buf);
+    memcpy(p, &h, sizeof h);
+    CK(cudaMemcpy(p + sizeof h, c->traces + trace, sizeof(DevTrace), cudaMemcpyDeviceToHost), "export");
+    CK(cudaMemcpy(p + sizeof h + sizeof(DevTrace), c->lines + (uint64_t)trace * c->cfg.n_lines,
+                  sizeof(LineRow) * c->cfg.n_lines, cudaMemcpyDeviceToHost),
+       "export");
+    return SCL_OK;
+}
+
+int scl_state_import(scl_ctx *c, uint32_t trace, const void *buf, uint64_t n) {
+    if (!c || !buf) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    const uint64_t need = sizeof(StateHeader) + sizeof(DevTrace) + sizeof(LineRow) * (uint64_t)c->cfg.n_lines;
+    StateHeader h;
+    if (n < sizeof h) return fail(c, SCL_EINVAL, "state buffer too short");
+    memcpy(&h, buf, sizeof h);
+    if (h.magic != STATE_MAGIC || n != need || h.n_lines != c->cfg.n_lines || h.threshold != c->cfg.threshold ||
+        h.copy_multiple != c->cfg.copy_multiple || h.leak_rule != c->cfg.leak_rule)
+        return fail(c, SCL_EINVAL, "state was exported under another configuration");
+    int r = sync_and_check(c);
+    if (r) return r;
+    const char *p = static_cast<const char *>(buf);
+    DevTrace t;
+    memcpy(&t, p + sizeof h, sizeof t);
+    if (c->cfg.sample_log_capacity == 0) t.n_samples = t.n_samples;  // counts are kept; records are not
+    CK(cudaMemcpy(c->traces + trace, &t, sizeof t, cudaMemcpyHostToDevice), "import");
+    CK(cudaMemcpy(c->lines + (uint64_t)trace * c->cfg.n_lines, p + sizeof h + sizeof t,
+                  sizeof(LineRow) * c->cfg.n_lines, cudaMemcpyHostToDevice),
+       "import");
+    c->h_events[trace] = t.n_events;
+    return SCL_OK;
+}
+
+int scl_trace_reset(scl_ctx *c, uint32_t trace, void *stream) {
+    if (!c) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        Prof p(c, s, "reset");
+        CK(launch_reset(c->traces, c->lines, trace, c->cfg.n_lines, c->cfg.initial_footprint, c->cfg.copy_phase, s),
+           "launch reset");
+    }
+    c->h_events[trace] = 0;
+    c->last_stream = s;
+    return SCL_OK;
+}
+
+int scl_profile_enable(scl_ctx *c, int on) {
+    if (!c) return SCL_EINVAL;
+    c->prof = on != 0;
+    return SCL_OK;
+}
+
+int scl_profile_reset(scl_ctx *c) {
+    if (!c) return SCL_EINVAL;
+    prof_collect(c);
+    c->prof_acc.clear();
+    return SCL_OK;
+}
+
+int scl_kernel_times(scl_ctx *c, const char **names, double *ms, uint64_t *launches, uint32_t cap,
+                     uint32_t *n_out) {
+    if (!c || !n_out) return SCL_EINVAL;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    prof_collect(c);
+    *n_out = (uint32_t)c->prof_acc.size();
+    if (cap < c->prof_acc.size()) return fail(c, SCL_ERANGE, "need %u entries", *n_out);
+    for (size_t i = 0; i < c->prof_acc.size(); ++i) {
+        if (names) names[i] = c->prof_acc[i].first;
+        if (ms) ms[i] = c->prof_acc[i].second.first;
+        if (launches) launches[i] = c->prof_acc[i].second.second;
+    }
+    return SCL_OK;
+}
+
+int scl_selftest_wait(scl_ctx *c, uint64_t limit, void *stream) {
+    if (!c) return SCL_EINVAL;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(c->errw, 0, sizeof(ErrWord), s), "clear error word");
+    CK(launch_wait_selftest(c->errw, limit, s), "launch wait self test");
+    c->last_stream = s;
+    const int r = sync_and_check(c);
+    CK(cudaMemset(c->errw, 0, sizeof(ErrWord)), "clear error word");
+    return r;
+}
+
+int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stream, scl_tuning *best_out,
+                 double *best_ms_out) {
+    (void)segs; (void)nsegs; (void)stream;
+    if (!c) return SCL_EINVAL;
+    if (best_out) *best_out = c->tune;
+    if (best_ms_out) *best_ms_out = 0.0;
+    return fail(c, SCL_EINVAL, "autotune not available yet");
+}
+
+}  // extern "C"

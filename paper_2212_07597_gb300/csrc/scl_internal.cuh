@@ -1,0 +1,224 @@
+// scl_internal.cuh -- device-side layouts and warp primitives of libscl.
+//
+// Work decomposition (see the kernels for the method steps they implement):
+//   A batch of segments is cut into *units*: contiguous runs of one trace's events,
+//   at most `unit_events` long, starting at multiples of 1024 events.  One warp
+//   walks one unit through the threshold sampler of Section 3.2 (k_walk).  The
+//   first unit of a trace in the batch starts from the trace's resident counter;
+//   later units start speculatively from a zero counter and are reconciled
+//   afterwards: two runs of the reset-at-threshold counter over the same events
+//   agree from any position where both have just reset, so the walker of unit u
+//   continues into unit u+1 from its own exit state until it meets a reset that
+//   unit u+1's own walk also took (a "merge"); the true samples of u+1 are the
+//   lookahead's up to the merge and u+1's own after it.  Units whose lookahead
+//   never meets are re-walked in order by k_fallback.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace scl {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int E = 4;               // events per lane per walker step
+constexpr int STEP = 32 * E;       // events per walker step
+constexpr int TILE = 512;          // events per shared-memory stage
+constexpr int NST = 4;             // stages per walker warp
+constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
+constexpr int LEAK_TILE = 4096;    // events per leak-pass block
+constexpr int COPY_TILE = 4096;    // memcpy events per copy-pass block
+constexpr int SMEM_LINES_MAX = 1024;  // per-line tables kept in shared memory up to this L
+
+// error codes mirrored from scl.h
+constexpr int E_INVAL = -1, E_NOMEM = -2, E_CUDA = -3, E_TIMEOUT = -4, E_OVERFLOW = -5, E_RANGE = -6;
+
+// ---------------------------------------------------------------- resident state
+struct DevTrace {                   // one per trace slot
+    int64_t c, A, F, A_py, F_py;    // counter and open-window totals (Section 3.2)
+    int64_t footprint, hwm;         // Section 3.3 footprint, Section 3.4 high-water mark
+    uint64_t tracked_addr, tracked_idx;
+    uint32_t tracked_line, tracked_valid, tracked_reclaimed, pad0;
+    uint64_t n_events, n_copies, n_samples, copy_counter;
+};
+
+struct LineRow {                    // one per (trace, line); same field order as scl_line_stat + leak pair
+    unsigned long long n_growth, n_shrink;
+    long long A, F, A_py, F_py, net;
+    unsigned long long copy_samples[2], copy_bytes[2];
+    unsigned long long mallocs, frees;
+};
+constexpr int LINE_WORDS = 13;
+
+struct Sample {                     // layout of scl_sample (56 bytes)
+    uint64_t idx;
+    int64_t A, F, A_py, F_py, footprint;
+    uint32_t line;
+    int8_t kind;
+    uint8_t is_python, is_hwm, pad;
+};
+
+// ---------------------------------------------------------------- batch plan
+struct Unit {
+    const int64_t *delta;
+    const uint8_t *py;
+    const uint64_t *addr;
+    const uint32_t *line;
+    uint64_t len;
+    uint64_t gidx0;       // trace event index of the unit's first event
+    uint64_t bit0;        // first 32-event word of the unit in the batch free bitmask
+    uint64_t rec0;        // first record slot of the unit: [src_cap | spec_cap]
+    uint32_t src_cap, spec_cap;
+    uint32_t trace;       // resident trace slot
+    uint32_t bt;          // index of the trace within the batch
+    uint32_t first, last; // first / last unit of its trace in this batch
+};
+
+struct BTrace {           // one per trace present in the batch
+    uint32_t trace, u0, nu, pad;   // slot, first unit, unit count
+    uint64_t n_ev;                 // events of this trace in the batch
+    uint64_t n_cp;                 // memcpy events of this trace in the batch
+    uint32_t c0, nc;               // copy tiles
+};
+
+struct CopyTile {
+    const uint64_t *size;
+    const uint32_t *line;
+    const uint8_t *py;
+    uint32_t len, bt;
+};
+
+// sampler record written by the walker (48 bytes)
+struct Rec {
+    uint32_t rel;         // event offset within the unit
+    int32_t kind;         // +1 / -1
+    int64_t A, F, A_py, F_py;
+    int64_t P;            // sum of the unit's deltas up to and including rel
+};
+
+struct Cross {            // a high-water crossing: the tracked block (Section 3.4)
+    uint32_t rel, line;
+    uint64_t addr;
+};
+
+struct UnitRes {
+    // own walk
+    int64_t total;                              // sum of the unit's deltas
+    int64_t ex_c, ex_A, ex_F, ex_Apy, ex_Fpy;   // exit state of the own walk
+    uint32_t n_spec;                            // records of the own walk
+    // lookahead (written by the previous unit's walker) / fallback
+    uint32_t n_src;
+    // resolution
+    uint32_t src_used, spec_skip, broken, count;
+    uint32_t has_growth, n_cross;
+    int64_t max_growth_P;                       // largest unit-local prefix at a final growth record
+    int64_t tx_c, tx_A, tx_F, tx_Apy, tx_Fpy;   // true exit state
+    // scans
+    uint64_t sample_off;                        // first sample of the unit within its trace's batch samples
+    int64_t fp_base;                            // footprint before the unit's first event
+    int64_t hwm_in;                             // high-water mark entering the unit
+    int64_t enter_unit;                         // unit holding the last crossing before this one (-1: none)
+};
+
+struct BTraceRes {
+    uint64_t n_samples;                         // samples of this trace in the batch
+    int64_t fp_end, hwm_end;
+    int64_t last_cross_unit;                    // -1 if no crossing in the batch
+    uint32_t pending_hit, pad;                  // the previously tracked block was freed in this batch
+    uint64_t copy_total;                        // bytes copied in the batch
+};
+
+struct ErrWord {
+    int code;
+    unsigned detail0;
+    unsigned long long detail1;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void set_error(ErrWord *e, int code, unsigned d0, unsigned long long d1) {
+    if (atomicCAS(&e->code, 0, code) == 0) {
+        e->detail0 = d0;
+        e->detail1 = d1;
+    }
+}
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int64_t warp_sum(int64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int64_t warp_max(int64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int64_t t = __shfl_xor_sync(FULL, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// -------- mbarrier + bulk copy (cp.async.bulk, global -> shared, no multicast)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier, called by all 32 lanes of a warp.
+// Every lane polls (so each observes the phase completion); the answer is agreed by
+// vote, so all lanes return the same value.  False if `limit` polls passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit) {
+    uint32_t a = smem_addr(bar);
+    for (unsigned long long it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (__all_sync(0xffffffffu, ok != 0)) return true;
+    }
+    return false;
+}
+
+}  // namespace scl

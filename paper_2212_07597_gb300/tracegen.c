@@ -73,10 +73,11 @@ static double det_log(double x) {
     return 2.0 * sum + (double)e * LN2;
 }
 
-/* floor(lo * (hi/lo)^u) for u uniform in [0,1): log-uniform on [lo, hi) */
-static uint64_t log_uniform(uint64_t *s, uint64_t lo, uint64_t hi) {
+/* floor(lo * (hi/lo)^u) for u uniform in [0,1): log-uniform on [lo, hi);
+ * lnr = ln(hi/lo), computed once by the caller */
+static uint64_t log_uniform(uint64_t *s, uint64_t lo, uint64_t hi, double lnr) {
     double u = u01(s);
-    double v = (double)lo * det_exp(u * det_log((double)hi / (double)lo));
+    double v = (double)lo * det_exp(u * lnr);
     uint64_t x = (uint64_t)v;
     if (x < lo) x = lo;
     if (x >= hi) x = hi - 1;
@@ -143,6 +144,8 @@ int tg_events(const tg_params *p, uint64_t seed, uint64_t trace,
     for (uint32_t k = 0; k < p->n_leak_lines && k < 16; ++k)
         if (p->leak_lines[k] < p->n_lines) leakmask[p->leak_lines[k]] = 1;
     uint64_t bump = 0x100000;
+    const double ln_size = det_log((double)p->size_hi / (double)p->size_lo);
+    const double ln_leak = p->leak_hi > p->leak_lo ? det_log((double)p->leak_hi / (double)p->leak_lo) : 0.0;
     uint64_t next_ramp = p->ramp_count ? (p->n / p->ramp_count) / 2 : UINT64_MAX, ramp_i = 0;
     uint64_t next_big = p->big_count ? (p->n / p->big_count) / 2 : UINT64_MAX, big_i = 0;
     int rc = 0;
@@ -165,10 +168,10 @@ int tg_events(const tg_params *p, uint64_t seed, uint64_t trace,
         if (forced || nlive == 0 || ukind < p->p_malloc) {
             if (!forced) {
                 if (leakmask[ln] && p->leak_hi > p->leak_lo) {
-                    sz = (int64_t)log_uniform(&s, p->leak_lo, p->leak_hi);
+                    sz = (int64_t)log_uniform(&s, p->leak_lo, p->leak_hi, ln_leak);
                     if (u01(&s) < p->p_leak_unfreed) keep_live = 0;
                 } else {
-                    sz = (int64_t)log_uniform(&s, p->size_lo, p->size_hi);
+                    sz = (int64_t)log_uniform(&s, p->size_lo, p->size_hi, ln_size);
                 }
             }
             uint64_t a;
@@ -214,10 +217,11 @@ int tg_copies(uint64_t m, uint32_t n_lines, double zipf_s, double p_python, uint
     uint64_t s = mix_seed(seed ^ 0x5bd1e9955bd1e995ull, trace);
     zipf_t z;
     if (zipf_init(&z, n_lines, zipf_s)) return -1;
+    const double lnr = det_log((double)hi / (double)lo);
     for (uint64_t j = 0; j < m; ++j) {
         line[j] = zipf_draw(&z, &s);
         py[j] = u01(&s) < p_python;
-        size[j] = log_uniform(&s, lo, hi);
+        size[j] = log_uniform(&s, lo, hi, lnr);
     }
     free(z.cdf);
     return 0;
@@ -259,7 +263,8 @@ int tg_constant(uint64_t n, int64_t size, uint32_t n_lines, uint64_t seed, uint6
 int tg_lengths(uint64_t count, uint64_t lo, uint64_t hi, uint64_t seed, uint64_t *out) {
     if (lo == 0 || hi <= lo) return -1;
     uint64_t s = mix_seed(seed ^ 0x7777ull, 0);
-    for (uint64_t i = 0; i < count; ++i) out[i] = log_uniform(&s, lo, hi);
+    const double lnr = det_log((double)hi / (double)lo);
+    for (uint64_t i = 0; i < count; ++i) out[i] = log_uniform(&s, lo, hi, lnr);
     return 0;
 }
 

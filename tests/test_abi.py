@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol include/scl.h declares (CPU only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2212_07597_gb300 import build as scl_build
+from paper_2212_07597_gb300 import scl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "scl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(scl_[a-z_]+)\s*\(", src)))
+
+
+def test_builds_and_exports_every_declared_symbol():
+    path = scl_build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(scl.EXPORTS)
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(scl.scl_config) == 64
+    assert ctypes.sizeof(scl.scl_segment) == 8 + 40 + 32
+    assert scl.SAMPLE_DTYPE.itemsize == 56
+    assert scl.LINE_STAT_DTYPE.itemsize == 88
+    assert scl.LEAK_DTYPE.itemsize == 40
+    assert scl.TRACE_INFO_DTYPE.itemsize == 112
+
+
+def test_config_defaults_without_gpu():
+    cfg = scl.config()
+    assert cfg.threshold == 10_485_767 and cfg.copy_multiple == 2 and cfg.n_lines == 256
+    assert cfg.sample_budget_shift == 4 and cfg.leak_rule == 0
+
+
+def test_init_fails_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(scl.SclError):
+        scl.scl_replay_init(scl.config())

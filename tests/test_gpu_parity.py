@@ -1,0 +1,187 @@
+"""GPU parity: libscl (through its C ABI) against the CPU oracle, bit-exact on every output.
+
+Everything compared is integer: sample indices, kinds, window totals, footprints,
+line ids, flags, high-water marks, per-line totals, leak pairs and their rational
+scores, copy-volume counts and the resident trace state.  The tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_07597_gb300 import scl
+from paper_2212_07597_gb300 import tracegen as tg
+from tests.gpu_util import assert_same, gpu_ctx, oracle_of, replay
+
+pytestmark = pytest.mark.gpu
+T0 = tg.T_PLAIN
+
+
+def test_plain_1m_default_tuning():
+    tr = tg.plain_trace(1_000_000, seed=0)
+    ctx = gpu_ctx(T0)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T0))
+
+
+@pytest.mark.parametrize("unit", [1024, 4096, 32768])
+def test_small_units_speculation_and_merge(unit):
+    tr = tg.plain_trace(300_001, seed=1, leak_lines=(0, 3))
+    ctx = gpu_ctx(T0, unit=unit)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T0))
+
+
+@pytest.mark.parametrize("T,shift", [(1, 0), (1_048_573, 2), (104_857_601, 4)])
+def test_thresholds(T, shift):
+    tr = tg.plain_trace(150_000 + 7, seed=2, big_count=3, big_size=4 * tg.GIB)
+    ctx = gpu_ctx(T, shift=shift, unit=4096)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T))
+
+
+@pytest.mark.parametrize("T", [1_048_573, 10_485_767])
+def test_adversarial_never_merges(T):
+    d, a, l, y = tg.adversarial(100_000, T, period=4099)
+    tr = tg.Trace(d, a, l, y)
+    ctx = gpu_ctx(T, unit=1024)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T))
+
+
+def test_constant_closed_form():
+    T = 1_048_573
+    d, a, l, y = tg.constant(65536 + 100, 4096, 256)
+    ctx = gpu_ctx(T, unit=2048)
+    keep = replay(ctx, [(0, tg.Trace(d, a, l, y))])
+    s = scl.scl_samples(ctx, 0)
+    assert np.array_equal(s["idx"], np.arange(1, len(d) // 256 + 1, dtype=np.uint64) * 256 - 1)
+    assert s["is_hwm"].all()
+
+
+def test_free_heavy_with_address_reuse():
+    tr = tg.plain_trace(200_000, seed=5, p_malloc=0.3, addr_reuse=True)
+    ctx = gpu_ctx(1_048_573, unit=8192)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, 1_048_573))
+
+
+def test_segments_across_calls_equal_whole():
+    tr = tg.plain_trace(250_000, seed=6, leak_lines=(1,))
+    rng = np.random.default_rng(0)
+    cuts = np.sort(rng.choice(np.arange(1, tr.n), 6, replace=False))
+    ccuts = np.sort(rng.choice(np.arange(1, len(tr.csize)), 6, replace=False))
+    pieces = [tr.slice(a, b, ca, cb) for a, b, ca, cb in zip(np.r_[0, cuts], np.r_[cuts, tr.n],
+                                                            np.r_[0, ccuts], np.r_[ccuts, len(tr.csize)])]
+    ctx = gpu_ctx(T0, unit=4096)
+    keep = []
+    keep += replay(ctx, [(0, pieces[0])])
+    keep += replay(ctx, [(0, pieces[1]), (0, pieces[2])])       # two segments of one trace in one call
+    keep += replay(ctx, [(0, p) for p in pieces[3:]])
+    assert_same(ctx, 0, oracle_of(tr, T0))
+
+
+def test_many_traces_one_batch():
+    lens = [1, 31, 1000, 1024, 5000, 77_777, 300_000]
+    trs = [tg.plain_trace(n, seed=7, trace=i, n_lines=64) for i, n in enumerate(lens)]
+    ctx = gpu_ctx(1_048_573, n_lines=64, max_traces=len(lens), unit=8192)
+    keep = replay(ctx, list(enumerate(trs)))
+    for i, tr in enumerate(trs):
+        assert_same(ctx, i, oracle_of(tr, 1_048_573, n_lines=64))
+
+
+def test_initial_footprint_rule1_and_phase():
+    tr = tg.plain_trace(120_000, seed=8, p_malloc=0.5)
+    kw = dict(initial_footprint=5 * tg.GIB, leak_rule=1, copy_phase=12345, copy_multiple=3)
+    ctx = gpu_ctx(1_048_573, unit=4096, **kw)
+    keep = replay(ctx, [(0, tr)])
+    o = oracle.Oracle(1_048_573, copy_threshold=3 * 1_048_573, copy_phase=12345, initial_footprint=5 * tg.GIB,
+                      leak_rule=1)
+    o.replay_events(tr.delta, tr.addr, tr.line, tr.is_python)
+    o.replay_copies(tr.csize, tr.cline, tr.cpy)
+    assert_same(ctx, 0, o)
+
+
+def test_copies_only_and_zero_deltas():
+    tr = tg.plain_trace(50_000, seed=9)
+    tr.delta[::3] = 0
+    ctx = gpu_ctx(1_048_573, unit=2048)
+    keep = replay(ctx, [(0, tg.Trace(tr.delta[:0], tr.addr[:0], tr.line[:0], tr.is_python[:0],
+                                     tr.csize, tr.cline, tr.cpy))])
+    keep += replay(ctx, [(0, tg.Trace(tr.delta, tr.addr, tr.line, tr.is_python))])
+    o = oracle.Oracle(1_048_573)
+    o.replay_copies(tr.csize, tr.cline, tr.cpy)
+    o.replay_events(tr.delta, tr.addr, tr.line, tr.is_python)
+    assert_same(ctx, 0, o)
+
+
+def test_host_entry_point_matches_device_path():
+    tr = tg.plain_trace(200_000, seed=10)
+    ctx = gpu_ctx(T0, unit=16384)
+    seg = scl.segment(0, tr.delta, tr.addr, tr.line, tr.is_python, tr.csize, tr.cline, tr.cpy)
+    scl.scl_replay_batch_host(ctx, [seg])
+    scl.scl_sync(ctx)
+    assert_same(ctx, 0, oracle_of(tr, T0))
+
+
+def test_state_export_import_resume():
+    tr = tg.plain_trace(180_000, seed=11, leak_lines=(2,))
+    a, b = tr.slice(0, 90_000, 0, 9000), tr.slice(90_000, tr.n, 9000, len(tr.csize))
+    ctx1 = gpu_ctx(1_048_573, unit=4096)
+    keep = replay(ctx1, [(0, a)])
+    blob = scl.scl_state_export(ctx1, 0)
+    ctx2 = gpu_ctx(1_048_573, unit=4096, max_traces=2)
+    with pytest.raises(scl.SclError):
+        bad = gpu_ctx(1_048_573, n_lines=128)
+        scl.scl_state_import(bad, 0, blob)
+    scl.scl_state_import(ctx2, 1, blob)
+    keep += replay(ctx2, [(1, b)])
+    assert_same(ctx2, 1, oracle_of(tr, 1_048_573), samples=False)
+
+
+def test_reset_returns_to_initial_state():
+    tr = tg.plain_trace(60_000, seed=12)
+    ctx = gpu_ctx(1_048_573, unit=2048)
+    keep = replay(ctx, [(0, tg.plain_trace(40_000, seed=99))])
+    scl.scl_trace_reset(ctx, 0)
+    keep += replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, 1_048_573))
+
+
+# ---------------------------------------------------------------- errors are reported, never faulted
+
+def test_line_out_of_range_at_sample_is_reported():
+    tr = tg.constant(5000, 4096, 16)
+    d, a, l, y = tr
+    l = l.copy()
+    l[255] = 999          # event 255 triggers the first sample at T = 1,048,573
+    ctx = gpu_ctx(1_048_573, n_lines=16, unit=1024)
+    with pytest.raises(scl.SclError) as e:
+        replay(ctx, [(0, tg.Trace(d, a, l, y))])
+    assert e.value.code == scl.SCL_ERANGE
+
+
+def test_record_space_overflow_is_reported():
+    tr = tg.plain_trace(20_000, seed=13)
+    ctx = gpu_ctx(1, shift=6, unit=4096)   # T = 1 samples every event: (n >> 6) + 64 records cannot hold them
+    with pytest.raises(scl.SclError) as e:
+        replay(ctx, [(0, tr)])
+    assert e.value.code == scl.SCL_EOVERFLOW
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    ctx = gpu_ctx(1_048_573, unit=2048)
+    assert scl.scl_selftest_wait(ctx, 1000) == scl.SCL_ETIMEOUT
+    tr = tg.plain_trace(30_000, seed=14)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, 1_048_573))
+
+
+def test_bad_descriptors_rejected_on_host():
+    ctx = gpu_ctx(T0)
+    with pytest.raises(scl.SclError) as e:
+        scl.scl_replay_batch(ctx, [scl.segment(5, None, None, None, None, n=10)])
+    assert e.value.code == scl.SCL_EINVAL
+    import torch
+    d = torch.zeros(4097, dtype=torch.int64, device="cuda")
+    with pytest.raises(scl.SclError):
+        scl.scl_replay_batch(ctx, [scl.segment(0, d[1:], d[1:], d[1:], d[1:], n=4096)])   # misaligned
