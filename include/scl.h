@@ -226,6 +226,36 @@ int scl_profile_reset(scl_ctx *ctx);
  * context's error word is cleared afterwards, so the context stays usable. */
 int scl_selftest_wait(scl_ctx *ctx, uint64_t limit, void *cuda_stream);
 
+/* Copy-volume sampler for callers that cannot allocate device memory.  The paper has
+ * no counterpart for this entry point: it is the copy sampler of scl_replay_batch
+ * (Section 3.5) packaged for code that must not call cudaMalloc -- code running
+ * inside an allocation hook (a profiler's interposition layer cannot re-enter the
+ * allocator it intercepts), processes whose device memory belongs to a caching
+ * allocator or a quota, and latency-bound callers (cudaMalloc synchronises).
+ *
+ * It allocates nothing.  Its only scratch, one 64-bit sum per 4,096 memcpy events,
+ * is a static 128 KiB device array that every GPU loading this library holds until
+ * the process exits; hence m <= 67,108,864 (SCL_EINVAL beyond).  All calls share that
+ * array: calls that overlap on the GPU (on different streams, or from several host
+ * threads) race on it and give wrong results; calls ordered on one stream are fine.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture on the device.
+ *
+ * Inputs (device pointers, length m): size, line (< n_lines; others are skipped and
+ * counted), is_python.  copy_threshold = T_c >= 1; counter_in in [0, T_c) is the
+ * running copy count carried from earlier memcpys (0 or copy_phase for a new trace).
+ * Outputs (device pointers, caller-owned, cleared by the call, asynchronous on
+ * cuda_stream): samples_out[2*n_lines] and bytes_out[2*n_lines], indexed
+ * 2*line + is_python, the same values as scl_line_stat.copy_samples / copy_bytes of
+ * a trace whose only events are these memcpys; state_out[3] = { counter after the
+ * memcpys (< T_c), memcpys skipped for a line id >= n_lines, 1 if the byte count
+ * overflowed uint64 }.  Returns SCL_EINVAL on bad arguments, SCL_ECUDA if a launch
+ * or the address lookup fails. */
+int scl_copy_volume_noalloc(const uint64_t *size, const uint32_t *line, const uint8_t *is_python, uint64_t m,
+                            uint64_t copy_threshold, uint64_t counter_in, uint32_t n_lines, uint64_t *samples_out,
+                            uint64_t *bytes_out, uint64_t *state_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

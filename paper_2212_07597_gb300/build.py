@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_objs")
 LIB = os.path.join(HERE, "libscl.so")
-SOURCES = ["scl_walk.cu", "scl_post.cu", "scl_host.cu"]
+SOURCES = ["scl_walk.cu", "scl_post.cu", "scl_host.cu", "scl_noalloc.cu"]
 HEADERS = ["scl_internal.cuh", "scl_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

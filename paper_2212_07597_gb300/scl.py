@@ -30,7 +30,7 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_replay_batch_host", "scl_sync", "scl_samples", "scl_line_stats", "scl_leak_scores",
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
-           "scl_selftest_wait")
+           "scl_selftest_wait", "scl_copy_volume_noalloc")
 
 
 class SclError(RuntimeError):
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(U64), U32, ctypes.POINTER(U32)], I),
             "scl_profile_reset": ([P], I),
             "scl_selftest_wait": ([P, U64, P], I),
+            "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -330,6 +331,16 @@ def scl_kernel_times(ctx: Context) -> dict:
 def scl_selftest_wait(ctx: Context, limit: int, stream=None) -> int:
     """Returns the status code of the bounded-wait self test (SCL_ETIMEOUT expected)."""
     return load().scl_selftest_wait(ctx.handle, limit, _stream(stream))
+
+
+def scl_copy_volume_noalloc(size, line, is_python, copy_threshold: int, counter_in: int, n_lines: int,
+                            samples_out, bytes_out, state_out, stream=None, m: int | None = None) -> int:
+    """Allocation-free copy-volume sampler (see include/scl.h); returns the status code.
+    Outputs are caller-owned device buffers of 2*n_lines, 2*n_lines and 3 64-bit words."""
+    m = len(size) if m is None else m
+    return load().scl_copy_volume_noalloc(_ptr(size), _ptr(line), _ptr(is_python), m, copy_threshold, counter_in,
+                                          n_lines, _ptr(samples_out), _ptr(bytes_out), _ptr(state_out),
+                                          _stream(stream))
 
 
 # ------------------------------------------------------------------ convenience
