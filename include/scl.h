@@ -57,6 +57,7 @@ extern "C" {
 #define SCL_ETIMEOUT (-4)   /* a bounded device wait gave up (see spin_limit) */
 #define SCL_EOVERFLOW (-5)  /* an int64 sum would overflow, or a record buffer overflowed */
 #define SCL_ERANGE (-6)     /* a line id >= n_lines was seen, or an output cap is too small */
+#define SCL_EINTERNAL (-7)  /* an internal consistency check failed (a library bug) */
 
 typedef struct scl_ctx scl_ctx;
 
@@ -202,9 +203,9 @@ int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
  * was.  The chosen values are returned by scl_tuning_get. */
 typedef struct {
     uint32_t unit_events;    /* events per work unit (multiple of 1024) */
-    uint32_t warps_per_block;/* walker warps per thread block (1..16) */
-    uint32_t ext_events;     /* cap on the lookahead a unit walks into its successor (0 = whole unit) */
-    uint32_t reserved;
+    uint32_t warps_per_block;/* sketch warps per thread block (1..12) */
+    uint32_t ext_events;     /* cap on the events a link walk reads into a unit (multiple of 128; 0 = whole unit) */
+    uint32_t final_warps;    /* exact-replay warps per thread block (1..6) */
 } scl_tuning;
 int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);

@@ -19,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_objs")
 LIB = os.path.join(HERE, "libscl.so")
-SOURCES = ["scl_walk.cu", "scl_post.cu", "scl_host.cu", "scl_noalloc.cu"]
-HEADERS = ["scl_internal.cuh", "scl_launch.h"]
+SOURCES = ["scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_host.cu", "scl_noalloc.cu"]
+HEADERS = ["scl_internal.cuh", "scl_launch.h", "scl_stage.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -45,7 +45,7 @@ struct scl_ctx {
     unsigned *queue = nullptr;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
-    DevBuf plan, ures, pub, recs, cross, recl, bits, btres, ctsum, stage;
+    DevBuf plan, usum, cand, link, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
     void *h_plan = nullptr;
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
@@ -152,6 +152,9 @@ int check_device_error(scl_ctx *c) {
     case E_TIMEOUT:
         return fail(c, SCL_ETIMEOUT, "a device wait exceeded spin_limit (site %u, %llu)", w.detail0,
                     (unsigned long long)w.detail1);
+    case E_INTERNAL:
+        return fail(c, SCL_EINTERNAL, "internal consistency check failed (site %u, %llu)", w.detail0,
+                    (unsigned long long)w.detail1);
     case E_OVERFLOW:
         return fail(c, SCL_EOVERFLOW,
                     "record space overflow or uint64 copy-count overflow (site %u, unit/tile %llu); "
@@ -202,8 +205,8 @@ void scl_replay_free(scl_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    for (DevBuf *b : {&c->plan, &c->ures, &c->pub, &c->recs, &c->cross, &c->recl, &c->bits, &c->btres, &c->ctsum,
-                      &c->stage})
+    for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->link, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
+                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
@@ -268,6 +271,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     c->tune.unit_events = cfg.unit_events ? cfg.unit_events : 131072;
     c->tune.warps_per_block = 8;
     c->tune.ext_events = 0;
+    c->tune.final_warps = 6;
     *out = c;
     return SCL_OK;
 }
@@ -281,9 +285,9 @@ int scl_tuning_get(const scl_ctx *c, scl_tuning *out) {
 int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
     if (!c || !t) return SCL_EINVAL;
     if (t->unit_events == 0 || t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 12 ||
-        (t->ext_events % TILE))
-        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024, warps_per_block 1..12, "
-                                   "ext_events multiple of %d", TILE);
+        t->final_warps < 1 || t->final_warps > 6 || (t->ext_events % STEP))
+        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024, warps_per_block 1..12, final_warps 1..6, "
+                                   "ext_events multiple of %d", STEP);
     c->tune = *t;
     return SCL_OK;
 }
@@ -336,9 +340,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     std::vector<Unit> units;
     std::vector<BTrace> bts(nbt);
     std::vector<CompactGroup> cgroups;
-    std::vector<LeakTile> ltiles;
     std::vector<CopyTile> ctiles;
-    uint64_t rec_total = 0, bit_total = 0;
+    uint64_t rec_total = 0;
     for (uint32_t bi = 0; bi < nbt; ++bi) {
         const uint32_t b = order[bi];
         BTrace &B = bts[bi];
@@ -358,16 +361,13 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 U.addr = g.ev.addr + off;
                 U.line = g.ev.line + off;
                 U.gidx0 = gidx;
-                U.bit0 = bit_total;
                 U.rec0 = rec_total;
-                const uint64_t cap = (U.len >> shift) + 64;
-                U.spec_cap = U.src_cap = (uint32_t)std::min<uint64_t>(cap, 0xffffffffu);
+                U.rec_cap = (uint32_t)std::min<uint64_t>((U.len >> shift) + 64, 0xffffffffu);
                 U.trace = B.trace;
                 U.bt = bi;
                 units.push_back(U);
                 gidx += U.len;
-                bit_total += (U.len + 31) / 32;
-                rec_total += (uint64_t)U.src_cap + U.spec_cap;
+                rec_total += U.rec_cap;
             }
             for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
                 CopyTile T;
@@ -389,16 +389,14 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         }
         for (uint32_t k = 0; k < B.nu; k += 8) cgroups.push_back({B.u0 + k, std::min<uint32_t>(8, B.nu - k)});
     }
-    for (uint32_t u = 0; u < units.size(); ++u)
-        for (uint64_t k = 0; k * LEAK_TILE < units[u].len; ++k) ltiles.push_back({u, (uint32_t)k});
     const int nunits = (int)units.size();
+    const size_t nu1 = std::max<size_t>(1, units.size());
 
-    // ---- plan blob: units | bts | groups | leak tiles | copy tiles
+    // ---- plan blob: units | bts | groups | copy tiles
     const size_t o_units = 0;
     const size_t o_bts = al256(o_units + sizeof(Unit) * units.size());
     const size_t o_grp = al256(o_bts + sizeof(BTrace) * bts.size());
-    const size_t o_lt = al256(o_grp + sizeof(CompactGroup) * cgroups.size());
-    const size_t o_ct = al256(o_lt + sizeof(LeakTile) * ltiles.size());
+    const size_t o_ct = al256(o_grp + sizeof(CompactGroup) * cgroups.size());
     const size_t blob = al256(o_ct + sizeof(CopyTile) * ctiles.size());
     if (c->plan_pending) {
         CK(cudaEventSynchronize(c->plan_done), "wait for previous plan upload");
@@ -415,17 +413,21 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     memcpy(hp + o_units, units.data(), sizeof(Unit) * units.size());
     memcpy(hp + o_bts, bts.data(), sizeof(BTrace) * bts.size());
     memcpy(hp + o_grp, cgroups.data(), sizeof(CompactGroup) * cgroups.size());
-    memcpy(hp + o_lt, ltiles.data(), sizeof(LeakTile) * ltiles.size());
     memcpy(hp + o_ct, ctiles.data(), sizeof(CopyTile) * ctiles.size());
 
     int r;
     if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;
-    if ((r = ensure(c, c->ures, sizeof(UnitRes) * std::max(1, nunits), s, "unit results"))) return r;
-    if ((r = ensure(c, c->pub, sizeof(uint32_t) * std::max(1, nunits), s, "progress counters"))) return r;
-    if ((r = ensure(c, c->recs, sizeof(Rec) * std::max<uint64_t>(1, rec_total), s, "sample records"))) return r;
-    if ((r = ensure(c, c->cross, sizeof(Cross) * std::max<uint64_t>(1, rec_total), s, "crossings"))) return r;
-    if ((r = ensure(c, c->recl, std::max<uint64_t>(1, rec_total), s, "reclaim flags"))) return r;
-    if ((r = ensure(c, c->bits, 4 * std::max<uint64_t>(1, bit_total), s, "free bitmask"))) return r;
+    if ((r = ensure(c, c->usum, sizeof(UnitSum) * nu1, s, "unit sums"))) return r;
+    if ((r = ensure(c, c->cand, sizeof(Cand) * K * nu1, s, "candidates"))) return r;
+    if ((r = ensure(c, c->link, sizeof(Link) * K * nu1, s, "links"))) return r;
+    if ((r = ensure(c, c->uwalk, sizeof(Link) * nu1, s, "walks"))) return r;
+    if ((r = ensure(c, c->utrue, sizeof(UnitTrue) * nu1, s, "true trajectories"))) return r;
+    if ((r = ensure(c, c->umode, sizeof(uint32_t) * nu1, s, "unit modes"))) return r;
+    if ((r = ensure(c, c->uexp, sizeof(int64_t) * nu1, s, "explicit counters"))) return r;
+    if ((r = ensure(c, c->uplan, sizeof(UnitPlan) * nu1, s, "unit plans"))) return r;
+    if ((r = ensure(c, c->uout, sizeof(UnitOut) * nu1, s, "unit outputs"))) return r;
+    if ((r = ensure(c, c->pref, sizeof(int64_t) * 3 * nu1, s, "window prefixes"))) return r;
+    if ((r = ensure(c, c->recs, sizeof(FRec) * std::max<uint64_t>(1, rec_total), s, "sample records"))) return r;
     if ((r = ensure(c, c->btres, sizeof(BTraceRes) * nbt, s, "batch trace results"))) return r;
     if ((r = ensure(c, c->ctsum, sizeof(uint64_t) * std::max<size_t>(1, ctiles.size()), s, "copy tile sums")))
         return r;
@@ -434,48 +436,48 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     CK(cudaMemcpyAsync(dp, hp, blob, cudaMemcpyHostToDevice, s), "plan upload");
     CK(cudaEventRecord(c->plan_done, s), "plan event");
     c->plan_pending = true;
-    CK(cudaMemsetAsync(c->ures.p, 0, sizeof(UnitRes) * nunits, s), "memset");
-    CK(cudaMemsetAsync(c->pub.p, 0, sizeof(uint32_t) * nunits, s), "memset");
-    CK(cudaMemsetAsync(c->recl.p, 0, rec_total, s), "memset");
     CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * nbt, s), "memset");
-    CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned), s), "memset");
+    CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
 
     const Unit *d_units = reinterpret_cast<const Unit *>(dp + o_units);
     const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + o_bts);
     c->last_stream = s;
 
     if (nunits) {
-        LaunchWalk w;
-        w.units = d_units;
-        w.nunits = nunits;
-        w.ures = static_cast<UnitRes *>(c->ures.p);
-        w.recs = static_cast<Rec *>(c->recs.p);
-        w.pub = static_cast<uint32_t *>(c->pub.p);
-        w.bits = static_cast<uint32_t *>(c->bits.p);
-        w.traces = c->traces;
-        w.T = cfg.threshold;
-        w.ext_cap = c->tune.ext_events;
-        w.queue = c->queue;
-        w.err = c->errw;
-        w.spin = cfg.spin_limit;
-        w.warps_per_block = (int)c->tune.warps_per_block;
+        LaunchSketch k;
+        k.units = d_units;
+        k.nunits = nunits;
+        k.bts = d_bts;
+        k.nbt = (int)nbt;
+        k.usum = static_cast<UnitSum *>(c->usum.p);
+        k.cand = static_cast<Cand *>(c->cand.p);
+        k.link = static_cast<Link *>(c->link.p);
+        k.uwalk = static_cast<Link *>(c->uwalk.p);
+        k.utrue = static_cast<UnitTrue *>(c->utrue.p);
+        k.umode = static_cast<uint32_t *>(c->umode.p);
+        k.uexp = static_cast<int64_t *>(c->uexp.p);
+        k.traces = c->traces;
+        k.T = cfg.threshold;
+        k.link_cap = c->tune.ext_events;
+        k.queue = c->queue;
+        k.err = c->errw;
+        k.spin = cfg.spin_limit;
+        k.num_sms = c->num_sms;
+        k.warps_per_block = (int)c->tune.warps_per_block;
         int bps = 0;
-        if (walk_occupancy(w.warps_per_block, &bps) || bps < 1) bps = 1;
-        const int max_blocks = bps * c->num_sms;
-        const int need = (nunits + w.warps_per_block - 1) / w.warps_per_block;
-        w.blocks = std::max(1, std::min(max_blocks, need));
+        if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
+        k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
         {
-            Prof p(c, s, "walk");
-            CK(launch_walk(w, s), "launch walk");
+            Prof p(c, s, "sketch");
+            CK(launch_sketch(k, s), "launch sketch");
         }
         {
-            Prof p(c, s, "resolve");
-            CK(launch_resolve(d_units, nunits, w.ures, w.recs, s), "launch resolve");
+            Prof p(c, s, "link");
+            CK(launch_link(k, s), "launch link");
         }
         {
-            Prof p(c, s, "fallback");
-            CK(launch_fallback(d_units, d_bts, (int)nbt, w.ures, w.recs, cfg.threshold, c->errw, cfg.spin_limit, s),
-               "launch fallback");
+            Prof p(c, s, "chain");
+            CK(launch_chain(k, s), "launch chain");
         }
     }
     LaunchPost a;
@@ -483,12 +485,13 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     a.nunits = nunits;
     a.bts = d_bts;
     a.nbt = (int)nbt;
-    a.ures = static_cast<UnitRes *>(c->ures.p);
+    a.usum = static_cast<const UnitSum *>(c->usum.p);
+    a.utrue = static_cast<const UnitTrue *>(c->utrue.p);
+    a.uplan = static_cast<UnitPlan *>(c->uplan.p);
+    a.uout = static_cast<UnitOut *>(c->uout.p);
     a.btres = static_cast<BTraceRes *>(c->btres.p);
-    a.recs = static_cast<const Rec *>(c->recs.p);
-    a.cross = static_cast<Cross *>(c->cross.p);
-    a.recl = static_cast<uint8_t *>(c->recl.p);
-    a.bits = static_cast<const uint32_t *>(c->bits.p);
+    a.recs = static_cast<FRec *>(c->recs.p);
+    a.pref = static_cast<int64_t *>(c->pref.p);
     a.traces = c->traces;
     a.lines = c->lines;
     a.log = c->log;
@@ -498,8 +501,6 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
     a.groups = reinterpret_cast<const CompactGroup *>(dp + o_grp);
     a.ngroups = (int)cgroups.size();
-    a.ltiles = reinterpret_cast<const LeakTile *>(dp + o_lt);
-    a.nltiles = (int)ltiles.size();
     a.ctiles = reinterpret_cast<const CopyTile *>(dp + o_ct);
     a.nctiles = (int)ctiles.size();
     a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
@@ -508,17 +509,32 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         Prof p(c, s, "scan");
         CK(launch_scan(a, s), "launch scan");
     }
+    if (nunits) {
+        LaunchFinal f;
+        f.units = d_units;
+        f.nunits = nunits;
+        f.utrue = a.utrue;
+        f.uplan = a.uplan;
+        f.recs = a.recs;
+        f.uout = a.uout;
+        f.T = cfg.threshold;
+        f.queue = c->queue + 2;
+        f.err = c->errw;
+        f.spin = cfg.spin_limit;
+        f.warps_per_block = (int)c->tune.final_warps;
+        int bps = 0;
+        if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
+        f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
+        Prof p(c, s, "final");
+        CK(launch_final(f, s), "launch final");
+    }
     {
         Prof p(c, s, "compact");
         CK(launch_compact(a, s), "launch compact");
     }
     {
-        Prof p(c, s, "scan2");
-        CK(launch_scan2(a, s), "launch scan2");
-    }
-    {
-        Prof p(c, s, "leak");
-        CK(launch_leak(a, s), "launch leak");
+        Prof p(c, s, "mark");
+        CK(launch_mark(a, s), "launch mark");
     }
     {
         Prof p(c, s, "epi");

@@ -1,17 +1,12 @@
 // scl_internal.cuh -- device-side layouts and warp primitives of libscl.
 //
-// Work decomposition (see the kernels for the method steps they implement):
-//   A batch of segments is cut into *units*: contiguous runs of one trace's events,
-//   at most `unit_events` long, starting at multiples of 1024 events.  One warp
-//   walks one unit through the threshold sampler of Section 3.2 (k_walk).  The
-//   first unit of a trace in the batch starts from the trace's resident counter;
-//   later units start speculatively from a zero counter and are reconciled
-//   afterwards: two runs of the reset-at-threshold counter over the same events
-//   agree from any position where both have just reset, so the walker of unit u
-//   continues into unit u+1 from its own exit state until it meets a reset that
-//   unit u+1's own walk also took (a "merge"); the true samples of u+1 are the
-//   lookahead's up to the merge and u+1's own after it.  Units whose lookahead
-//   never meets are re-walked in order by k_fallback.
+// Work decomposition.  A batch of segments is cut into *units*: contiguous runs of
+// one trace's events, at most `unit_events` long, starting at multiples of 1024
+// events.  The threshold sampler of Section 3.2 is a sequential counter; its state
+// at each unit start is found in parallel (scl_sketch.cu: candidate counters per
+// unit, links between neighbouring units, a per-trace chain), after which every
+// unit is replayed exactly and independently (scl_final.cu), and the per-trace
+// bookkeeping of Sections 3.3-3.5 follows (scl_post.cu).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -24,12 +19,12 @@ constexpr int STEP = 32 * E;       // events per walker step
 constexpr int TILE = 512;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
 constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
-constexpr int LEAK_TILE = 4096;    // events per leak-pass block
 constexpr int COPY_TILE = 4096;    // memcpy events per copy-pass block
 constexpr int SMEM_LINES_MAX = 1024;  // per-line tables kept in shared memory up to this L
 
 // error codes mirrored from scl.h
-constexpr int E_INVAL = -1, E_NOMEM = -2, E_CUDA = -3, E_TIMEOUT = -4, E_OVERFLOW = -5, E_RANGE = -6;
+constexpr int E_INVAL = -1, E_NOMEM = -2, E_CUDA = -3, E_TIMEOUT = -4, E_OVERFLOW = -5, E_RANGE = -6,
+              E_INTERNAL = -7;
 
 // ---------------------------------------------------------------- resident state
 struct DevTrace {                   // one per trace slot
@@ -64,12 +59,12 @@ struct Unit {
     const uint32_t *line;
     uint64_t len;
     uint64_t gidx0;       // trace event index of the unit's first event
-    uint64_t bit0;        // first 32-event word of the unit in the batch free bitmask
-    uint64_t rec0;        // first record slot of the unit: [src_cap | spec_cap]
-    uint32_t src_cap, spec_cap;
+    uint64_t rec0;        // first final-record slot of the unit
+    uint32_t rec_cap;     // final-record slots of the unit
     uint32_t trace;       // resident trace slot
     uint32_t bt;          // index of the trace within the batch
     uint32_t first, last; // first / last unit of its trace in this batch
+    uint32_t pad;
 };
 
 struct BTrace {           // one per trace present in the batch
@@ -86,43 +81,83 @@ struct CopyTile {
     uint32_t len, bt;
 };
 
-// sampler record written by the walker (48 bytes)
-struct Rec {
+// ---- sketch: K candidate counters per unit (one per lane)
+constexpr int K = 32;     // candidates per unit
+constexpr int R = 32;     // leading resets kept per candidate (merge detection, growth suffixes)
+
+struct UnitSum {          // lane-independent facts of a unit
+    int64_t total;                 // sum of deltas
+    int64_t totA, totApy, totSpy;  // sum of mallocs, python mallocs, python deltas
+    int64_t minQ, maxQ;            // extremes of the unit-local inclusive prefix sum
+};
+
+struct Cand {             // candidate k of unit u, started at the unit's first event
+    int64_t c;            // counter after the unit
+    int32_t last;         // position of its last reset (-1: none)
+    uint32_t n;           // resets
+    uint32_t pos[R];      // positions of its first R resets
+    int64_t suf[R + 1];   // suf[r]: largest unit-local prefix at a growth reset of index >= r
+    uint32_t arg[R + 1];  // first position attaining suf[r]
+    uint32_t pad;
+};
+
+enum : uint32_t { LINK_MERGED = 1, LINK_TRANSPARENT = 2, LINK_END = 3, LINK_OPEN = 4 };
+
+struct Link {             // the counter leaving candidate k of unit u-1, walked through unit u
+    uint32_t kind;        // LINK_*
+    uint32_t j, i;        // merged: shares reset i (< R) of candidate j of unit u
+    uint32_t n;           // its own resets, up to and including the shared one
+    int32_t last;         // its last own reset (-1: none)
+    uint32_t garg;        // first position of gmax
+    int64_t gmax;         // largest prefix at an own growth reset (INT64_MIN: none)
+    int64_t c;            // LINK_END: counter at the unit's end
+};
+
+struct UnitTrue {         // the true trajectory through a unit (k_chain)
+    int64_t entry_c;      // counter before the unit's first event
+    int64_t entry_last;   // trace index of the last reset before the unit (-1: none in this batch)
+    int64_t gmax;         // largest unit-local prefix at a growth sample (INT64_MIN: none)
+    uint32_t garg;        // its first position
+    uint32_t n;           // samples in the unit
+    int64_t exit_c;       // counter after the unit
+    int64_t exit_last;    // trace index of the last reset up to the unit's end (-1: none)
+};
+
+struct UnitPlan {         // per unit, from k_scan
+    int64_t fp_base;      // footprint before the unit
+    int64_t hwm_in;       // high-water mark entering the unit
+    int64_t wA, wApy, wSpy;   // open-window totals entering the unit, except the read-back part
+    int64_t rb_unit;      // unit whose tail (rb_from .. end) still belongs to the open window (-1: none)
+    uint32_t rb_from, enter_kind;   // enter_kind: 0 none, 1 a crossing of this batch, 2 the block tracked before the batch
+    uint64_t enter_idx;   // trace index of the entering tracked block's crossing
+    uint64_t enter_addr;
+    int64_t enter_unit;   // unit holding that crossing
+    uint64_t sample_off;  // first sample of the unit within the trace's batch samples
+};
+
+// final sample record (k_final), 56 bytes
+struct FRec {
     uint32_t rel;         // event offset within the unit
-    int32_t kind;         // +1 / -1
+    uint32_t line;
+    int8_t kind;
+    uint8_t is_hwm, recl, py;
+    uint32_t pad;
     int64_t A, F, A_py, F_py;
-    int64_t P;            // sum of the unit's deltas up to and including rel
+    int64_t P;            // unit-local prefix sum at rel
 };
 
-struct Cross {            // a high-water crossing: the tracked block (Section 3.4)
-    uint32_t rel, line;
-    uint64_t addr;
-};
-
-struct UnitRes {
-    // own walk
-    int64_t total;                              // sum of the unit's deltas
-    int64_t ex_c, ex_A, ex_F, ex_Apy, ex_Fpy;   // exit state of the own walk
-    uint32_t n_spec;                            // records of the own walk
-    // lookahead (written by the previous unit's walker) / fallback
-    uint32_t n_src;
-    // resolution
-    uint32_t src_used, spec_skip, broken, count;
-    uint32_t has_growth, n_cross;
-    int64_t max_growth_P;                       // largest unit-local prefix at a final growth record
-    int64_t tx_c, tx_A, tx_F, tx_Apy, tx_Fpy;   // true exit state
-    // scans
-    uint64_t sample_off;                        // first sample of the unit within its trace's batch samples
-    int64_t fp_base;                            // footprint before the unit's first event
-    int64_t hwm_in;                             // high-water mark entering the unit
-    int64_t enter_unit;                         // unit holding the last crossing before this one (-1: none)
+struct UnitOut {          // per unit, from k_final
+    uint32_t count;       // records written
+    uint32_t enter_hit;   // the entering tracked block was freed inside the unit
+    int64_t c, A, F, Apy, Fpy;   // state after the unit
 };
 
 struct BTraceRes {
     uint64_t n_samples;                         // samples of this trace in the batch
     int64_t fp_end, hwm_end;
-    int64_t last_cross_unit;                    // -1 if no crossing in the batch
-    uint32_t pending_hit, pad;                  // the previously tracked block was freed in this batch
+    int64_t last_cross_unit;                    // unit of the batch's last crossing (-1: none)
+    uint64_t last_cross_idx;                    // its trace index
+    uint32_t pending_hit, pad;                  // the block tracked before the batch was freed before the first crossing
     uint64_t copy_total;                        // bytes copied in the batch
 };
 

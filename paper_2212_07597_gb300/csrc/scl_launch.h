@@ -6,16 +6,35 @@
 
 namespace scl {
 
-struct LaunchWalk {
+struct LaunchSketch {
     const Unit *units;
     int nunits;
-    UnitRes *ures;
-    Rec *recs;
-    uint32_t *pub;
-    uint32_t *bits;
+    const BTrace *bts;
+    int nbt;
+    UnitSum *usum;
+    Cand *cand;
+    Link *link;
+    Link *uwalk;
+    UnitTrue *utrue;
+    uint32_t *umode;
+    int64_t *uexp;
     const DevTrace *traces;
     int64_t T;
-    uint32_t ext_cap;
+    uint32_t link_cap;
+    unsigned *queue;     // [0] sketch, [1] link, [2] final
+    ErrWord *err;
+    unsigned long long spin;
+    int blocks, warps_per_block, num_sms;
+};
+
+struct LaunchFinal {
+    const Unit *units;
+    int nunits;
+    const UnitTrue *utrue;
+    const UnitPlan *uplan;
+    FRec *recs;
+    UnitOut *uout;
+    int64_t T;
     unsigned *queue;
     ErrWord *err;
     unsigned long long spin;
@@ -26,21 +45,18 @@ struct CompactGroup {
     uint32_t u0, nu;
 };
 
-struct LeakTile {
-    uint32_t unit, k;
-};
-
 struct LaunchPost {
     const Unit *units;
     int nunits;
     const BTrace *bts;
     int nbt;
-    UnitRes *ures;
+    const UnitSum *usum;
+    const UnitTrue *utrue;
+    UnitPlan *uplan;
+    UnitOut *uout;
     BTraceRes *btres;
-    const Rec *recs;
-    Cross *cross;
-    uint8_t *recl;
-    const uint32_t *bits;
+    FRec *recs;
+    int64_t *pref;         // per unit: exclusive prefix of (totA, totApy, totSpy) within its trace
     DevTrace *traces;
     LineRow *lines;
     Sample *log;
@@ -50,27 +66,27 @@ struct LaunchPost {
     uint64_t Tc;
     const CompactGroup *groups;
     int ngroups;
-    const LeakTile *ltiles;
-    int nltiles;
     const CopyTile *ctiles;
     int nctiles;
     uint64_t *ctile_sum;   // per copy tile: sum, then (after the scan) base counter
     ErrWord *err;
 };
 
-size_t walk_smem_per_warp();
-int walk_occupancy(int warps_per_block, int *blocks_per_sm);
-cudaError_t launch_walk(const LaunchWalk &a, cudaStream_t s);
-cudaError_t launch_resolve(const Unit *units, int nunits, UnitRes *ures, const Rec *recs, cudaStream_t s);
-cudaError_t launch_fallback(const Unit *units, const BTrace *bts, int nbt, UnitRes *ures, Rec *recs, int64_t T,
-                            ErrWord *err, unsigned long long spin, cudaStream_t s);
+size_t sketch_smem_per_warp();
+size_t link_smem_per_warp();
+size_t final_smem_per_warp();
+int sketch_occupancy(int warps_per_block, int *blocks_per_sm);
+int final_occupancy(int warps_per_block, int *blocks_per_sm);
+cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_link(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s);
 
 cudaError_t launch_wait_selftest(ErrWord *err, unsigned long long limit, cudaStream_t s);
 
 cudaError_t launch_scan(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_compact(const LaunchPost &a, cudaStream_t s);
-cudaError_t launch_scan2(const LaunchPost &a, cudaStream_t s);
-cudaError_t launch_leak(const LaunchPost &a, cudaStream_t s);
+cudaError_t launch_mark(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_epi(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_copy_sum(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s);

@@ -1,14 +1,13 @@
 // scl_post.cu -- everything after the sampler walk:
 //   k_scan     per trace, over its units: sample offsets, footprint at each unit
-//              start (Section 3.3: the footprint is tracked at every event), and
-//              the high-water mark entering each unit (Section 3.4).
-//   k_compact  writes the final samples (Section 3.3 entries), attributes each to
-//              the line of its triggering event, marks high-water crossings and
-//              lists the tracked blocks (Section 3.4: "records the sampled
-//              allocation"); per-line totals go through a shared-memory table.
-//   k_scan2    the crossing tracked when each unit starts.
-//   k_leak     the pointer comparison of every free against the block tracked at
-//              that moment (Section 3.4), one bit per object.
+//              start (Section 3.3: the footprint is tracked at every event), the
+//              high-water mark and tracked block entering each unit (Section 3.4),
+//              and the sampling window open at each unit start.
+//   k_compact  writes the final samples (Section 3.3 entries) to the log and to
+//              per-line totals through a shared-memory table; crossings count one
+//              tracked malloc for their line.
+//   k_mark     a block tracked when a unit starts and freed inside it is marked
+//              reclaimed (Section 3.4's pointer comparison spans units).
 //   k_epi      closes each object's trial at the next crossing: frees += reclaimed.
 //   k_copy_*   the copy-volume sampler of Section 3.5: one sample per T_c bytes
 //              copied, counted from the running byte count.
@@ -71,44 +70,196 @@ __device__ int64_t block_excl_max(int64_t v, int64_t *sh, int64_t *total) {
 }
 
 // ---------------------------------------------------------------- k_scan
+// Per trace, over its units in order (Sections 3.3-3.4): footprint before each unit,
+// sample offsets, the high-water mark entering each unit and the tracked block then
+// (the first event attaining the largest growth-sample footprint so far, if that
+// beats the mark the trace entered the batch with), and the open sampling window
+// entering each unit (whole-unit totals plus the tail of the unit holding the last
+// reset, which k_final reads back).
+struct MaxPos {
+    int64_t v;
+    uint64_t pos;
+    int64_t unit;
+};
+
+__device__ __forceinline__ MaxPos mp_better(const MaxPos &a, const MaxPos &b) {   // a earlier than b
+    return b.v > a.v ? b : a;
+}
+
+__device__ __forceinline__ MaxPos mp_shfl_up(const MaxPos &x, int o) {
+    MaxPos y;
+    y.v = __shfl_up_sync(FULL, x.v, o);
+    y.pos = __shfl_up_sync(FULL, x.pos, o);
+    y.unit = __shfl_up_sync(FULL, x.unit, o);
+    return y;
+}
+
+__device__ __forceinline__ MaxPos mp_shfl(const MaxPos &x, int l) {
+    MaxPos y;
+    y.v = __shfl_sync(FULL, x.v, l);
+    y.pos = __shfl_sync(FULL, x.pos, l);
+    y.unit = __shfl_sync(FULL, x.unit, l);
+    return y;
+}
+
+// block-wide exclusive (max, first position) scan; *total = block result
+__device__ MaxPos block_excl_maxpos(MaxPos v, MaxPos *sh, MaxPos *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const MaxPos id = {INT64_MIN, 0, -1};
+    MaxPos x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        MaxPos t = mp_shfl_up(x, o);
+        if (lane >= o) x = mp_better(t, x);
+    }
+    MaxPos ex = mp_shfl_up(x, 1);
+    if (lane == 0) ex = id;
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        MaxPos y = lane < NT / 32 ? sh[lane] : id;
+        MaxPos yi = y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            MaxPos t = mp_shfl_up(yi, o);
+            if (lane >= o) yi = mp_better(t, yi);
+        }
+        MaxPos ye = mp_shfl_up(yi, 1);
+        if (lane == 0) ye = id;
+        if (lane < NT / 32) sh[lane] = ye;
+        if (lane == NT / 32 - 1) sh[NT / 32] = yi;
+    }
+    __syncthreads();
+    const MaxPos r = mp_better(sh[w], ex);
+    *total = sh[NT / 32];
+    __syncthreads();
+    return r;
+}
+
 __global__ void __launch_bounds__(NT) k_scan(LaunchPost a) {
     __shared__ int64_t sh[NT / 32 + 1];
+    __shared__ MaxPos shm[NT / 32 + 1];
     const int b = blockIdx.x;
     const BTrace B = a.bts[b];
-    const DevTrace &st = a.traces[B.trace];
-    int64_t ccnt = 0, cfp = st.footprint, chwm = st.hwm;
+    const DevTrace st = a.traces[B.trace];
+    const MaxPos none = {INT64_MIN, 0, -1};
+    int64_t ccnt = 0, cfp = st.footprint, cA = 0, cApy = 0, cSpy = 0;
+    MaxPos cg = none;     // best growth footprint of the batch so far
+    MaxPos clast = none;  // latest reset so far (v = trace index)
     for (uint32_t base = 0; base < B.nu; base += NT) {
         const uint32_t i = base + threadIdx.x;
         const bool valid = i < B.nu;
-        UnitRes *R = valid ? &a.ures[B.u0 + i] : nullptr;
-        int64_t tc, tt, tm;
-        const int64_t cnt = valid ? (int64_t)R->count : 0;
-        const int64_t tot = valid ? R->total : 0;
-        const int64_t ec = block_excl_sum(cnt, sh, &tc);
-        const int64_t et = block_excl_sum(tot, sh, &tt);
+        const uint32_t u = B.u0 + (valid ? i : 0);
+        const Unit &U = a.units[u];
+        const UnitTrue Tu = a.utrue[u];
+        const UnitSum S = a.usum[u];
+        int64_t t;
+        const int64_t ec = block_excl_sum(valid ? (int64_t)Tu.n : 0, sh, &t);
+        const int64_t ncnt = ccnt + t;
+        const int64_t et = block_excl_sum(valid ? S.total : 0, sh, &t);
         const int64_t fpb = cfp + et;
-        const int64_t mg = (valid && R->has_growth) ? fpb + R->max_growth_P : INT64_MIN;
-        const int64_t em = block_excl_max(mg, sh, &tm);
+        const int64_t nfp = cfp + t;
+        const int64_t eA = block_excl_sum(valid ? S.totA : 0, sh, &t);
+        const int64_t nA = cA + t;
+        const int64_t eApy = block_excl_sum(valid ? S.totApy : 0, sh, &t);
+        const int64_t nApy = cApy + t;
+        const int64_t eSpy = block_excl_sum(valid ? S.totSpy : 0, sh, &t);
+        const int64_t nSpy = cSpy + t;
+        MaxPos g = none;
+        if (valid && Tu.gmax != INT64_MIN) { g.v = fpb + Tu.gmax; g.pos = U.gidx0 + Tu.garg; g.unit = u; }
+        MaxPos gt;
+        const MaxPos eg = mp_better(cg, block_excl_maxpos(g, shm, &gt));
+        MaxPos lr = none;
+        if (valid && Tu.exit_last >= 0) { lr.v = Tu.exit_last; lr.pos = (uint64_t)Tu.exit_last; lr.unit = u; }
+        MaxPos lt;
+        const MaxPos el = mp_better(clast, block_excl_maxpos(lr, shm, &lt));
         if (valid) {
-            R->sample_off = (uint64_t)(ccnt + ec);
-            R->fp_base = fpb;
-            R->hwm_in = em > chwm ? em : chwm;
+            UnitPlan Pn;
+            Pn.fp_base = fpb;
+            Pn.sample_off = (uint64_t)(ccnt + ec);
+            Pn.hwm_in = eg.v > st.hwm ? eg.v : st.hwm;
+            if (eg.v > st.hwm) {
+                const Unit &W = a.units[eg.unit];
+                Pn.enter_kind = 1; Pn.enter_idx = eg.pos; Pn.enter_unit = eg.unit;
+                Pn.enter_addr = W.addr[eg.pos - W.gidx0];
+            } else if (st.tracked_valid) {
+                Pn.enter_kind = 2; Pn.enter_idx = st.tracked_idx; Pn.enter_unit = -1; Pn.enter_addr = st.tracked_addr;
+            } else {
+                Pn.enter_kind = 0; Pn.enter_idx = 0; Pn.enter_unit = -1; Pn.enter_addr = 0;
+            }
+            if (i == 0 || el.unit < 0) {
+                // no reset yet in this batch: the resident window is still open
+                Pn.rb_unit = -1; Pn.rb_from = 0;
+                Pn.wA = st.A + cA + eA; Pn.wApy = st.A_py + cApy + eApy; Pn.wSpy = (st.A_py - st.F_py) + cSpy + eSpy;
+            } else {
+                const Unit &W = a.units[el.unit];
+                // totals of the units strictly between the reset's unit and this one
+                const UnitSum &SW = a.usum[el.unit];
+                (void)SW;
+                Pn.rb_unit = el.unit;
+                Pn.rb_from = (uint32_t)(el.pos - W.gidx0 + 1);
+                Pn.wA = 0; Pn.wApy = 0; Pn.wSpy = 0;
+            }
+            a.uplan[u] = Pn;
         }
-        ccnt += tc;
-        cfp += tt;
-        chwm = tm > chwm ? tm : chwm;
+        ccnt = ncnt;
+        cfp = nfp;
+        cA = nA; cApy = nApy; cSpy = nSpy;
+        cg = mp_better(cg, gt);
+        clast = mp_better(clast, lt);
     }
     if (threadIdx.x == 0) {
         BTraceRes &BR = a.btres[b];
         BR.n_samples = (uint64_t)ccnt;
         BR.fp_end = cfp;
-        BR.hwm_end = chwm;
-        BR.last_cross_unit = -1;
+        BR.hwm_end = cg.v > st.hwm ? cg.v : st.hwm;
+        BR.last_cross_unit = cg.v > st.hwm ? cg.unit : -1;
+        BR.last_cross_idx = cg.v > st.hwm ? cg.pos : 0;
         BR.pending_hit = 0;
     }
 }
 
+// window totals of the units strictly between a reset's unit and the unit it opens
+// into: a second pass over the units, once every unit's read-back unit is known
+__global__ void __launch_bounds__(NT) k_scan_window(LaunchPost a) {
+    __shared__ int64_t sh[NT / 32 + 1];
+    const BTrace B = a.bts[blockIdx.x];
+    // prefix sums of the unit totals, then differences
+    int64_t cA = 0, cApy = 0, cSpy = 0;
+    for (uint32_t base = 0; base < B.nu; base += NT) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < B.nu;
+        const uint32_t u = B.u0 + (valid ? i : 0);
+        const UnitSum S = a.usum[u];
+        int64_t t;
+        const int64_t eA = block_excl_sum(valid ? S.totA : 0, sh, &t);
+        const int64_t nA = cA + t;
+        const int64_t eApy = block_excl_sum(valid ? S.totApy : 0, sh, &t);
+        const int64_t nApy = cApy + t;
+        const int64_t eSpy = block_excl_sum(valid ? S.totSpy : 0, sh, &t);
+        const int64_t nSpy = cSpy + t;
+        if (valid) {
+            a.pref[3 * (size_t)u + 0] = cA + eA;
+            a.pref[3 * (size_t)u + 1] = cApy + eApy;
+            a.pref[3 * (size_t)u + 2] = cSpy + eSpy;
+        }
+        cA = nA; cApy = nApy; cSpy = nSpy;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < B.nu; i += NT) {
+        const uint32_t u = B.u0 + i;
+        UnitPlan &Pn = a.uplan[u];
+        if (Pn.rb_unit < 0) continue;
+        const uint32_t w1 = (uint32_t)Pn.rb_unit + 1;
+        Pn.wA = a.pref[3 * (size_t)u + 0] - a.pref[3 * (size_t)w1 + 0];
+        Pn.wApy = a.pref[3 * (size_t)u + 1] - a.pref[3 * (size_t)w1 + 1];
+        Pn.wSpy = a.pref[3 * (size_t)u + 2] - a.pref[3 * (size_t)w1 + 2];
+    }
+}
+
 // ---------------------------------------------------------------- k_compact
+// Section 3.3: each final sample goes to the sample log and to its line's totals;
+// crossings count one tracked malloc for their line (Section 3.4).
 constexpr int HCOLS = 8;   // n_growth, n_shrink, A, F, A_py, F_py, net, mallocs
 
 __device__ __forceinline__ void row_add(unsigned long long *row, bool growth, int64_t A, int64_t F, int64_t Apy,
@@ -134,86 +285,54 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
     if ((uint32_t)w < G.nu) {
         const uint32_t u = G.u0 + w;
         const Unit U = a.units[u];
-        UnitRes &R = a.ures[u];
+        const UnitOut O = a.uout[u];
+        const UnitPlan &Pn = a.uplan[u];
         const DevTrace &st = a.traces[U.trace];
         Sample *log = a.log ? a.log + (uint64_t)U.trace * a.log_cap : nullptr;
-        const uint64_t log_base = st.n_samples + R.sample_off;
+        const uint64_t log_base = st.n_samples + Pn.sample_off;
         LineRow *grow = a.lines + (uint64_t)U.trace * a.n_lines;
-        const Rec *src = a.recs + U.rec0;
-        const Rec *spec = a.recs + U.rec0 + U.src_cap;
-        int64_t run = R.hwm_in;
-        uint32_t ncross = 0;
-        for (uint32_t j0 = 0; j0 < R.count; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            bool valid = j < R.count;
-            Rec r;
-            if (valid) r = j < R.src_used ? src[j] : spec[R.spec_skip + (j - R.src_used)];
-            if (valid && r.rel >= U.len) {   // never index past the unit, whatever the records hold
-                set_error(a.err, E_OVERFLOW, 8, u);
-                valid = false;
-            }
-            if (!valid) { r.rel = 0; r.kind = 0; r.A = r.F = r.A_py = r.F_py = r.P = 0; }
-            uint32_t line = valid ? U.line[r.rel] : 0;
-            const uint8_t py = valid ? U.py[r.rel] : 0;
-            bool line_ok = valid;
-            if (valid && line >= a.n_lines) {
+        const FRec *rec = a.recs + U.rec0;
+        const uint32_t cnt = O.count < U.rec_cap ? O.count : U.rec_cap;
+        for (uint32_t j = lane; j < cnt; j += 32) {
+            const FRec r = rec[j];
+            uint32_t line = r.line;
+            bool line_ok = true;
+            if (line >= a.n_lines) {
                 set_error(a.err, E_RANGE, line, U.gidx0 + r.rel);
                 line_ok = false;
                 line = 0;
             }
-            const int64_t fp = R.fp_base + r.P;
-            const int64_t g = (valid && r.kind > 0) ? fp : INT64_MIN;
-            const int64_t incl = warp_incl_max(g, lane);
-            int64_t ex = __shfl_up_sync(FULL, incl, 1);
-            if (lane == 0) ex = INT64_MIN;
-            const int64_t before = ex > run ? ex : run;
-            const bool hwm = valid && r.kind > 0 && fp > before;
-            const int64_t wm = __shfl_sync(FULL, incl, 31);
-            run = wm > run ? wm : run;
-            if (valid && log && log_base + j < a.log_cap) {
+            const int64_t fp = Pn.fp_base + r.P;
+            if (log && log_base + j < a.log_cap) {
                 Sample s;
                 s.idx = U.gidx0 + r.rel;
                 s.A = r.A; s.F = r.F; s.A_py = r.A_py; s.F_py = r.F_py;
                 s.footprint = fp;
                 s.line = line;
-                s.kind = (int8_t)r.kind;
-                s.is_python = py ? 1 : 0;
-                s.is_hwm = hwm ? 1 : 0;
+                s.kind = r.kind;
+                s.is_python = r.py;
+                s.is_hwm = r.is_hwm;
                 s.pad = 0;
                 log[log_base + j] = s;
             }
-            if (line_ok) {
-                unsigned long long *row = use_smem ? &hist[line * HCOLS] : reinterpret_cast<unsigned long long *>(&grow[line]);
-                if (use_smem) {
-                    row_add(row, r.kind > 0, r.A, r.F, r.A_py, r.F_py, hwm);
-                } else {
-                    // global row: the first 7 fields of LineRow match the histogram columns; mallocs is field 11
-                    atomicAdd(&row[r.kind > 0 ? 0 : 1], 1ull);
-                    atomicAdd(&row[2], (unsigned long long)r.A);
-                    atomicAdd(&row[3], (unsigned long long)r.F);
-                    atomicAdd(&row[4], (unsigned long long)r.A_py);
-                    atomicAdd(&row[5], (unsigned long long)r.F_py);
-                    atomicAdd(&row[6], (unsigned long long)(r.A - r.F));
-                    if (hwm) atomicAdd(&grow[line].mallocs, 1ull);
-                }
+            if (!line_ok) continue;
+            if (use_smem) {
+                row_add(&hist[line * HCOLS], r.kind > 0, r.A, r.F, r.A_py, r.F_py, r.is_hwm);
+            } else {
+                unsigned long long *row = reinterpret_cast<unsigned long long *>(&grow[line]);
+                atomicAdd(&row[r.kind > 0 ? 0 : 1], 1ull);
+                atomicAdd(&row[2], (unsigned long long)r.A);
+                atomicAdd(&row[3], (unsigned long long)r.F);
+                atomicAdd(&row[4], (unsigned long long)r.A_py);
+                atomicAdd(&row[5], (unsigned long long)r.F_py);
+                atomicAdd(&row[6], (unsigned long long)(r.A - r.F));
+                if (r.is_hwm) atomicAdd(&grow[line].mallocs, 1ull);
             }
-            const unsigned hm = __ballot_sync(FULL, hwm);
-            if (hwm) {
-                const uint32_t k = ncross + __popc(hm & ((1u << lane) - 1u));
-                Cross c;
-                c.rel = r.rel;
-                c.line = line;
-                c.addr = U.addr[r.rel];
-                a.cross[U.rec0 + k] = c;
-            }
-            ncross += __popc(hm);
         }
-        if (lane == 0) R.n_cross = ncross;
     }
     if (use_smem) {
         __syncthreads();
-        // all units of a group belong to one trace
-        const uint32_t tr = a.units[G.u0].trace;
+        const uint32_t tr = a.units[G.u0].trace;   // all units of a group belong to one trace
         LineRow *grow = a.lines + (uint64_t)tr * a.n_lines;
         for (uint32_t l = threadIdx.x; l < a.n_lines; l += NT) {
             const unsigned long long *h = &hist[l * HCOLS];
@@ -230,110 +349,34 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
     }
 }
 
-// ---------------------------------------------------------------- k_scan2
-__global__ void k_scan2(LaunchPost a) {
-    const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= a.nbt) return;
-    const BTrace B = a.bts[b];
-    int64_t last = -1;
-    for (uint32_t base = 0; base < B.nu; base += 32) {
-        const uint32_t i = base + lane;
-        const bool valid = i < B.nu;
-        const bool has = valid && a.ures[B.u0 + i].n_cross > 0;
-        const unsigned m = __ballot_sync(FULL, has);
-        const unsigned below = m & ((1u << lane) - 1u);
-        if (valid) a.ures[B.u0 + i].enter_unit = below ? (int64_t)(B.u0 + base + 31 - __clz(below)) : last;
-        if (m) last = (int64_t)(B.u0 + base + 31 - __clz(m));
+// index of the record with unit offset `rel` among a unit's sorted records (or count)
+__device__ __forceinline__ uint32_t find_record(const FRec *rec, uint32_t count, uint32_t rel) {
+    uint32_t lo = 0, hi = count;
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (rec[m].rel < rel) lo = m + 1; else hi = m;
     }
-    if (lane == 0) a.btres[b].last_cross_unit = last;
+    return lo < count && rec[lo].rel == rel ? lo : count;
 }
 
-// ---------------------------------------------------------------- k_leak
-// Section 3.4: "Every call to free then checks to see whether this object is
-// ever reclaimed ... a pointer comparison".  The object tracked at event i is
-// the crossing with the largest index below i (or, before the batch's first
-// crossing, the block the trace was already tracking).
-__global__ void __launch_bounds__(NT) k_leak(LaunchPost a) {
-    extern __shared__ __align__(16) unsigned char lsm[];
-    uint64_t *s_addr = reinterpret_cast<uint64_t *>(lsm);
-    uint32_t *s_rel = reinterpret_cast<uint32_t *>(lsm + sizeof(uint64_t) * LEAK_TILE);
-    __shared__ uint32_t s_ja, s_n;
-    __shared__ uint64_t s_in_addr, s_in_slot;
-    __shared__ int s_in_kind;   // 0 none, 1 crossing slot, 2 block tracked before the batch
-    const LeakTile LT = a.ltiles[blockIdx.x];
-    const Unit U = a.units[LT.unit];
-    const UnitRes &R = a.ures[LT.unit];
-    const uint64_t t0 = (uint64_t)LT.k * LEAK_TILE;
-    const uint64_t t1 = t0 + LEAK_TILE < U.len ? t0 + LEAK_TILE : U.len;
-    const Cross *cr = a.cross + U.rec0;
-    if (threadIdx.x == 0) {
-        const uint32_t n = R.n_cross;
-        uint32_t lo = 0, hi = n;
-        while (lo < hi) { uint32_t m = (lo + hi) >> 1; if (cr[m].rel < t0) lo = m + 1; else hi = m; }
-        const uint32_t ja = lo;
-        hi = n;
-        while (lo < hi) { uint32_t m = (lo + hi) >> 1; if (cr[m].rel < t1) lo = m + 1; else hi = m; }
-        s_ja = ja;
-        s_n = lo - ja <= (uint32_t)LEAK_TILE ? lo - ja : (uint32_t)LEAK_TILE;
-        if (ja > 0) {
-            s_in_kind = 1; s_in_slot = U.rec0 + ja - 1; s_in_addr = cr[ja - 1].addr;
-        } else if (R.enter_unit >= 0) {
-            const Unit &Ue = a.units[R.enter_unit];
-            const uint64_t slot = Ue.rec0 + a.ures[R.enter_unit].n_cross - 1;
-            s_in_kind = 1; s_in_slot = slot; s_in_addr = a.cross[slot].addr;
-        } else if (a.traces[U.trace].tracked_valid) {
-            s_in_kind = 2; s_in_slot = 0; s_in_addr = a.traces[U.trace].tracked_addr;
-        } else {
-            s_in_kind = 0; s_in_slot = 0; s_in_addr = 0;
-        }
-    }
-    __syncthreads();
-    const uint32_t ja = s_ja, nc = s_n;
-    for (uint32_t j = threadIdx.x; j < nc; j += NT) {
-        s_rel[j] = cr[ja + j].rel;
-        s_addr[j] = cr[ja + j].addr;
-    }
-    __syncthreads();
-    const int in_kind = s_in_kind;
-    if (in_kind == 0 && nc == 0) return;
-    const uint64_t in_addr = s_in_addr, in_slot = s_in_slot;
-    const uint32_t *bits = a.bits + U.bit0;
-    const bool vec = (reinterpret_cast<uintptr_t>(U.addr) & 15u) == 0;
-    constexpr int PAIRS = LEAK_TILE / (2 * NT);
-    ulonglong2 ad[PAIRS];
-    uint32_t wd[PAIRS];
-#pragma unroll
-    for (int r = 0; r < PAIRS; ++r) {
-        const uint64_t i = t0 + 2ull * (r * NT + threadIdx.x);
-        wd[r] = 0;
-        if (i < t1) {
-            wd[r] = bits[i >> 5];
-            if (vec && i + 1 < t1) ad[r] = *reinterpret_cast<const ulonglong2 *>(U.addr + i);
-            else { ad[r].x = U.addr[i]; ad[r].y = i + 1 < t1 ? U.addr[i + 1] : 0; }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < PAIRS; ++r) {
-        const uint64_t i = t0 + 2ull * (r * NT + threadIdx.x);
-        const uint32_t fb = (wd[r] >> (i & 31)) & 3u;
-        if (!fb) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (!((fb >> h) & 1u)) continue;
-            const uint64_t e = i + h;
-            const uint64_t av = h ? ad[r].y : ad[r].x;
-            // last crossing of this tile strictly before e
-            uint32_t lo = 0, hi = nc;
-            while (lo < hi) { uint32_t m = (lo + hi) >> 1; if (s_rel[m] < e) lo = m + 1; else hi = m; }
-            if (lo > 0) {
-                if (s_addr[lo - 1] == av) a.recl[U.rec0 + ja + lo - 1] = 1;
-            } else if (in_kind == 1) {
-                if (in_addr == av) a.recl[in_slot] = 1;
-            } else if (in_kind == 2) {
-                if (in_addr == av) a.btres[U.bt].pending_hit = 1;
-            }
-        }
+// ---------------------------------------------------------------- k_mark
+// Section 3.4: the block tracked when a unit starts was freed inside the unit ->
+// mark its crossing's record (or the trace's pre-batch block) reclaimed.
+__global__ void k_mark(LaunchPost a) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= a.nunits) return;
+    const UnitOut &O = a.uout[u];
+    if (!O.enter_hit) return;
+    const UnitPlan &Pn = a.uplan[u];
+    if (Pn.enter_kind == 1) {
+        const Unit &W = a.units[Pn.enter_unit];
+        const uint32_t cnt = a.uout[Pn.enter_unit].count < W.rec_cap ? a.uout[Pn.enter_unit].count : W.rec_cap;
+        FRec *rec = a.recs + W.rec0;
+        const uint32_t j = find_record(rec, cnt, (uint32_t)(Pn.enter_idx - W.gidx0));
+        if (j < cnt) rec[j].recl = 1;
+        else set_error(a.err, E_INTERNAL, 11, (unsigned long long)u);
+    } else if (Pn.enter_kind == 2) {
+        a.btres[a.units[u].bt].pending_hit = 1;
     }
 }
 
@@ -345,12 +388,15 @@ __global__ void k_epi(LaunchPost a) {
     const int lane = threadIdx.x & 31;
     if (u >= a.nunits) return;
     const Unit U = a.units[u];
-    const uint32_t n = a.ures[u].n_cross;
-    const int64_t last_u = a.btres[U.bt].last_cross_unit;
+    const uint32_t cnt = a.uout[u].count < U.rec_cap ? a.uout[u].count : U.rec_cap;
+    const BTraceRes &BR = a.btres[U.bt];
     LineRow *grow = a.lines + (uint64_t)U.trace * a.n_lines;
-    for (uint32_t j = lane; j < n; j += 32) {
-        if ((int64_t)u == last_u && j == n - 1) continue;
-        if (a.recl[U.rec0 + j]) atomicAdd(&grow[a.cross[U.rec0 + j].line].frees, 1ull);
+    const FRec *rec = a.recs + U.rec0;
+    for (uint32_t j = lane; j < cnt; j += 32) {
+        const FRec r = rec[j];
+        if (!r.is_hwm || !r.recl || r.line >= a.n_lines) continue;
+        if (BR.last_cross_unit == (int64_t)u && U.gidx0 + r.rel == BR.last_cross_idx) continue;
+        atomicAdd(&grow[r.line].frees, 1ull);
     }
 }
 
@@ -450,21 +496,26 @@ __global__ void k_state(LaunchPost a) {
     DevTrace &st = a.traces[B.trace];
     LineRow *grow = a.lines + (uint64_t)B.trace * a.n_lines;
     if (B.nu > 0) {
-        const UnitRes &RL = a.ures[B.u0 + B.nu - 1];
-        st.c = RL.tx_c; st.A = RL.tx_A; st.F = RL.tx_F; st.A_py = RL.tx_Apy; st.F_py = RL.tx_Fpy;
+        const UnitOut &O = a.uout[B.u0 + B.nu - 1];
+        st.c = O.c; st.A = O.A; st.F = O.F; st.A_py = O.Apy; st.F_py = O.Fpy;
         st.footprint = BR.fp_end;
         st.hwm = BR.hwm_end;
         if (BR.last_cross_unit >= 0) {
-            if (st.tracked_valid && (st.tracked_reclaimed || BR.pending_hit))
+            // the block tracked before the batch closes its trial at the batch's first crossing
+            if (st.tracked_valid && (st.tracked_reclaimed || BR.pending_hit) && st.tracked_line < a.n_lines)
                 atomicAdd(&grow[st.tracked_line].frees, 1ull);
-            const Unit &Ue = a.units[BR.last_cross_unit];
-            const uint64_t slot = Ue.rec0 + a.ures[BR.last_cross_unit].n_cross - 1;
-            const Cross c = a.cross[slot];
+            const Unit &W = a.units[BR.last_cross_unit];
+            const uint32_t cnt = a.uout[BR.last_cross_unit].count < W.rec_cap ? a.uout[BR.last_cross_unit].count
+                                                                              : W.rec_cap;
+            const FRec *rec = a.recs + W.rec0;
+            const uint32_t rel = (uint32_t)(BR.last_cross_idx - W.gidx0);
+            const uint32_t j = find_record(rec, cnt, rel);
             st.tracked_valid = 1;
-            st.tracked_addr = c.addr;
-            st.tracked_line = c.line;
-            st.tracked_idx = Ue.gidx0 + c.rel;
-            st.tracked_reclaimed = a.recl[slot] ? 1 : 0;
+            st.tracked_addr = W.addr[rel];
+            st.tracked_idx = BR.last_cross_idx;
+            st.tracked_line = j < cnt ? rec[j].line : 0;
+            st.tracked_reclaimed = j < cnt ? rec[j].recl : 0;
+            if (j >= cnt) set_error(a.err, E_INTERNAL, 12, b);
         } else if (st.tracked_valid && BR.pending_hit) {
             st.tracked_reclaimed = 1;
         }
@@ -522,6 +573,9 @@ __global__ void k_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines,
 cudaError_t launch_scan(const LaunchPost &a, cudaStream_t s) {
     if (!a.nbt) return cudaSuccess;
     k_scan<<<a.nbt, NT, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_window<<<a.nbt, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -534,18 +588,9 @@ cudaError_t launch_compact(const LaunchPost &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan2(const LaunchPost &a, cudaStream_t s) {
-    if (!a.nbt) return cudaSuccess;
-    k_scan2<<<(a.nbt + 7) / 8, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_leak(const LaunchPost &a, cudaStream_t s) {
-    if (!a.nltiles) return cudaSuccess;
-    const size_t smem = (sizeof(uint64_t) + sizeof(uint32_t)) * LEAK_TILE;
-    cudaError_t e = cudaFuncSetAttribute(k_leak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_leak<<<a.nltiles, NT, smem, s>>>(a);
+cudaError_t launch_mark(const LaunchPost &a, cudaStream_t s) {
+    if (!a.nunits) return cudaSuccess;
+    k_mark<<<(a.nunits + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

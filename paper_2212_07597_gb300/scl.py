@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libscl.so")
 
 SCL_OK, SCL_EINVAL, SCL_ENOMEM, SCL_ECUDA, SCL_ETIMEOUT, SCL_EOVERFLOW, SCL_ERANGE = 0, -1, -2, -3, -4, -5, -6
 _NAMES = {-1: "SCL_EINVAL", -2: "SCL_ENOMEM", -3: "SCL_ECUDA", -4: "SCL_ETIMEOUT", -5: "SCL_EOVERFLOW",
-          -6: "SCL_ERANGE"}
+          -6: "SCL_ERANGE", -7: "SCL_EINTERNAL"}
 
 # every symbol include/scl.h declares
 EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last_error", "scl_replay_batch",
@@ -64,7 +64,7 @@ class scl_segment(ctypes.Structure):
 
 class scl_tuning(ctypes.Structure):
     _fields_ = [("unit_events", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
-                ("ext_events", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("ext_events", ctypes.c_uint32), ("final_warps", ctypes.c_uint32)]
 
 
 SAMPLE_DTYPE = np.dtype([
@@ -294,8 +294,9 @@ def scl_tuning_get(ctx: Context) -> scl_tuning:
     return t
 
 
-def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int, ext_events: int = 0) -> None:
-    t = scl_tuning(unit_events, warps_per_block, ext_events, 0)
+def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int = 8, ext_events: int = 0,
+                   final_warps: int = 6) -> None:
+    t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps)
     _check(ctx, load().scl_tuning_set(ctx.handle, ctypes.byref(t)))
 
 

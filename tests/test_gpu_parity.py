@@ -31,6 +31,15 @@ def test_small_units_speculation_and_merge(unit):
     assert_same(ctx, 0, oracle_of(tr, T0))
 
 
+@pytest.mark.parametrize("cap", [128, 1024])
+def test_link_cap_forces_on_demand_walks(cap):
+    # links that stop after `cap` events leave most units to the chain's own walk
+    tr = tg.plain_trace(200_000, seed=15, leak_lines=(0,))
+    ctx = gpu_ctx(1_048_573, unit=8192, ext=cap)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, 1_048_573))
+
+
 @pytest.mark.parametrize("T,shift", [(1, 0), (1_048_573, 2), (104_857_601, 4)])
 def test_thresholds(T, shift):
     tr = tg.plain_trace(150_000 + 7, seed=2, big_count=3, big_size=4 * tg.GIB)
