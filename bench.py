@@ -37,11 +37,12 @@ sys.path.insert(0, ROOT)
 
 # algorithmic bytes each kernel must read per unit it processes
 ALG_BYTES = {
-    "walk": 9.0,          # delta (8) + is_python (1) per event
-    "leak": 8.0 + 1 / 8,  # addr (8) per event + the free bit the walk wrote
+    "sketch": 9.0,        # delta (8) + is_python (1) per event: candidate counters and unit totals
+    "final": 17.0,        # delta (8) + addr (8) + is_python (1) per event: the exact replay
     "copy_apply": 13.0,   # size (8) + line (4) + is_python (1) per memcpy event
     "copy_sum": 8.0,      # size per memcpy event
 }
+EVENT_KERNELS = ("sketch", "final")
 PATH_BYTES_PER_EVENT = 17.0        # delta + addr + is_python: every event field the path reads
 PATH_BYTES_PER_COPY = 13.0
 
@@ -124,7 +125,7 @@ class Clocks:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("scl_walk.cu", "scl_post.cu", "scl_internal.cuh"):
+    for f in ("scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_stage.cuh", "scl_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2212_07597_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -245,7 +246,7 @@ def main():
     launches = sum(c for _, c in ktimes.values())
     dom = max((k for k in ktimes if k in ALG_BYTES), key=lambda k: ktimes[k][0])
     d_ms, d_cnt = ktimes[dom]
-    per_launch_units = n if dom in ("walk", "leak") else m
+    per_launch_units = n if dom in EVENT_KERNELS else m
     alg = ALG_BYTES[dom] * per_launch_units
     achieved = alg / (d_ms / d_cnt / 1e3) / 1e9
     peaks = {}

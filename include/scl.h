@@ -203,9 +203,9 @@ int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
  * was.  The chosen values are returned by scl_tuning_get. */
 typedef struct {
     uint32_t unit_events;    /* events per work unit (multiple of 1024) */
-    uint32_t warps_per_block;/* sketch warps per thread block (1..12) */
-    uint32_t ext_events;     /* cap on the events a link walk reads into a unit (multiple of 128; 0 = whole unit) */
-    uint32_t final_warps;    /* exact-replay warps per thread block (1..6) */
+    uint32_t warps_per_block;/* sketch warps per thread block (1..16) */
+    uint32_t ext_events;     /* warm-up events each unit's candidates run before the unit (multiple of 256; 0 = 16384) */
+    uint32_t final_warps;    /* exact-replay warps per thread block (1..12) */
 } scl_tuning;
 int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);

@@ -15,7 +15,7 @@
 
 namespace scl {
 
-__global__ void __launch_bounds__(32 * 8) k_final(const Unit *__restrict__ units, int nunits,
+__global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ units, int nunits,
                                                   const UnitTrue *__restrict__ utrue,
                                                   const UnitPlan *__restrict__ uplan, FRec *recs, UnitOut *uout,
                                                   int64_t T, unsigned *queue, ErrWord *err,
@@ -177,8 +177,6 @@ cudaError_t launch_wait_selftest(ErrWord *err, unsigned long long limit, cudaStr
     k_wait_selftest<<<1, 32, 0, s>>>(err, limit);
     return cudaGetLastError();
 }
-
-size_t final_smem_per_warp() { return sizeof(Ring<true>); }
 
 cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s) {
     const size_t smem = sizeof(Ring<true>) * a.warps_per_block;

@@ -45,7 +45,7 @@ struct scl_ctx {
     unsigned *queue = nullptr;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
-    DevBuf plan, usum, cand, link, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
+    DevBuf plan, usum, cand, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
     void *h_plan = nullptr;
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
@@ -205,7 +205,7 @@ void scl_replay_free(scl_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->link, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
+    for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
                       &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
@@ -269,9 +269,9 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     }
     c->h_events.assign(NTr, 0);
     c->tune.unit_events = cfg.unit_events ? cfg.unit_events : 131072;
-    c->tune.warps_per_block = 8;
+    c->tune.warps_per_block = 16;
     c->tune.ext_events = 0;
-    c->tune.final_warps = 6;
+    c->tune.final_warps = 12;
     *out = c;
     return SCL_OK;
 }
@@ -284,10 +284,10 @@ int scl_tuning_get(const scl_ctx *c, scl_tuning *out) {
 
 int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
     if (!c || !t) return SCL_EINVAL;
-    if (t->unit_events == 0 || t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 12 ||
-        t->final_warps < 1 || t->final_warps > 6 || (t->ext_events % STEP))
-        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024, warps_per_block 1..12, final_warps 1..6, "
-                                   "ext_events multiple of %d", STEP);
+    if (t->unit_events == 0 || t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 16 ||
+        t->final_warps < 1 || t->final_warps > 12 || (t->ext_events % TILE))
+        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024, warps_per_block 1..16, final_warps 1..12, "
+                                   "ext_events multiple of %d", TILE);
     c->tune = *t;
     return SCL_OK;
 }
@@ -419,8 +419,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;
     if ((r = ensure(c, c->usum, sizeof(UnitSum) * nu1, s, "unit sums"))) return r;
     if ((r = ensure(c, c->cand, sizeof(Cand) * K * nu1, s, "candidates"))) return r;
-    if ((r = ensure(c, c->link, sizeof(Link) * K * nu1, s, "links"))) return r;
-    if ((r = ensure(c, c->uwalk, sizeof(Link) * nu1, s, "walks"))) return r;
+    if ((r = ensure(c, c->match, sizeof(uint8_t) * K * nu1, s, "candidate matches"))) return r;
+    if ((r = ensure(c, c->uwalk, sizeof(Walk) * nu1, s, "walks"))) return r;
     if ((r = ensure(c, c->utrue, sizeof(UnitTrue) * nu1, s, "true trajectories"))) return r;
     if ((r = ensure(c, c->umode, sizeof(uint32_t) * nu1, s, "unit modes"))) return r;
     if ((r = ensure(c, c->uexp, sizeof(int64_t) * nu1, s, "explicit counters"))) return r;
@@ -451,14 +451,14 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         k.nbt = (int)nbt;
         k.usum = static_cast<UnitSum *>(c->usum.p);
         k.cand = static_cast<Cand *>(c->cand.p);
-        k.link = static_cast<Link *>(c->link.p);
-        k.uwalk = static_cast<Link *>(c->uwalk.p);
+        k.match = static_cast<uint8_t *>(c->match.p);
+        k.uwalk = static_cast<Walk *>(c->uwalk.p);
         k.utrue = static_cast<UnitTrue *>(c->utrue.p);
         k.umode = static_cast<uint32_t *>(c->umode.p);
         k.uexp = static_cast<int64_t *>(c->uexp.p);
         k.traces = c->traces;
         k.T = cfg.threshold;
-        k.link_cap = c->tune.ext_events;
+        k.warmup = c->tune.ext_events ? c->tune.ext_events : 16384;
         k.queue = c->queue;
         k.err = c->errw;
         k.spin = cfg.spin_limit;
@@ -472,8 +472,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
             CK(launch_sketch(k, s), "launch sketch");
         }
         {
-            Prof p(c, s, "link");
-            CK(launch_link(k, s), "launch link");
+            Prof p(c, s, "match");
+            CK(launch_match(k, s), "launch match");
         }
         {
             Prof p(c, s, "chain");

@@ -16,7 +16,7 @@ namespace scl {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int E = 4;               // events per lane per walker step
 constexpr int STEP = 32 * E;       // events per walker step
-constexpr int TILE = 512;          // events per shared-memory stage
+constexpr int TILE = 256;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
 constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
 constexpr int COPY_TILE = 4096;    // memcpy events per copy-pass block
@@ -83,7 +83,7 @@ struct CopyTile {
 
 // ---- sketch: K candidate counters per unit (one per lane)
 constexpr int K = 32;     // candidates per unit
-constexpr int R = 32;     // leading resets kept per candidate (merge detection, growth suffixes)
+constexpr uint8_t NO_MATCH = 0xff;
 
 struct UnitSum {          // lane-independent facts of a unit
     int64_t total;                 // sum of deltas
@@ -91,26 +91,21 @@ struct UnitSum {          // lane-independent facts of a unit
     int64_t minQ, maxQ;            // extremes of the unit-local inclusive prefix sum
 };
 
-struct Cand {             // candidate k of unit u, started at the unit's first event
-    int64_t c;            // counter after the unit
-    int32_t last;         // position of its last reset (-1: none)
-    uint32_t n;           // resets
-    uint32_t pos[R];      // positions of its first R resets
-    int64_t suf[R + 1];   // suf[r]: largest unit-local prefix at a growth reset of index >= r
-    uint32_t arg[R + 1];  // first position attaining suf[r]
-    uint32_t pad;
+struct Cand {             // candidate k of unit u
+    int64_t c0;           // its counter at the unit's first event
+    int64_t c;            // its counter after the unit
+    int32_t last;         // position of its last reset in the unit (-1: none)
+    uint32_t n;           // resets in the unit
+    int64_t gmax;         // largest unit-local prefix at a growth reset (INT64_MIN: none)
+    uint32_t garg, pad;   // first position attaining it
 };
 
-enum : uint32_t { LINK_MERGED = 1, LINK_TRANSPARENT = 2, LINK_END = 3, LINK_OPEN = 4 };
-
-struct Link {             // the counter leaving candidate k of unit u-1, walked through unit u
-    uint32_t kind;        // LINK_*
-    uint32_t j, i;        // merged: shares reset i (< R) of candidate j of unit u
-    uint32_t n;           // its own resets, up to and including the shared one
-    int32_t last;         // its last own reset (-1: none)
-    uint32_t garg;        // first position of gmax
-    int64_t gmax;         // largest prefix at an own growth reset (INT64_MIN: none)
-    int64_t c;            // LINK_END: counter at the unit's end
+struct Walk {             // one unit walked by k_chain from an exact counter
+    int64_t c;            // counter after the unit
+    int32_t last;
+    uint32_t n;
+    int64_t gmax;
+    uint32_t garg, pad;
 };
 
 struct UnitTrue {         // the true trajectory through a unit (k_chain)

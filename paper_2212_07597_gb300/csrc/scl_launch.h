@@ -13,15 +13,15 @@ struct LaunchSketch {
     int nbt;
     UnitSum *usum;
     Cand *cand;
-    Link *link;
-    Link *uwalk;
+    uint8_t *match;
+    Walk *uwalk;
     UnitTrue *utrue;
     uint32_t *umode;
     int64_t *uexp;
     const DevTrace *traces;
     int64_t T;
-    uint32_t link_cap;
-    unsigned *queue;     // [0] sketch, [1] link, [2] final
+    uint32_t warmup;
+    unsigned *queue;     // [0] sketch, [2] final
     ErrWord *err;
     unsigned long long spin;
     int blocks, warps_per_block, num_sms;
@@ -72,13 +72,11 @@ struct LaunchPost {
     ErrWord *err;
 };
 
-size_t sketch_smem_per_warp();
-size_t link_smem_per_warp();
-size_t final_smem_per_warp();
+
 int sketch_occupancy(int warps_per_block, int *blocks_per_sm);
 int final_occupancy(int warps_per_block, int *blocks_per_sm);
 cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s);
-cudaError_t launch_link(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s);
 

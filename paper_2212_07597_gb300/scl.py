@@ -294,8 +294,8 @@ def scl_tuning_get(ctx: Context) -> scl_tuning:
     return t
 
 
-def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int = 8, ext_events: int = 0,
-                   final_warps: int = 6) -> None:
+def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int = 16, ext_events: int = 0,
+                   final_warps: int = 12) -> None:
     t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps)
     _check(ctx, load().scl_tuning_set(ctx.handle, ctypes.byref(t)))
 

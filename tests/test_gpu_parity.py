@@ -31,11 +31,11 @@ def test_small_units_speculation_and_merge(unit):
     assert_same(ctx, 0, oracle_of(tr, T0))
 
 
-@pytest.mark.parametrize("cap", [128, 1024])
-def test_link_cap_forces_on_demand_walks(cap):
-    # links that stop after `cap` events leave most units to the chain's own walk
+@pytest.mark.parametrize("warmup", [256, 1024])
+def test_short_warmup_forces_on_demand_walks(warmup):
+    # a warm-up too short for the candidates to collapse leaves many units to the chain's own walk
     tr = tg.plain_trace(200_000, seed=15, leak_lines=(0,))
-    ctx = gpu_ctx(1_048_573, unit=8192, ext=cap)
+    ctx = gpu_ctx(1_048_573, unit=8192, ext=warmup)
     keep = replay(ctx, [(0, tr)])
     assert_same(ctx, 0, oracle_of(tr, 1_048_573))
 
