@@ -233,6 +233,7 @@ def main():
     scl.scl_profile_enable(ctx, False)
     ktimes = scl.scl_kernel_times(ctx)
     scl.scl_sync(ctx)
+    bstats = scl.scl_batch_stats(ctx)
 
     times = [ms]
     if ws > 1:
@@ -324,6 +325,7 @@ def main():
                              "alg_bytes_per_unit": ALG_BYTES[dom]},
                 "kernels_ms_per_step": {k: v[0] / max(1, v[1]) * (v[1] / args.steps) for k, v in ktimes.items()},
                 "gpu_launches": launches,
+                "batch": bstats,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "parity": parity}
         print(json.dumps(line), flush=True)
     if ws > 1:

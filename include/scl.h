@@ -97,7 +97,7 @@ typedef struct {
     uint64_t sample_log_capacity; /* samples kept per trace for scl_samples (0: keep none) */
     uint32_t sample_budget_shift; /* record space per work unit = (events >> shift) + 64; 0 never
                                      overflows (needed when T is tiny), default 4 */
-    uint32_t unit_events;         /* events per walker work unit (multiple of 1024; 0: tuned default) */
+    uint32_t unit_events;         /* events per work unit (multiple of 1024; 0: one unit per resident warp) */
 } scl_config;
 
 /* Fill *cfg with the defaults listed above. */
@@ -202,10 +202,10 @@ int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
  * fastest; it replays into scratch trace slots and leaves the traces' state as it
  * was.  The chosen values are returned by scl_tuning_get. */
 typedef struct {
-    uint32_t unit_events;    /* events per work unit (multiple of 1024) */
+    uint32_t unit_events;    /* events per work unit (multiple of 1024; 0 = one unit per resident warp) */
     uint32_t warps_per_block;/* sketch warps per thread block (1..16) */
-    uint32_t ext_events;     /* warm-up events each unit's candidates run before the unit (multiple of 256; 0 = 16384) */
-    uint32_t final_warps;    /* exact-replay warps per thread block (1..12) */
+    uint32_t ext_events;     /* warm-up events each unit's candidates run before the unit (multiple of 256; 0 = 32768) */
+    uint32_t final_warps;    /* exact-replay warps per thread block (1..14) */
 } scl_tuning;
 int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);
@@ -220,6 +220,19 @@ int scl_profile_enable(scl_ctx *ctx, int on);
 int scl_kernel_times(scl_ctx *ctx, const char **names, double *ms, uint64_t *launches,
                      uint32_t cap, uint32_t *n_out);
 int scl_profile_reset(scl_ctx *ctx);
+
+/* How the last replay call found each unit's entering counter (for tuning): units
+ * whose true run matched no warm-up candidate are walked on demand, and stop as soon as
+ * they share a reset with one of the unit's candidates. */
+typedef struct {
+    uint64_t units;             /* work units of the last batch */
+    uint64_t walked;            /* units walked on demand by the per-trace chain */
+    uint64_t walked_merged;     /* ... of which stopped early by merging into a candidate */
+    uint64_t explicit_entries;  /* units entered with a counter no candidate carried */
+    uint64_t transparent;       /* ... of which held no sample (skipped in O(1)) */
+    uint64_t unit_events;       /* tuned events per unit (0: sized per batch) */
+} scl_batch_info;
+int scl_batch_stats(scl_ctx *ctx, scl_batch_info *out);
 
 /* Failure-detection self test (no counterpart in the paper): launches one warp that
  * waits, with the same bounded wait the walker uses, on a barrier nothing arrives at.

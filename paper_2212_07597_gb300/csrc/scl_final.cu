@@ -15,14 +15,16 @@
 
 namespace scl {
 
-__global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ units, int nunits,
+using FinalRing = Ring<true, 3, 256, 8>;
+
+__global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ units, int nunits,
                                                   const UnitTrue *__restrict__ utrue,
                                                   const UnitPlan *__restrict__ uplan, FRec *recs, UnitOut *uout,
                                                   int64_t T, unsigned *queue, ErrWord *err,
                                                   unsigned long long spin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Ring<true> &sm = reinterpret_cast<Ring<true> *>(smem_raw)[warp];
+    FinalRing &sm = reinterpret_cast<FinalRing *>(smem_raw)[warp];
     ring_init(sm, lane);
     uint32_t phase = 0;
     while (true) {
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ unit
                 enter_hit = 1;
             }
         };
-        auto add_events = [&](const StepIn &in, int after, int upto, int64_t &sA, int64_t &sApy, int64_t &sSpy) {
+        auto add_events = [&](const StepIn<E> &in, int after, int upto, int64_t &sA, int64_t &sApy, int64_t &sSpy) {
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const int pos = lane * E + k;
@@ -74,11 +76,11 @@ __global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ unit
                     const int64_t x = in.d[k];
                     const int64_t ps = x > 0 ? x : 0;
                     sA += ps;
-                    if ((in.pw >> (8 * k)) & 0xffu) { sApy += ps; sSpy += x; }
+                    if (py_of(in, k)) { sApy += ps; sSpy += x; }
                 }
             }
         };
-        auto frees_hit = [&](const StepIn &in, int after, int upto) -> bool {
+        auto frees_hit = [&](const StepIn<E> &in, int after, int upto) -> bool {
             bool h = false;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
@@ -88,12 +90,21 @@ __global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ unit
             return __any_sync(FULL, h);
         };
 
-        auto step = [&](const StepIn &in, uint32_t rel0) -> bool {
-            StepPrefix sp;
-            step_prefix(in, lane, sp);
+        auto step = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+            StepPrefix<E> sp;
+            step_prefix(in, lane, sp, sm.xq);
             if (__ballot_sync(FULL, c + sp.lmax >= T || c + sp.lmin <= -T) == 0) {
-                if (tk && frees_hit(in, -1, STEP)) hit_tracked();
-                add_events(in, -1, STEP, accA, accApy, accSpy);
+                // no sample in this step: every event joins the open window
+                bool h = false;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int64_t x = in.d[k];
+                    h |= x < 0 && in.a[k] == taddr;
+                    const int64_t ps = x > 0 ? x : 0;
+                    accA += ps;
+                    if (py_of(in, k)) { accApy += ps; accSpy += x; }
+                }
+                if (tk && __any_sync(FULL, h)) hit_tracked();
                 c += sp.tot;
                 P += sp.tot;
                 return false;
@@ -102,7 +113,7 @@ __global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ unit
             int after = -1;
             while (true) {
                 int64_t Qr;
-                const int r = first_cross(sp, lane, b, T, after, Qr);
+                const int r = first_cross(sp, sm.xq, lane, b, T, after, Qr);
                 // frees up to and including the sample's event see the block tracked so far
                 if (tk && frees_hit(in, after, r < 0 ? STEP : r)) hit_tracked();
                 if (r < 0) break;
@@ -111,10 +122,10 @@ __global__ void __launch_bounds__(32 * 12) k_final(const Unit *__restrict__ unit
                 const int64_t wA = warp_sum(sA), wApy = warp_sum(sApy), wSpy = warp_sum(sSpy);
                 const int fl = r / E, kf = r % E;
                 uint64_t av = in.a[0];
-                uint32_t pyv = in.pw & 0xffu;
+                uint32_t pyv = py_of(in, 0);
 #pragma unroll
                 for (int k = 1; k < E; ++k)
-                    if (k == kf) { av = in.a[k]; pyv = (in.pw >> (8 * k)) & 0xffu; }
+                    if (k == kf) { av = in.a[k]; pyv = py_of(in, k); }
                 av = __shfl_sync(FULL, av, fl);
                 pyv = __shfl_sync(FULL, pyv, fl);
                 const int64_t cr = b + Qr;
@@ -179,7 +190,7 @@ cudaError_t launch_wait_selftest(ErrWord *err, unsigned long long limit, cudaStr
 }
 
 cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s) {
-    const size_t smem = sizeof(Ring<true>) * a.warps_per_block;
+    const size_t smem = sizeof(FinalRing) * a.warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_final<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.utrue, a.uplan, a.recs, a.uout,
@@ -188,7 +199,7 @@ cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s) {
 }
 
 int final_occupancy(int warps_per_block, int *blocks_per_sm) {
-    const size_t smem = sizeof(Ring<true>) * warps_per_block;
+    const size_t smem = sizeof(FinalRing) * warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_final, 32 * warps_per_block, smem);

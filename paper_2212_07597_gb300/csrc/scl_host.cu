@@ -43,6 +43,8 @@ struct scl_ctx {
     ErrWord *errw = nullptr;
     void *scores = nullptr;
     unsigned *queue = nullptr;
+    unsigned long long *stats = nullptr;   // device: chain counters of the last batch
+    uint64_t last_units = 0;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
     DevBuf plan, usum, cand, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
@@ -214,6 +216,7 @@ void scl_replay_free(scl_ctx *c) {
     cudaFree(c->errw);
     cudaFree(c->scores);
     cudaFree(c->queue);
+    cudaFree(c->stats);
     if (c->h_plan) cudaFreeHost(c->h_plan);
     if (c->plan_done) cudaEventDestroy(c->plan_done);
     delete c;
@@ -249,6 +252,8 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMalloc(&c->errw, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaMalloc(&c->scores, sizeof(scl_leak_score) * L);
     if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -268,10 +273,10 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
         return r;
     }
     c->h_events.assign(NTr, 0);
-    c->tune.unit_events = cfg.unit_events ? cfg.unit_events : 131072;
+    c->tune.unit_events = cfg.unit_events;   // 0: sized per batch
     c->tune.warps_per_block = 16;
     c->tune.ext_events = 0;
-    c->tune.final_warps = 12;
+    c->tune.final_warps = 14;
     *out = c;
     return SCL_OK;
 }
@@ -284,10 +289,10 @@ int scl_tuning_get(const scl_ctx *c, scl_tuning *out) {
 
 int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
     if (!c || !t) return SCL_EINVAL;
-    if (t->unit_events == 0 || t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 16 ||
-        t->final_warps < 1 || t->final_warps > 12 || (t->ext_events % TILE))
-        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024, warps_per_block 1..16, final_warps 1..12, "
-                                   "ext_events multiple of %d", TILE);
+    if (t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 16 ||
+        t->final_warps < 1 || t->final_warps > 14 || (t->ext_events % 256))
+        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024 (0: per batch), warps_per_block 1..16, final_warps 1..14, "
+                                   "ext_events multiple of %d", 256);
     c->tune = *t;
     return SCL_OK;
 }
@@ -335,7 +340,17 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return tev[x] > tev[y]; });
 
     // ---- plan
-    const uint64_t UE = c->tune.unit_events;
+    // events per unit: as tuned, or (0) one unit per resident final-replay warp
+    uint64_t UE = c->tune.unit_events;
+    if (UE == 0) {
+        uint64_t total = 0;
+        for (uint32_t i = 0; i < nsegs; ++i) total += segs[i].ev.n;
+        const uint64_t warps = (uint64_t)c->num_sms * c->tune.final_warps;
+        UE = (total + warps - 1) / warps;
+        UE = (UE + UNIT_ALIGN - 1) / UNIT_ALIGN * UNIT_ALIGN;
+        UE = std::max<uint64_t>(UE, 32768);
+        UE = std::min<uint64_t>(UE, 1ull << 22);
+    }
     const uint32_t shift = cfg.sample_budget_shift;
     std::vector<Unit> units;
     std::vector<BTrace> bts(nbt);
@@ -438,6 +453,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     c->plan_pending = true;
     CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * nbt, s), "memset");
     CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
+    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 4, s), "memset");
+    c->last_units = units.size();
 
     const Unit *d_units = reinterpret_cast<const Unit *>(dp + o_units);
     const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + o_bts);
@@ -458,12 +475,15 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         k.uexp = static_cast<int64_t *>(c->uexp.p);
         k.traces = c->traces;
         k.T = cfg.threshold;
-        k.warmup = c->tune.ext_events ? c->tune.ext_events : 16384;
+        k.warmup = c->tune.ext_events ? c->tune.ext_events : 32768;
         k.queue = c->queue;
         k.err = c->errw;
         k.spin = cfg.spin_limit;
+        k.stats = c->stats;
         k.num_sms = c->num_sms;
-        k.warps_per_block = (int)c->tune.warps_per_block;
+        // spread the units over all SMs: fewer warps per block when units are few
+        k.warps_per_block = std::max(1, std::min((int)c->tune.warps_per_block,
+                                                 (nunits + c->num_sms - 1) / c->num_sms));
         int bps = 0;
         if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
         k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
@@ -478,6 +498,10 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         {
             Prof p(c, s, "chain");
             CK(launch_chain(k, s), "launch chain");
+        }
+        {
+            Prof p(c, s, "totals");
+            CK(launch_totals(k, s), "launch totals");
         }
     }
     LaunchPost a;
@@ -521,7 +545,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         f.queue = c->queue + 2;
         f.err = c->errw;
         f.spin = cfg.spin_limit;
-        f.warps_per_block = (int)c->tune.final_warps;
+        f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (nunits + c->num_sms - 1) / c->num_sms));
         int bps = 0;
         if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
         f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
@@ -774,6 +798,22 @@ int scl_kernel_times(scl_ctx *c, const char **names, double *ms, uint64_t *launc
         if (ms) ms[i] = c->prof_acc[i].second.first;
         if (launches) launches[i] = c->prof_acc[i].second.second;
     }
+    return SCL_OK;
+}
+
+int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
+    if (!c || !out) return SCL_EINVAL;
+    int r = sync_and_check(c);
+    if (r) return r;
+    unsigned long long v[4];
+    CK(cudaMemcpy(v, c->stats, sizeof v, cudaMemcpyDeviceToHost), "read batch stats");
+    memset(out, 0, sizeof *out);
+    out->units = c->last_units;
+    out->walked = v[0];
+    out->walked_merged = v[1];
+    out->explicit_entries = v[2];
+    out->transparent = v[3];
+    out->unit_events = c->tune.unit_events;
     return SCL_OK;
 }
 

@@ -14,7 +14,7 @@
 namespace scl {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int E = 4;               // events per lane per walker step
+constexpr int E = 8;               // events per lane per walker step
 constexpr int STEP = 32 * E;       // events per walker step
 constexpr int TILE = 256;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
@@ -91,13 +91,18 @@ struct UnitSum {          // lane-independent facts of a unit
     int64_t minQ, maxQ;            // extremes of the unit-local inclusive prefix sum
 };
 
+constexpr int RM = 32;    // leading resets kept per candidate, to let a walk merge into it
+
 struct Cand {             // candidate k of unit u
     int64_t c0;           // its counter at the unit's first event
     int64_t c;            // its counter after the unit
     int32_t last;         // position of its last reset in the unit (-1: none)
     uint32_t n;           // resets in the unit
     int64_t gmax;         // largest unit-local prefix at a growth reset (INT64_MIN: none)
-    uint32_t garg, pad;   // first position attaining it
+    uint32_t garg, targ;  // first position attaining gmax; same for tmax
+    int64_t tmax;         // largest prefix at a growth reset of index >= RM (INT64_MIN: none)
+    uint32_t pos[RM];     // positions of its first RM resets
+    int64_t gp[RM];       // their prefixes if growth resets, else INT64_MIN
 };
 
 struct Walk {             // one unit walked by k_chain from an exact counter
@@ -105,7 +110,8 @@ struct Walk {             // one unit walked by k_chain from an exact counter
     int32_t last;
     uint32_t n;
     int64_t gmax;
-    uint32_t garg, pad;
+    uint32_t garg;
+    int32_t into;         // candidate of the unit the walk merged into (-1: none)
 };
 
 struct UnitTrue {         // the true trajectory through a unit (k_chain)

@@ -24,6 +24,7 @@ struct LaunchSketch {
     unsigned *queue;     // [0] sketch, [2] final
     ErrWord *err;
     unsigned long long spin;
+    unsigned long long *stats;   // [walked, walked and merged, explicit entries, transparent]
     int blocks, warps_per_block, num_sms;
 };
 
@@ -78,6 +79,7 @@ int final_occupancy(int warps_per_block, int *blocks_per_sm);
 cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s);
 
 cudaError_t launch_wait_selftest(ErrWord *err, unsigned long long limit, cudaStream_t s);

@@ -437,34 +437,46 @@ __global__ void __launch_bounds__(NT) k_copy_scan(LaunchPost a) {
 
 constexpr int CPT = COPY_TILE / NT;   // memcpy events per thread
 
+// Section 3.5 per tile: the copy counter before the tile (from k_copy_scan) plus the
+// running byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
+// Each thread owns CPT consecutive memcpys (sizes staged through shared memory, padded
+// against bank conflicts) and carries the remainder mod T_c, so a division is needed
+// only for a memcpy of at least 8 T_c.
 __global__ void __launch_bounds__(NT) k_copy_apply(LaunchPost a) {
     extern __shared__ __align__(16) unsigned long long chist[];   // [n_lines][4]: samples py0, py1, bytes py0, py1
+    __shared__ unsigned long long ssz[COPY_TILE + COPY_TILE / CPT];
     __shared__ int64_t sh[NT / 32 + 1];
     const CopyTile C = a.ctiles[blockIdx.x];
     const BTrace &B = a.bts[C.bt];
     const bool use_smem = a.n_lines <= (uint32_t)SMEM_LINES_MAX;
-    if (use_smem) {
+    if (use_smem)
         for (uint32_t i = threadIdx.x; i < a.n_lines * 4; i += NT) chist[i] = 0;
-        __syncthreads();
-    }
-    const uint64_t base = a.ctile_sum[blockIdx.x];   // copy counter before the tile's first event
-    const uint64_t Tc = a.Tc;
+    for (uint32_t j = threadIdx.x; j < COPY_TILE; j += NT) ssz[j + j / CPT] = j < C.len ? C.size[j] : 0ull;
+    __syncthreads();
+    const unsigned long long Tc = a.Tc;
     const uint32_t j0 = threadIdx.x * CPT;
-    uint64_t loc = 0;
-    for (int k = 0; k < CPT; ++k)
-        if (j0 + k < C.len) loc += C.size[j0 + k];
+    const unsigned long long *mine = &ssz[j0 + threadIdx.x];
+    unsigned long long loc = 0;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) loc += mine[k];
     int64_t tot;
     const uint64_t ex = (uint64_t)block_excl_sum((int64_t)loc, sh, &tot);
+    const uint64_t start = a.ctile_sum[blockIdx.x] + ex;   // bytes counted before this thread's first memcpy
+    unsigned long long rem = start % Tc;
     LineRow *grow = a.lines + (uint64_t)B.trace * a.n_lines;
-    uint64_t run = base + ex;   // bytes counted before event j0
-    uint64_t qprev = run / Tc;
     for (int k = 0; k < CPT; ++k) {
         const uint32_t j = j0 + k;
         if (j >= C.len) break;
-        run += C.size[j];
-        const uint64_t qn = run / Tc;
-        const uint64_t q = qn - qprev;
-        qprev = qn;
+        const unsigned long long sz = mine[k];
+        unsigned long long q;
+        if (sz >= 8 * Tc) {
+            q = (rem + sz) / Tc;
+            rem = (rem + sz) % Tc;
+        } else {
+            rem += sz;
+            q = 0;
+            while (rem >= Tc) { rem -= Tc; ++q; }
+        }
         if (!q) continue;
         const uint32_t line = C.line[j];
         if (line >= a.n_lines) { set_error(a.err, E_RANGE, line, j); continue; }

@@ -33,9 +33,9 @@ __device__ __forceinline__ int64_t candidate_entry(int k, int64_t T) {
 
 // Advance this lane's counter c (if `active`) over one step; at each reset of an
 // active lane call on_reset(lane_k, pos, growth, Qr) on all lanes (warp-uniform).
-template <class F>
-__device__ __forceinline__ void advance(const StepPrefix &sp, int64_t qmax, int64_t qmin, int lane, int64_t T,
-                                        bool active, int64_t &c, F &&on_reset) {
+template <int EL, class F>
+__device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, int64_t qmax, int64_t qmin, int lane,
+                                        int64_t T, bool active, int64_t &c, F &&on_reset) {
     unsigned m = __ballot_sync(FULL, active && (c + qmax >= T || c + qmin <= -T));
     int64_t cnew = c + sp.tot;
     while (m) {
@@ -45,7 +45,7 @@ __device__ __forceinline__ void advance(const StepPrefix &sp, int64_t qmax, int6
         int after = -1;
         while (true) {
             int64_t Qr;
-            const int r = first_cross(sp, lane, b, T, after, Qr);
+            const int r = first_cross(sp, xq, lane, b, T, after, Qr);
             if (r < 0) break;
             on_reset(k, r, b + Qr > 0, Qr);
             b = -Qr;
@@ -60,12 +60,15 @@ __device__ __forceinline__ void advance(const StepPrefix &sp, int64_t qmax, int6
 }
 
 // ---------------------------------------------------------------- k_sketch
+using SketchRing = Ring<false, 4, 256, 8>;
+using ChainRing = Ring<false, 16, 512, 16>;   // a lone walker: 512-event steps, 8k events in flight
+
 __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
                                                     Cand *cand, const DevTrace *traces, int64_t T, uint32_t warmup,
                                                     unsigned *queue, ErrWord *err, unsigned long long spin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Ring<false> &sm = reinterpret_cast<Ring<false> *>(smem_raw)[warp];
+    SketchRing &sm = reinterpret_cast<SketchRing *>(smem_raw)[warp];
     ring_init(sm, lane);
     uint32_t phase = 0;
     while (true) {
@@ -79,45 +82,54 @@ __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ uni
         if (U.first) {
             c = traces[U.trace].c;   // the exact counter: every lane runs it, lane 0 leads
         } else {
-            // warm-up over the tail of the previous unit of the trace
+            // warm-up over the tail of the previous unit of the trace; candidates whose
+            // counters become equal run on as one (the lowest lane leads)
             c = candidate_entry(lane, T);
+            int lead = lane;
             const Unit Up = units[u - 1];
-            const uint64_t from = Up.len > warmup ? ((Up.len - warmup) / TILE) * TILE : 0;
-            auto wstep = [&](const StepIn &in, uint32_t) -> bool {
-                StepPrefix sp;
-                step_prefix(in, lane, sp);
+            const uint64_t from = Up.len > warmup ? ((Up.len - warmup) / SketchRing::kTL) * SketchRing::kTL : 0;
+            auto wstep = [&](const StepIn<8> &in, uint32_t) -> bool {
+                StepPrefix<8> sp;
+                step_prefix(in, lane, sp, sm.xq);
                 const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
-                advance(sp, qmax, qmin, lane, T, true, c, [](int, int, bool, int64_t) {});
+                const bool act = lead == lane;
+                advance(sp, sm.xq, qmax, qmin, lane, T, act, c, [](int, int, bool, int64_t) {});
+                const unsigned same = __match_any_sync(FULL, (unsigned long long)c) & __ballot_sync(FULL, act);
+                if (act) lead = __ffs(same) - 1;
                 return false;
             };
             ok = ring_walk<false>(sm, Up, from, Up.len, phase, spin, err, lane, wstep);
+            // followers take their leader's counter (leaders may have joined others later)
+#pragma unroll
+            for (int r = 0; r < 5; ++r) lead = __shfl_sync(FULL, lead, lead);
+            c = __shfl_sync(FULL, c, lead);
         }
         const int64_t c0 = c;
         const unsigned same = __match_any_sync(FULL, (unsigned long long)c);
         const int leader = __ffs(same) - 1;
         const bool active = leader == lane;
+        Cand *C = cand + (size_t)u * K + lane;
         uint32_t n = 0;
         int32_t last = -1;
-        int64_t gmax = INT64_MIN;
-        uint32_t garg = 0;
+        int64_t gmax = INT64_MIN, tmax = INT64_MIN;
+        uint32_t garg = 0, targ = 0;
         int64_t P = 0, umax = INT64_MIN, umin = INT64_MAX;
-        int64_t accA = 0, accApy = 0, accSpy = 0;
-        auto step = [&](const StepIn &in, uint32_t rel0) -> bool {
-            StepPrefix sp;
-            step_prefix(in, lane, sp);
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const int64_t x = in.d[k];
-                const int64_t ps = x > 0 ? x : 0;
-                accA += ps;
-                if ((in.pw >> (8 * k)) & 0xffu) { accApy += ps; accSpy += x; }
-            }
+        auto step = [&](const StepIn<8> &in, uint32_t rel0) -> bool {
+            StepPrefix<8> sp;
+            step_prefix(in, lane, sp, sm.xq);
             const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
-            advance(sp, qmax, qmin, lane, T, active, c, [&](int k, int r, bool growth, int64_t Qr) {
+            advance(sp, sm.xq, qmax, qmin, lane, T, active, c, [&](int k, int r, bool growth, int64_t Qr) {
                 if (lane == k) {
                     const uint32_t pos = rel0 + (uint32_t)r;
                     const int64_t Pl = P + Qr;
                     if (growth && Pl > gmax) { gmax = Pl; garg = pos; }
+                    if (n < (uint32_t)RM) {
+                        C->pos[n] = pos;
+                        C->gp[n] = growth ? Pl : INT64_MIN;
+                    } else if (growth && Pl > tmax) {
+                        tmax = Pl;
+                        targ = pos;
+                    }
                     ++n;
                     last = (int32_t)pos;
                 }
@@ -129,20 +141,27 @@ __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ uni
             return false;
         };
         if (ok) ok = ring_walk<false>(sm, U, 0, U.len, phase, spin, err, lane, step);
+        __syncwarp();
         // followers take their leader's run
-        Cand C;
-        C.c0 = c0;
-        C.c = __shfl_sync(FULL, c, leader);
-        C.last = __shfl_sync(FULL, last, leader);
-        C.n = __shfl_sync(FULL, n, leader);
-        C.gmax = __shfl_sync(FULL, gmax, leader);
-        C.garg = __shfl_sync(FULL, garg, leader);
-        C.pad = 0;
-        cand[(size_t)u * K + lane] = C;
-        const int64_t a = warp_sum(accA), ap = warp_sum(accApy), spy = warp_sum(accSpy);
+        if (active) {
+            for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
+        }
+        __syncwarp();
+        if (!active) {
+            const Cand *Lc = cand + (size_t)u * K + leader;
+            for (int r = 0; r < RM; ++r) { C->pos[r] = Lc->pos[r]; C->gp[r] = Lc->gp[r]; }
+        }
+        C->c0 = c0;
+        C->c = __shfl_sync(FULL, c, leader);
+        C->last = __shfl_sync(FULL, last, leader);
+        C->n = __shfl_sync(FULL, n, leader);
+        C->gmax = __shfl_sync(FULL, gmax, leader);
+        C->garg = __shfl_sync(FULL, garg, leader);
+        C->tmax = __shfl_sync(FULL, tmax, leader);
+        C->targ = __shfl_sync(FULL, targ, leader);
         if (lane == 0) {
-            UnitSum S;
-            S.total = P; S.totA = a; S.totApy = ap; S.totSpy = spy; S.minQ = umin; S.maxQ = umax;
+            UnitSum S;   // window totals are filled by k_totals, for the units that need them
+            S.total = P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = umin; S.maxQ = umax;
             usum[u] = S;
         }
         if (!ok) break;
@@ -164,25 +183,33 @@ __global__ void k_match(const Unit *__restrict__ units, int nunits, const Cand *
 }
 
 // ---------------------------------------------------------------- k_chain
-constexpr int CHAIN_CHUNK = 4096;   // units per shared-memory chunk
+constexpr int CHAIN_CHUNK = 4096;   // units per shared-memory chunk (with a 66 KB walker ring)
 
 constexpr uint32_t MODE_TRANSPARENT = 0x100u;   // explicit counter entering, no reset in the unit
 constexpr uint32_t MODE_WALKED = 0x200u;        // explicit counter entering, walked here (uwalk)
 
 struct ChainSmem {
     uint8_t m[CHAIN_CHUNK][K];
-    Ring<false> ring;
+    uint16_t mode[CHAIN_CHUNK];
+    ChainRing ring;
 };
 
-// Walk unit U from counter c to its end (one warp, through the bulk-copy ring).
-__device__ Walk walk_unit(Ring<false> &ring, uint32_t &phase, const Unit &U, int64_t c, int64_t T, int lane,
-                          unsigned long long spin, ErrWord *err) {
+// Walk unit U from counter c (one warp, through the bulk-copy ring) until one of its
+// resets is among the first RM resets of a candidate of the unit -- from there the run
+// is that candidate's -- or to the unit's end.  Lane j holds candidate j's positions.
+__device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const Cand *cu, int64_t c, int64_t T,
+                          int lane, unsigned long long spin, ErrWord *err) {
     Walk W;
-    W.last = -1; W.n = 0; W.gmax = INT64_MIN; W.garg = 0; W.pad = 0;
+    W.last = -1; W.n = 0; W.gmax = INT64_MIN; W.garg = 0; W.into = -1;
+    uint32_t mypos[RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) mypos[r] = cu[lane].pos[r];
     int64_t P = 0;
-    auto step = [&](const StepIn &in, uint32_t rel0) -> bool {
-        StepPrefix sp;
-        step_prefix(in, lane, sp);
+    int mj = -1;
+    uint32_t mi = 0;
+    auto step = [&](const StepIn<16> &in, uint32_t rel0) -> bool {
+        StepPrefix<16> sp;
+        step_prefix(in, lane, sp, ring.xq);
         if (__ballot_sync(FULL, c + sp.lmax >= T || c + sp.lmin <= -T) == 0) {
             c += sp.tot;
             P += sp.tot;
@@ -192,13 +219,23 @@ __device__ Walk walk_unit(Ring<false> &ring, uint32_t &phase, const Unit &U, int
         int after = -1;
         while (true) {
             int64_t Qr;
-            const int r = first_cross(sp, lane, b, T, after, Qr);
+            const int r = first_cross(sp, ring.xq, lane, b, T, after, Qr);
             if (r < 0) break;
             const uint32_t pos = rel0 + (uint32_t)r;
             const int64_t Pl = P + Qr;
             if (b + Qr > 0 && Pl > W.gmax) { W.gmax = Pl; W.garg = pos; }
             ++W.n;
             W.last = (int32_t)pos;
+            int hit = -1;
+#pragma unroll
+            for (int q = 0; q < RM; ++q)
+                if (mypos[q] == pos) hit = q;
+            const unsigned m = __ballot_sync(FULL, hit >= 0);
+            if (m) {
+                mj = __ffs(m) - 1;
+                mi = (uint32_t)__shfl_sync(FULL, hit, mj);
+                return true;
+            }
             b = -Qr;
             after = r;
         }
@@ -207,7 +244,21 @@ __device__ Walk walk_unit(Ring<false> &ring, uint32_t &phase, const Unit &U, int
         return false;
     };
     ring_walk<false>(ring, U, 0, U.len, phase, spin, err, lane, step);
-    W.c = c;
+    if (mj >= 0) {
+        // the rest of the unit follows candidate mj from its reset mi on
+        const Cand &Cj = cu[mj];
+        W.n += Cj.n - (mi + 1);
+        int64_t sg = Cj.tmax;
+        uint32_t sa = Cj.targ;
+        for (int q = RM - 1; q > (int)mi; --q)
+            if (Cj.gp[q] != INT64_MIN && Cj.gp[q] >= sg) { sg = Cj.gp[q]; sa = Cj.pos[q]; }
+        if (sg != INT64_MIN && sg > W.gmax) { W.gmax = sg; W.garg = sa; }
+        W.last = Cj.last;
+        W.c = Cj.c;
+        W.into = mj;
+    } else {
+        W.c = c;
+    }
     return W;
 }
 
@@ -217,7 +268,7 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
                                              const UnitSum *__restrict__ usum, const Cand *__restrict__ cand,
                                              const uint8_t *__restrict__ match, Walk *uwalk, UnitTrue *utrue,
                                              uint32_t *umode, int64_t *uexp, int64_t T, ErrWord *err,
-                                             unsigned long long spin) {
+                                             unsigned long long spin, unsigned long long *stats) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
     const int lane = threadIdx.x & 31;
@@ -253,8 +304,8 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
             const uint32_t u = B.u0 + c0 + i;
             if (!expl) {
                 const uint8_t j = sm.m[i][k];
-                if (j != NO_MATCH) {
-                    if (lane == 0) umode[u] = j;
+                if (j != NO_MATCH) {   // the common case: the true run carries on as candidate j
+                    if (lane == 0) sm.mode[i] = j;
                     k = j;
                     continue;
                 }
@@ -268,19 +319,28 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
             if (mm) {
                 k = __ffs(mm) - 1;
                 expl = false;
-                if (lane == 0) umode[u] = k;
+                if (lane == 0) sm.mode[i] = (uint16_t)k;
                 continue;
             }
             const UnitSum S = usum[u];
+            if (lane == 0) atomicAdd(&stats[2], 1ull);
             if (ec + S.maxQ < T && ec + S.minQ > -T) {
-                if (lane == 0) umode[u] = MODE_TRANSPARENT;
+                if (lane == 0) { sm.mode[i] = (uint16_t)MODE_TRANSPARENT; atomicAdd(&stats[3], 1ull); }
                 ec += S.total;
                 continue;
             }
-            const Walk W = walk_unit(sm.ring, phase, units[u], ec, T, lane, spin, err);
-            if (lane == 0) { uwalk[u] = W; umode[u] = MODE_WALKED; }
+            const Walk W = walk_unit(sm.ring, phase, units[u], cand + (size_t)u * K, ec, T, lane, spin, err);
+            if (lane == 0) {
+                uwalk[u] = W;
+                sm.mode[i] = (uint16_t)MODE_WALKED;
+                atomicAdd(&stats[0], 1ull);
+                if (W.into >= 0) atomicAdd(&stats[1], 1ull);
+            }
             ec = W.c;
+            if (W.into >= 0) { k = (uint32_t)W.into; expl = false; }
         }
+        __syncwarp();
+        for (uint32_t i = lane; i < cn; i += 32) umode[B.u0 + c0 + i] = sm.mode[i];
         __syncwarp();
     }
     __syncwarp();
@@ -307,9 +367,38 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
     }
 }
 
+// ---------------------------------------------------------------- k_totals
+// Sum of mallocs, python mallocs and python deltas over a unit whose true run takes no
+// sample: such units lie inside one open window, whose totals k_scan assembles from
+// them.  Units that do sample are never needed whole and keep zeros.
+__global__ void k_totals(const Unit *__restrict__ units, int nunits, const UnitTrue *__restrict__ utrue,
+                         UnitSum *usum) {
+    const int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= nunits) return;
+    if (utrue[u].n != 0) return;
+    const Unit U = units[u];
+    int64_t a = 0, ap = 0, sp = 0;
+    for (uint64_t e = lane; e < U.len; e += 32) {
+        const int64_t x = U.delta[e];
+        const int64_t ps = x > 0 ? x : 0;
+        a += ps;
+        if (U.py[e]) { ap += ps; sp += x; }
+    }
+    a = warp_sum(a);
+    ap = warp_sum(ap);
+    sp = warp_sum(sp);
+    if (lane == 0) { usum[u].totA = a; usum[u].totApy = ap; usum[u].totSpy = sp; }
+}
+
 // ---------------------------------------------------------------- launchers
+cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s) {
+    k_totals<<<(a.nunits + 7) / 8, 256, 0, s>>>(a.units, a.nunits, a.utrue, a.usum);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s) {
-    const size_t smem = sizeof(Ring<false>) * a.warps_per_block;
+    const size_t smem = sizeof(SketchRing) * a.warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.traces, a.T,
@@ -329,12 +418,12 @@ cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_chain<<<a.nbt, 32, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.match, a.uwalk, a.utrue, a.umode,
-                                    a.uexp, a.T, a.err, a.spin);
+                                    a.uexp, a.T, a.err, a.spin, a.stats);
     return cudaGetLastError();
 }
 
 int sketch_occupancy(int warps_per_block, int *blocks_per_sm) {
-    const size_t smem = sizeof(Ring<false>) * warps_per_block;
+    const size_t smem = sizeof(SketchRing) * warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sketch, 32 * warps_per_block, smem);

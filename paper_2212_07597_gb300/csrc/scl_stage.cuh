@@ -11,54 +11,86 @@
 
 namespace scl {
 
-template <bool ADDR>
+// Ring<ADDR, NS, TL, EL>: NS stages of TL events; EL events per lane per step.
+template <bool ADDR, int NS = NST, int TL = TILE, int EL = E>
 struct Ring;
 
-template <>
-struct Ring<false> {
-    int64_t d[NST][TILE];
-    uint8_t p[NST][TILE];
-    uint64_t bar[NST];
+// Every array starts on a 16-byte boundary (bulk-copy destinations and 16-byte shared
+// loads and stores need it) and the struct size is a multiple of 128, so per-warp rings
+// laid end to end stay aligned.
+template <int NS, int TL, int EL>
+struct alignas(128) Ring<false, NS, TL, EL> {   // deltas only
+    static constexpr int kNS = NS, kTL = TL, kE = EL;
+    alignas(16) int64_t d[NS][TL];
+    alignas(16) int64_t xq[32 * EL];   // every lane's step prefixes, for the crossing search
+    alignas(16) uint64_t bar[NS];
+    __device__ __forceinline__ uint8_t *p(int) { return nullptr; }
     __device__ __forceinline__ uint64_t *a(int) { return nullptr; }
 };
 
-template <>
-struct Ring<true> {
-    int64_t d[NST][TILE];
-    uint64_t addr[NST][TILE];
-    uint8_t p[NST][TILE];
-    uint64_t bar[NST];
+template <int NS, int TL, int EL>
+struct alignas(128) Ring<true, NS, TL, EL> {    // deltas, addresses, python flags
+    static constexpr int kNS = NS, kTL = TL, kE = EL;
+    alignas(16) int64_t d[NS][TL];
+    alignas(16) uint64_t addr[NS][TL];
+    alignas(16) int64_t xq[32 * EL];
+    alignas(16) uint8_t py[NS][TL];
+    alignas(16) uint64_t bar[NS];
+    __device__ __forceinline__ uint8_t *p(int s) { return py[s]; }
     __device__ __forceinline__ uint64_t *a(int s) { return addr[s]; }
 };
 
-template <bool ADDR>
-__device__ __forceinline__ void ring_init(Ring<ADDR> &sm, int lane) {
+template <class RingT>
+__device__ __forceinline__ void ring_init(RingT &sm, int lane) {
+    static_assert(sizeof(RingT) % 128 == 0, "rings laid end to end must stay aligned");
+    static_assert(RingT::kTL % 16 == 0 && (RingT::kTL * 8) % 16 == 0, "bulk copies move 16-byte multiples");
     if (lane == 0) {
-        for (int s = 0; s < NST; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < RingT::kNS; ++s) mbar_init(&sm.bar[s], 1);
         fence_mbar_init();
     }
     __syncwarp();
 }
 
-// One step's events for this lane: E consecutive events at tile offset e0.
+// One step's events for this lane: EL consecutive events at tile offset e0.
+template <int EL>
 struct StepIn {
-    int64_t d[E];
-    uint64_t a[E];
-    uint32_t pw;   // python flags, one byte per event
+    int64_t d[EL];
+    uint64_t a[EL];
+    uint64_t pw[(EL + 7) / 8];   // python flags, one byte per event
 };
+
+template <int EL>
+__device__ __forceinline__ uint32_t py_of(const StepIn<EL> &in, int k) {
+    return (uint32_t)(in.pw[k >> 3] >> (8 * (k & 7))) & 0xffu;
+}
+
+// EL consecutive 64-bit values of this lane, as 16-byte shared loads.  (Quarter-warps
+// then touch each bank group several times; that costs shared-memory cycles, which are
+// spare here, rather than issue slots, which are not.)
+template <int EL, class V>
+__device__ __forceinline__ void load_lane(const V *base, V (&out)[EL]) {
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(base);
+#pragma unroll
+    for (int q = 0; q < EL / 2; ++q) {
+        const ulonglong2 v = src[q];
+        out[2 * q] = (V)v.x;
+        out[2 * q + 1] = (V)v.y;
+    }
+}
 
 // Walk events [from, limit) of unit U (from and limit multiples of STEP, except
 // limit may be the unit length).  step(in, rel0) is called per step of STEP events
 // starting at unit offset rel0, events past `limit` read as delta 0 / flag 0 /
 // address 0; it returns true to stop early.  Returns false if a wait timed out.
-template <bool ADDR, class F>
-__device__ bool ring_walk(Ring<ADDR> &sm, const Unit &U, uint64_t from, uint64_t limit, uint32_t &phase,
+template <bool ADDR, class RingT, class F>
+__device__ bool ring_walk(RingT &sm, const Unit &U, uint64_t from, uint64_t limit, uint32_t &phase,
                           unsigned long long spin, ErrWord *err, int lane, F &&step) {
+    constexpr int NST = RingT::kNS, TILE = RingT::kTL, E = RingT::kE, STEP = 32 * E;
     if (limit <= from) return true;
     const uint64_t t_first = from / TILE;
     const uint64_t ntiles = (limit + TILE - 1) / TILE;
-    const bool bulk = ((reinterpret_cast<uintptr_t>(U.delta) | reinterpret_cast<uintptr_t>(U.py) |
-                        (ADDR ? reinterpret_cast<uintptr_t>(U.addr) : 0)) & 15u) == 0;
+    const bool bulk = ((reinterpret_cast<uintptr_t>(U.delta) |
+                        (ADDR ? reinterpret_cast<uintptr_t>(U.py) | reinterpret_cast<uintptr_t>(U.addr) : 0)) & 15u) == 0;
     uint32_t pending = 0;
 
     auto issue = [&](uint64_t t) {
@@ -68,17 +100,21 @@ __device__ bool ring_walk(Ring<ADDR> &sm, const Unit &U, uint64_t from, uint64_t
         if (bulk && cnt == (uint64_t)TILE) {
             if (lane == 0) {
                 fence_proxy_async();
-                mbar_expect_tx(&sm.bar[s], TILE * (ADDR ? 17 : 9));
+                mbar_expect_tx(&sm.bar[s], TILE * (ADDR ? 17 : 8));
                 bulk_g2s(sm.d[s], U.delta + t0, TILE * 8, &sm.bar[s]);
-                bulk_g2s(sm.p[s], U.py + t0, TILE, &sm.bar[s]);
-                if (ADDR) bulk_g2s(sm.a(s), U.addr + t0, TILE * 8, &sm.bar[s]);
+                if (ADDR) {
+                    bulk_g2s(sm.p(s), U.py + t0, TILE, &sm.bar[s]);
+                    bulk_g2s(sm.a(s), U.addr + t0, TILE * 8, &sm.bar[s]);
+                }
             }
             pending |= 1u << s;
         } else {
             for (uint32_t j = lane; j < (uint32_t)cnt; j += 32) {
                 sm.d[s][j] = U.delta[t0 + j];
-                sm.p[s][j] = U.py[t0 + j];
-                if (ADDR) sm.a(s)[j] = U.addr[t0 + j];
+                if (ADDR) {
+                    sm.p(s)[j] = U.py[t0 + j];
+                    sm.a(s)[j] = U.addr[t0 + j];
+                }
             }
         }
     };
@@ -103,27 +139,23 @@ __device__ bool ring_walk(Ring<ADDR> &sm, const Unit &U, uint64_t from, uint64_t
         bool stop = false;
         for (uint32_t b = b0; b < cnt; b += STEP) {
             const uint32_t e0 = b + lane * E;
-            StepIn in;
-            const int rot = (lane >> 2) & 1;   // alternate 16-byte halves: conflict-free shared loads
-            {
-                const longlong2 *src = reinterpret_cast<const longlong2 *>(&sm.d[s][e0]);
-                const longlong2 h0 = src[rot], h1 = src[rot ^ 1];
-                const longlong2 x0 = rot ? h1 : h0, x1 = rot ? h0 : h1;
-                in.d[0] = x0.x; in.d[1] = x0.y; in.d[2] = x1.x; in.d[3] = x1.y;
-            }
+            StepIn<E> in;
+            load_lane<E>(&sm.d[s][e0], in.d);
             if (ADDR) {
-                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(&sm.a(s)[e0]);
-                const ulonglong2 h0 = src[rot], h1 = src[rot ^ 1];
-                const ulonglong2 x0 = rot ? h1 : h0, x1 = rot ? h0 : h1;
-                in.a[0] = x0.x; in.a[1] = x0.y; in.a[2] = x1.x; in.a[3] = x1.y;
+                load_lane<E>(sm.a(s) + e0, in.a);
+#pragma unroll
+                for (int w = 0; w < (E + 7) / 8; ++w)
+                    in.pw[w] = *reinterpret_cast<const unsigned long long *>(sm.p(s) + e0 + 8 * w);
             } else {
-                in.a[0] = in.a[1] = in.a[2] = in.a[3] = 0;
+#pragma unroll
+                for (int k = 0; k < E; ++k) in.a[k] = 0;
+#pragma unroll
+                for (int w = 0; w < (E + 7) / 8; ++w) in.pw[w] = 0;
             }
-            in.pw = *reinterpret_cast<const uint32_t *>(&sm.p[s][e0]);
             if (e0 + E > cnt) {
 #pragma unroll
                 for (int k = 0; k < E; ++k)
-                    if (e0 + k >= cnt) { in.d[k] = 0; in.a[k] = 0; in.pw &= ~(0xffu << (8 * k)); }
+                    if (e0 + k >= cnt) { in.d[k] = 0; in.a[k] = 0; in.pw[k >> 3] &= ~(0xffull << (8 * (k & 7))); }
             }
             if (step(in, (uint32_t)(t0 + b))) { stop = true; break; }
         }
@@ -149,29 +181,38 @@ __device__ bool ring_walk(Ring<ADDR> &sm, const Unit &U, uint64_t from, uint64_t
 }
 
 // Block-relative prefix sums of one step: lane-local inclusive prefixes lp, the
-// exclusive prefix ex of this lane's first event, the step total, and the step's
-// prefix extremes (all lanes).
+// exclusive prefix ex of this lane's first event, the step total, and this lane's
+// extremes lmax / lmin of the step prefix over its E events (ex included).  The
+// lane's E step prefixes are also stored to xq[lane*E ..] for first_cross.
+template <int EL>
 struct StepPrefix {
-    int64_t lp[E];
-    int64_t ex, tot, qmax, qmin, lmax, lmin;
+    int64_t lp[EL];
+    int64_t ex, tot, lmax, lmin;
 };
 
-__device__ __forceinline__ void step_prefix(const StepIn &in, int lane, StepPrefix &sp) {
+template <int EL>
+__device__ __forceinline__ void step_prefix(const StepIn<EL> &in, int lane, StepPrefix<EL> &sp, int64_t *xq) {
     sp.lp[0] = in.d[0];
 #pragma unroll
-    for (int k = 1; k < E; ++k) sp.lp[k] = sp.lp[k - 1] + in.d[k];
-    sp.lmax = sp.lp[0];
-    sp.lmin = sp.lp[0];
+    for (int k = 1; k < EL; ++k) sp.lp[k] = sp.lp[k - 1] + in.d[k];
+    int64_t mx = sp.lp[0], mn = sp.lp[0];
 #pragma unroll
-    for (int k = 1; k < E; ++k) {
-        sp.lmax = sp.lp[k] > sp.lmax ? sp.lp[k] : sp.lmax;
-        sp.lmin = sp.lp[k] < sp.lmin ? sp.lp[k] : sp.lmin;
+    for (int k = 1; k < EL; ++k) {
+        mx = sp.lp[k] > mx ? sp.lp[k] : mx;
+        mn = sp.lp[k] < mn ? sp.lp[k] : mn;
     }
-    const int64_t incl = warp_incl_scan(sp.lp[E - 1], lane);
-    sp.ex = incl - sp.lp[E - 1];
+    const int64_t lt = sp.lp[EL - 1];
+    const int64_t incl = warp_incl_scan(lt, lane);
+    sp.ex = incl - lt;
     sp.tot = __shfl_sync(FULL, incl, 31);
-    sp.lmax += sp.ex;
-    sp.lmin += sp.ex;
+    sp.lmax = mx + sp.ex;
+    sp.lmin = mn + sp.ex;
+    if (xq) {
+        longlong2 *dst = reinterpret_cast<longlong2 *>(xq + lane * EL);
+#pragma unroll
+        for (int q = 0; q < EL / 2; ++q) dst[q] = make_longlong2(sp.ex + sp.lp[2 * q], sp.ex + sp.lp[2 * q + 1]);
+        __syncwarp();
+    }
 }
 
 __device__ __forceinline__ int64_t warp_min(int64_t v) {
@@ -184,25 +225,26 @@ __device__ __forceinline__ int64_t warp_min(int64_t v) {
 }
 
 // First step position after `after` where counter base b + Q crosses +-T; -1 if none.
-// Returns the position (lane*E + k) and the prefix Q there (warp-uniform).
-__device__ __forceinline__ int first_cross(const StepPrefix &sp, int lane, int64_t b, int64_t T, int after,
-                                           int64_t &Qr) {
-    int fk = E;
-#pragma unroll
-    for (int k = E - 1; k >= 0; --k) {
-        const int64_t v = b + sp.ex + sp.lp[k];
-        if (lane * E + k > after && (v >= T || v <= -T)) fk = k;
+// Returns the position (lane*EL + k) and the prefix Q there (warp-uniform).  Lanes are
+// screened with their extremes; the first candidate lane's EL prefixes (published to xq
+// by step_prefix) are then tested by EL lanes at once.
+template <int EL>
+__device__ __forceinline__ int first_cross(const StepPrefix<EL> &sp, const int64_t *xq, int lane, int64_t b,
+                                           int64_t T, int after, int64_t &Qr) {
+    const int64_t hi = T - b, lo = -T - b;   // cross iff Q >= hi or Q <= lo
+    unsigned m = __ballot_sync(FULL, lane * EL + EL - 1 > after && (sp.lmax >= hi || sp.lmin <= lo));
+    while (m) {
+        const int fl = __ffs(m) - 1;
+        m &= m - 1;
+        const int64_t q = lane < EL ? xq[fl * EL + lane] : 0;
+        const unsigned h = __ballot_sync(FULL, lane < EL && fl * EL + lane > after && (q >= hi || q <= lo));
+        if (h) {
+            const int kf = __ffs(h) - 1;
+            Qr = __shfl_sync(FULL, q, kf);
+            return fl * EL + kf;
+        }
     }
-    const unsigned m = __ballot_sync(FULL, fk < E);
-    if (!m) return -1;
-    const int fl = __ffs(m) - 1;
-    int64_t myQ = sp.ex;
-#pragma unroll
-    for (int k = 0; k < E; ++k)
-        if (k == fk) myQ = sp.ex + sp.lp[k];
-    const int kf = __shfl_sync(FULL, fk, fl);
-    Qr = __shfl_sync(FULL, myQ, fl);
-    return fl * E + kf;
+    return -1;
 }
 
 }  // namespace scl

@@ -30,7 +30,7 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_replay_batch_host", "scl_sync", "scl_samples", "scl_line_stats", "scl_leak_scores",
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
-           "scl_selftest_wait", "scl_copy_volume_noalloc")
+           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats")
 
 
 class SclError(RuntimeError):
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(U64), U32, ctypes.POINTER(U32)], I),
             "scl_profile_reset": ([P], I),
             "scl_selftest_wait": ([P, U64, P], I),
+            "scl_batch_stats": ([P, P], I),
             "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -295,7 +296,7 @@ def scl_tuning_get(ctx: Context) -> scl_tuning:
 
 
 def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int = 16, ext_events: int = 0,
-                   final_warps: int = 12) -> None:
+                   final_warps: int = 14) -> None:
     t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps)
     _check(ctx, load().scl_tuning_set(ctx.handle, ctypes.byref(t)))
 
@@ -327,6 +328,16 @@ def scl_kernel_times(ctx: Context) -> dict:
     cnt = (ctypes.c_uint64 * max(1, k))()
     _check(ctx, lib.scl_kernel_times(ctx.handle, names, ms, cnt, k, ctypes.byref(n)))
     return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(k)}
+
+
+BATCH_INFO_DTYPE = np.dtype([("units", "<u8"), ("walked", "<u8"), ("walked_merged", "<u8"),
+                             ("explicit_entries", "<u8"), ("transparent", "<u8"), ("unit_events", "<u8")])
+
+
+def scl_batch_stats(ctx: Context) -> dict:
+    out = np.zeros(1, BATCH_INFO_DTYPE)
+    _check(ctx, load().scl_batch_stats(ctx.handle, out.ctypes.data))
+    return {k: int(out[0][k]) for k in BATCH_INFO_DTYPE.names}
 
 
 def scl_selftest_wait(ctx: Context, limit: int, stream=None) -> int:

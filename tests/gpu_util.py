@@ -12,7 +12,7 @@ STATE_FIELDS = ("c", "A", "F", "A_py", "F_py", "footprint", "hwm", "tracked_vali
                 "copy_counter")
 
 
-def gpu_ctx(T, n_lines=256, max_traces=1, log_cap=1 << 20, shift=4, unit=None, warps=16, ext=0, final_warps=12, **kw):
+def gpu_ctx(T, n_lines=256, max_traces=1, log_cap=1 << 20, shift=4, unit=None, warps=16, ext=0, final_warps=14, **kw):
     ctx = scl.scl_replay_init(scl.config(threshold=T, n_lines=n_lines, max_traces=max_traces,
                                          sample_log_capacity=log_cap, sample_budget_shift=shift, **kw))
     if unit is not None or ext:

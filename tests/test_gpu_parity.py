@@ -31,7 +31,7 @@ def test_small_units_speculation_and_merge(unit):
     assert_same(ctx, 0, oracle_of(tr, T0))
 
 
-@pytest.mark.parametrize("warmup", [256, 1024])
+@pytest.mark.parametrize("warmup", [512, 1024])
 def test_short_warmup_forces_on_demand_walks(warmup):
     # a warm-up too short for the candidates to collapse leaves many units to the chain's own walk
     tr = tg.plain_trace(200_000, seed=15, leak_lines=(0,))
