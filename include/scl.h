@@ -194,13 +194,17 @@ int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_info *out);
 int scl_state_export(scl_ctx *ctx, uint32_t trace, void *buf, uint64_t cap, uint64_t *n_out);
 int scl_state_import(scl_ctx *ctx, uint32_t trace, const void *buf, uint64_t n);
 
-/* Return a trace to its initial state (F0, counters 0, empty tables and log). */
+/* Return a trace to its initial state (F0, counters 0, empty tables and log);
+ * trace = SCL_ALL_TRACES resets every trace slot in one launch. */
+#define SCL_ALL_TRACES 0xffffffffu
 int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
 
-/* Tuning of the walker: events per work unit, walker warps per block.  scl_autotune
- * times scl_replay_batch on the given segments for each candidate and keeps the
- * fastest; it replays into scratch trace slots and leaves the traces' state as it
- * was.  The chosen values are returned by scl_tuning_get. */
+/* Tuning: events per work unit, warps per block of the sketch and of the exact replay,
+ * warm-up events.  scl_autotune times scl_replay_batch on the given segments (median of
+ * three after a warm-up run) for 32 candidate settings (units 0/64k/128k/256k, replay
+ * warps 10/14, sketch warps 8/16, warm-up 16k/32k), restoring the touched traces' state
+ * before every run and at the end; it keeps the fastest setting in the context (read it
+ * back with scl_tuning_get).  It allocates one device buffer for the saved states. */
 typedef struct {
     uint32_t unit_events;    /* events per work unit (multiple of 1024; 0 = one unit per resident warp) */
     uint32_t warps_per_block;/* sketch warps per thread block (1..16) */
@@ -211,6 +215,12 @@ int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);
 int scl_autotune(scl_ctx *ctx, const scl_segment *segs, uint32_t nsegs, void *cuda_stream,
                  scl_tuning *best_out, double *best_ms_out);
+
+/* Graph replay: with on != 0, a replay call on a non-default stream whose plan (segment
+ * pointers and lengths, trace states' event counts, tuning, buffers) is byte-identical to
+ * the previous call's is relaunched as one captured CUDA graph; any other call captures a
+ * new graph.  Not used while profiling is enabled.  Default off. */
+int scl_graph_enable(scl_ctx *ctx, int on);
 
 /* Per-kernel device time of replay calls, for measurement.  When enabled, each
  * replay call records CUDA events around its kernels on its stream; scl_kernel_times
@@ -233,6 +243,46 @@ typedef struct {
     uint64_t unit_events;       /* tuned events per unit (0: sized per batch) */
 } scl_batch_info;
 int scl_batch_stats(scl_ctx *ctx, scl_batch_info *out);
+
+/* Serving loop (Section 3.1 deployment: one profiler process per profiled process, each
+ * streaming its events).  Requests are segments of many traces in HOST memory (pinned for
+ * asynchronous copies), each with an offered arrival time; requests of one trace appear
+ * in arrival order.  scl_serve admits arrived requests into a batch while its device
+ * staging slot has room (three slots sized from the budget), copies a slot's arrays to
+ * the device on a copy stream while the previous batch replays on a compute stream, and
+ * replays each batch with scl_replay_batch; a trace's results equal those of replaying
+ * its requests alone, in order.  The call returns when every request has been replayed
+ * (then scl_sync's status). */
+typedef struct {
+    uint32_t trace_id;    /* trace slot of the process (< max_traces) */
+    uint32_t reserved;
+    uint64_t arrival_ns;  /* offered arrival, ns after the call starts (used when realtime) */
+    scl_events ev;        /* HOST pointers */
+    scl_copies cp;        /* HOST pointers */
+} scl_request;
+
+typedef struct {
+    uint64_t hbm_budget;  /* device staging bytes for the three slots (0: half the free HBM, <= 8 GiB);
+                             SCL_ENOMEM if a slot cannot hold the largest request */
+    uint32_t max_batch;   /* requests per batch (0: 256) */
+    uint32_t realtime;    /* 1: admit a request only after its arrival time; 0: all arrived at start */
+} scl_serve_opts;
+
+typedef struct {
+    uint64_t done_ns;     /* when its batch's replay was seen complete, ns after the call started */
+    uint64_t latency_ns;  /* done_ns - arrival_ns (realtime), else done_ns */
+    uint32_t batch;       /* index of the batch that replayed it */
+    uint32_t reserved;
+} scl_request_result;
+
+typedef struct {
+    uint64_t requests, batches, events;
+    uint64_t staging_bytes; /* device bytes held by the staging slots */
+    double wall_s;          /* from the first arrival to the last completion */
+} scl_serve_summary;
+
+int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, const scl_serve_opts *opts,
+              scl_request_result *out, scl_serve_summary *summary);
 
 /* Failure-detection self test (no counterpart in the paper): launches one warp that
  * waits, with the same bounded wait the walker uses, on a barrier nothing arrives at.

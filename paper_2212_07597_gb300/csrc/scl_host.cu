@@ -54,6 +54,10 @@ struct scl_ctx {
     bool plan_pending = false;
     // tuning
     scl_tuning tune{};
+    // graph replay of repeated identical batches
+    bool graph_on = false;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gsig = 0;
     // profiling
     bool prof = false;
     std::vector<ProfEntry> prof_pending;
@@ -178,7 +182,164 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 }  // namespace
 
+struct EnqArgs {
+    char *dp;
+    const char *hp;
+    size_t blob, o_units, o_bts, o_grp, o_ct;
+    uint32_t nbt;
+    int nunits, ngroups, nctiles;
+};
+
+// The device work of one replay call, in stream order (captured into a graph when
+// graph replay is on).
+// plan_done marks when the pinned plan buffer may be rewritten; it is recorded here
+// only outside stream capture (an event recorded during capture is not usable after it).
+int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan) {
+    const scl_config &cfg = c->cfg;
+    char *dp = q.dp;
+    CK(cudaMemcpyAsync(dp, q.hp, q.blob, cudaMemcpyHostToDevice, s), "plan upload");
+    if (record_plan) {
+        CK(cudaEventRecord(c->plan_done, s), "plan event");
+        c->plan_pending = true;
+    }
+    CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * q.nbt, s), "memset");
+    CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
+    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 4, s), "memset");
+
+    const Unit *d_units = reinterpret_cast<const Unit *>(dp + q.o_units);
+    const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + q.o_bts);
+
+    const int nunits = q.nunits;
+    const uint32_t nbt = q.nbt;
+    if (nunits) {
+        LaunchSketch k;
+        k.units = d_units;
+        k.nunits = nunits;
+        k.bts = d_bts;
+        k.nbt = (int)nbt;
+        k.usum = static_cast<UnitSum *>(c->usum.p);
+        k.cand = static_cast<Cand *>(c->cand.p);
+        k.match = static_cast<uint8_t *>(c->match.p);
+        k.uwalk = static_cast<Walk *>(c->uwalk.p);
+        k.utrue = static_cast<UnitTrue *>(c->utrue.p);
+        k.umode = static_cast<uint32_t *>(c->umode.p);
+        k.uexp = static_cast<int64_t *>(c->uexp.p);
+        k.traces = c->traces;
+        k.T = cfg.threshold;
+        k.warmup = c->tune.ext_events ? c->tune.ext_events : 32768;
+        k.queue = c->queue;
+        k.err = c->errw;
+        k.spin = cfg.spin_limit;
+        k.stats = c->stats;
+        k.num_sms = c->num_sms;
+        // spread the units over all SMs: fewer warps per block when units are few
+        k.warps_per_block = std::max(1, std::min((int)c->tune.warps_per_block,
+                                                 (nunits + c->num_sms - 1) / c->num_sms));
+        int bps = 0;
+        if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
+        k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
+        {
+            Prof p(c, s, "sketch");
+            CK(launch_sketch(k, s), "launch sketch");
+        }
+        {
+            Prof p(c, s, "match");
+            CK(launch_match(k, s), "launch match");
+        }
+        {
+            Prof p(c, s, "chain");
+            CK(launch_chain(k, s), "launch chain");
+        }
+        {
+            Prof p(c, s, "totals");
+            CK(launch_totals(k, s), "launch totals");
+        }
+    }
+    LaunchPost a;
+    a.units = d_units;
+    a.nunits = nunits;
+    a.bts = d_bts;
+    a.nbt = (int)nbt;
+    a.usum = static_cast<const UnitSum *>(c->usum.p);
+    a.utrue = static_cast<const UnitTrue *>(c->utrue.p);
+    a.uplan = static_cast<UnitPlan *>(c->uplan.p);
+    a.uout = static_cast<UnitOut *>(c->uout.p);
+    a.btres = static_cast<BTraceRes *>(c->btres.p);
+    a.recs = static_cast<FRec *>(c->recs.p);
+    a.pref = static_cast<int64_t *>(c->pref.p);
+    a.traces = c->traces;
+    a.lines = c->lines;
+    a.log = c->log;
+    a.log_cap = cfg.sample_log_capacity;
+    a.n_lines = cfg.n_lines;
+    a.T = cfg.threshold;
+    a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
+    a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
+    a.ngroups = q.ngroups;
+    a.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
+    a.nctiles = q.nctiles;
+    a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
+    a.err = c->errw;
+    {
+        Prof p(c, s, "scan");
+        CK(launch_scan(a, s), "launch scan");
+    }
+    if (nunits) {
+        LaunchFinal f;
+        f.units = d_units;
+        f.nunits = nunits;
+        f.utrue = a.utrue;
+        f.uplan = a.uplan;
+        f.recs = a.recs;
+        f.uout = a.uout;
+        f.T = cfg.threshold;
+        f.queue = c->queue + 2;
+        f.err = c->errw;
+        f.spin = cfg.spin_limit;
+        f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (nunits + c->num_sms - 1) / c->num_sms));
+        int bps = 0;
+        if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
+        f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
+        Prof p(c, s, "final");
+        CK(launch_final(f, s), "launch final");
+    }
+    {
+        Prof p(c, s, "compact");
+        CK(launch_compact(a, s), "launch compact");
+    }
+    {
+        Prof p(c, s, "mark");
+        CK(launch_mark(a, s), "launch mark");
+    }
+    {
+        Prof p(c, s, "epi");
+        CK(launch_epi(a, s), "launch epi");
+    }
+    {
+        Prof p(c, s, "copy_sum");
+        CK(launch_copy_sum(a, s), "launch copy sum");
+    }
+    {
+        Prof p(c, s, "copy_scan");
+        CK(launch_copy_scan(a, s), "launch copy scan");
+    }
+    {
+        Prof p(c, s, "copy_apply");
+        CK(launch_copy_apply(a, s), "launch copy apply");
+    }
+    {
+        Prof p(c, s, "state");
+        CK(launch_state(a, s), "launch state");
+    }
+    return SCL_OK;
+}
+
 // ============================================================================ C ABI
+
+uint32_t scl_ctx_max_traces(const scl_ctx *c) { return c->cfg.max_traces; }
+int scl_ctx_device(const scl_ctx *c) { return c->device; }
+int scl_ctx_fail(scl_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
+void scl_ctx_forget_stream(scl_ctx *c) { c->last_stream = nullptr; }
 
 extern "C" {
 
@@ -219,6 +380,7 @@ void scl_replay_free(scl_ctx *c) {
     cudaFree(c->stats);
     if (c->h_plan) cudaFreeHost(c->h_plan);
     if (c->plan_done) cudaEventDestroy(c->plan_done);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     delete c;
 }
 
@@ -262,10 +424,9 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
         scl_replay_free(c);
         return r;
     }
-    for (uint32_t t = 0; t < cfg.max_traces; ++t) {
-        e = launch_reset(c->traces, c->lines, t, cfg.n_lines, cfg.initial_footprint, cfg.copy_phase, nullptr);
-        if (e != cudaSuccess) break;
-    }
+    if (e == cudaSuccess)
+        e = launch_reset(c->traces, c->lines, 0, cfg.max_traces, cfg.n_lines, cfg.initial_footprint, cfg.copy_phase,
+                         nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         int r = cuda_fail(c, e, "context initialisation");
@@ -448,137 +609,42 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         return r;
 
     char *dp = static_cast<char *>(c->plan.p);
-    CK(cudaMemcpyAsync(dp, hp, blob, cudaMemcpyHostToDevice, s), "plan upload");
-    CK(cudaEventRecord(c->plan_done, s), "plan event");
-    c->plan_pending = true;
-    CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * nbt, s), "memset");
-    CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
-    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 4, s), "memset");
     c->last_units = units.size();
-
-    const Unit *d_units = reinterpret_cast<const Unit *>(dp + o_units);
-    const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + o_bts);
     c->last_stream = s;
-
-    if (nunits) {
-        LaunchSketch k;
-        k.units = d_units;
-        k.nunits = nunits;
-        k.bts = d_bts;
-        k.nbt = (int)nbt;
-        k.usum = static_cast<UnitSum *>(c->usum.p);
-        k.cand = static_cast<Cand *>(c->cand.p);
-        k.match = static_cast<uint8_t *>(c->match.p);
-        k.uwalk = static_cast<Walk *>(c->uwalk.p);
-        k.utrue = static_cast<UnitTrue *>(c->utrue.p);
-        k.umode = static_cast<uint32_t *>(c->umode.p);
-        k.uexp = static_cast<int64_t *>(c->uexp.p);
-        k.traces = c->traces;
-        k.T = cfg.threshold;
-        k.warmup = c->tune.ext_events ? c->tune.ext_events : 32768;
-        k.queue = c->queue;
-        k.err = c->errw;
-        k.spin = cfg.spin_limit;
-        k.stats = c->stats;
-        k.num_sms = c->num_sms;
-        // spread the units over all SMs: fewer warps per block when units are few
-        k.warps_per_block = std::max(1, std::min((int)c->tune.warps_per_block,
-                                                 (nunits + c->num_sms - 1) / c->num_sms));
-        int bps = 0;
-        if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
-        k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
-        {
-            Prof p(c, s, "sketch");
-            CK(launch_sketch(k, s), "launch sketch");
+    EnqArgs q{dp, hp, blob, o_units, o_bts, o_grp, o_ct, nbt, nunits, (int)cgroups.size(), (int)ctiles.size()};
+    if (c->graph_on && !c->prof && s != nullptr) {
+        // identical plan bytes and buffers -> the captured graph is exactly this batch's work
+        uint64_t sig = 1469598103934665603ull;
+        auto mix = [&](const void *p, size_t n) {
+            const unsigned char *b = static_cast<const unsigned char *>(p);
+            for (size_t i = 0; i < n; ++i) sig = (sig ^ b[i]) * 1099511628211ull;
+        };
+        mix(hp, blob);
+        const void *ptrs[] = {c->plan.p, c->usum.p, c->cand.p, c->match.p, c->uwalk.p, c->utrue.p, c->umode.p,
+                              c->uexp.p, c->uplan.p, c->uout.p, c->pref.p, c->recs.p, c->btres.p, c->ctsum.p};
+        mix(ptrs, sizeof ptrs);
+        mix(&c->tune, sizeof c->tune);
+        mix(&blob, sizeof blob);
+        if (!c->gexec || sig != c->gsig) {
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+            const int rq = enqueue_batch(c, s, q, false);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(s, &g);
+            if (rq) { if (g) cudaGraphDestroy(g); return rq; }
+            CK(ec, "end capture");
+            const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            CK(ei, "instantiate graph");
+            c->gsig = sig;
         }
-        {
-            Prof p(c, s, "match");
-            CK(launch_match(k, s), "launch match");
-        }
-        {
-            Prof p(c, s, "chain");
-            CK(launch_chain(k, s), "launch chain");
-        }
-        {
-            Prof p(c, s, "totals");
-            CK(launch_totals(k, s), "launch totals");
-        }
-    }
-    LaunchPost a;
-    a.units = d_units;
-    a.nunits = nunits;
-    a.bts = d_bts;
-    a.nbt = (int)nbt;
-    a.usum = static_cast<const UnitSum *>(c->usum.p);
-    a.utrue = static_cast<const UnitTrue *>(c->utrue.p);
-    a.uplan = static_cast<UnitPlan *>(c->uplan.p);
-    a.uout = static_cast<UnitOut *>(c->uout.p);
-    a.btres = static_cast<BTraceRes *>(c->btres.p);
-    a.recs = static_cast<FRec *>(c->recs.p);
-    a.pref = static_cast<int64_t *>(c->pref.p);
-    a.traces = c->traces;
-    a.lines = c->lines;
-    a.log = c->log;
-    a.log_cap = cfg.sample_log_capacity;
-    a.n_lines = cfg.n_lines;
-    a.T = cfg.threshold;
-    a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
-    a.groups = reinterpret_cast<const CompactGroup *>(dp + o_grp);
-    a.ngroups = (int)cgroups.size();
-    a.ctiles = reinterpret_cast<const CopyTile *>(dp + o_ct);
-    a.nctiles = (int)ctiles.size();
-    a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
-    a.err = c->errw;
-    {
-        Prof p(c, s, "scan");
-        CK(launch_scan(a, s), "launch scan");
-    }
-    if (nunits) {
-        LaunchFinal f;
-        f.units = d_units;
-        f.nunits = nunits;
-        f.utrue = a.utrue;
-        f.uplan = a.uplan;
-        f.recs = a.recs;
-        f.uout = a.uout;
-        f.T = cfg.threshold;
-        f.queue = c->queue + 2;
-        f.err = c->errw;
-        f.spin = cfg.spin_limit;
-        f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (nunits + c->num_sms - 1) / c->num_sms));
-        int bps = 0;
-        if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
-        f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
-        Prof p(c, s, "final");
-        CK(launch_final(f, s), "launch final");
-    }
-    {
-        Prof p(c, s, "compact");
-        CK(launch_compact(a, s), "launch compact");
-    }
-    {
-        Prof p(c, s, "mark");
-        CK(launch_mark(a, s), "launch mark");
-    }
-    {
-        Prof p(c, s, "epi");
-        CK(launch_epi(a, s), "launch epi");
-    }
-    {
-        Prof p(c, s, "copy_sum");
-        CK(launch_copy_sum(a, s), "launch copy sum");
-    }
-    {
-        Prof p(c, s, "copy_scan");
-        CK(launch_copy_scan(a, s), "launch copy scan");
-    }
-    {
-        Prof p(c, s, "copy_apply");
-        CK(launch_copy_apply(a, s), "launch copy apply");
-    }
-    {
-        Prof p(c, s, "state");
-        CK(launch_state(a, s), "launch state");
+        CK(cudaGraphLaunch(c->gexec, s), "graph launch");
+        // the graph reads the plan buffer in its first node: it may be rewritten once the graph is done
+        CK(cudaEventRecord(c->plan_done, s), "plan event");
+        c->plan_pending = true;
+    } else {
+        const int rq = enqueue_batch(c, s, q, true);
+        if (rq) return rq;
     }
     for (uint32_t bi = 0; bi < nbt; ++bi) c->h_events[bts[bi].trace] += bts[bi].n_ev;
     return SCL_OK;
@@ -760,15 +826,17 @@ int scl_state_import(scl_ctx *c, uint32_t trace, const void *buf, uint64_t n) {
 
 int scl_trace_reset(scl_ctx *c, uint32_t trace, void *stream) {
     if (!c) return SCL_EINVAL;
-    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    const bool all = trace == SCL_ALL_TRACES;
+    if (!all && trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t t0 = all ? 0 : trace, nt = all ? c->cfg.max_traces : 1;
     {
         Prof p(c, s, "reset");
-        CK(launch_reset(c->traces, c->lines, trace, c->cfg.n_lines, c->cfg.initial_footprint, c->cfg.copy_phase, s),
+        CK(launch_reset(c->traces, c->lines, t0, nt, c->cfg.n_lines, c->cfg.initial_footprint, c->cfg.copy_phase, s),
            "launch reset");
     }
-    c->h_events[trace] = 0;
+    for (uint32_t t = t0; t < t0 + nt; ++t) c->h_events[t] = 0;
     c->last_stream = s;
     return SCL_OK;
 }
@@ -829,13 +897,102 @@ int scl_selftest_wait(scl_ctx *c, uint64_t limit, void *stream) {
     return r;
 }
 
+int scl_graph_enable(scl_ctx *c, int on) {
+    if (!c) return SCL_EINVAL;
+    c->graph_on = on != 0;
+    if (!c->graph_on && c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return SCL_OK;
+}
+
 int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stream, scl_tuning *best_out,
                  double *best_ms_out) {
-    (void)segs; (void)nsegs; (void)stream;
     if (!c) return SCL_EINVAL;
-    if (best_out) *best_out = c->tune;
-    if (best_ms_out) *best_ms_out = 0.0;
-    return fail(c, SCL_EINVAL, "autotune not available yet");
+    if (nsegs == 0 || !segs) return fail(c, SCL_EINVAL, "autotune needs at least one segment");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    // save the resident state of every trace the segments touch; restore it after each trial
+    std::vector<uint32_t> tr;
+    for (uint32_t i = 0; i < nsegs; ++i)
+        if (segs[i].trace_id < c->cfg.max_traces &&
+            std::find(tr.begin(), tr.end(), segs[i].trace_id) == tr.end())
+            tr.push_back(segs[i].trace_id);
+    const size_t L = c->cfg.n_lines;
+    const size_t per = sizeof(DevTrace) + sizeof(LineRow) * L;
+    void *save = nullptr;
+    CK(cudaMalloc(&save, per * std::max<size_t>(1, tr.size())), "autotune state copy");
+    std::vector<uint64_t> h_ev(tr.size());
+    auto copy_state = [&](bool to_save) -> cudaError_t {
+        for (size_t i = 0; i < tr.size(); ++i) {
+            char *b = static_cast<char *>(save) + i * per;
+            DevTrace *t = c->traces + tr[i];
+            LineRow *l = c->lines + (size_t)tr[i] * L;
+            cudaError_t e = to_save ? cudaMemcpyAsync(b, t, sizeof(DevTrace), cudaMemcpyDeviceToDevice, s)
+                                    : cudaMemcpyAsync(t, b, sizeof(DevTrace), cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = to_save ? cudaMemcpyAsync(b + sizeof(DevTrace), l, sizeof(LineRow) * L, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpyAsync(l, b + sizeof(DevTrace), sizeof(LineRow) * L, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            if (to_save) h_ev[i] = c->h_events[tr[i]];
+            else c->h_events[tr[i]] = h_ev[i];
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const scl_tuning keep = c->tune;
+    const bool prof = c->prof, graph = c->graph_on;
+    c->prof = false;
+    c->graph_on = false;
+    scl_tuning best = keep;
+    double best_ms = 1e300;
+    int rc = copy_state(true) == cudaSuccess ? SCL_OK : SCL_ECUDA;
+    const uint32_t units[] = {0, 65536, 131072, 262144};
+    const uint32_t fwarps[] = {10, 14};
+    const uint32_t swarps[] = {8, 16};
+    const uint32_t warm[] = {16384, 32768};
+    for (uint32_t ue : units)
+        for (uint32_t fw : fwarps)
+            for (uint32_t sw : swarps)
+                for (uint32_t wm : warm) {
+                    if (rc) break;
+                    c->tune.unit_events = ue;
+                    c->tune.final_warps = fw;
+                    c->tune.warps_per_block = sw;
+                    c->tune.ext_events = wm;
+                    std::vector<float> ts;
+                    for (int rep = 0; rep < 4 && !rc; ++rep) {
+                        if (copy_state(false) != cudaSuccess) { rc = SCL_ECUDA; break; }
+                        cudaEventRecord(e0, s);
+                        rc = scl_replay_batch(c, segs, nsegs, stream);
+                        cudaEventRecord(e1, s);
+                        if (rc) break;
+                        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SCL_ECUDA; break; }
+                        if ((rc = check_device_error(c))) break;
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0) ts.push_back(ms);   // the first run warms up
+                    }
+                    if (rc) break;
+                    std::sort(ts.begin(), ts.end());
+                    const double med = ts[ts.size() / 2];
+                    if (med < best_ms) { best_ms = med; best = c->tune; }
+                }
+    if (copy_state(false) != cudaSuccess && !rc) rc = SCL_ECUDA;
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save);
+    c->prof = prof;
+    c->graph_on = graph;
+    c->tune = rc ? keep : best;
+    if (rc) return rc == SCL_ECUDA ? fail(c, rc, "autotune: a CUDA call failed") : rc;
+    if (best_out) *best_out = best;
+    if (best_ms_out) *best_ms_out = best_ms;
+    return SCL_OK;
 }
 
 }  // extern "C"

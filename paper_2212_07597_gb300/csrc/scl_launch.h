@@ -93,9 +93,16 @@ cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_state(const LaunchPost &a, cudaStream_t s);
 
-cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace, uint32_t n_lines, int64_t F0,
-                         uint64_t phase, cudaStream_t s);
+cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
+                         int64_t F0, uint64_t phase, cudaStream_t s);
 cudaError_t launch_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines, uint32_t rule, void *out,
                           cudaStream_t s);
 
 }  // namespace scl
+
+// context facts the serving loop needs (scl_serve.cu); defined in scl_host.cu
+struct scl_ctx;
+uint32_t scl_ctx_max_traces(const scl_ctx *c);
+int scl_ctx_device(const scl_ctx *c);
+int scl_ctx_fail(scl_ctx *c, int code, const char *msg);
+void scl_ctx_forget_stream(scl_ctx *c);   // the last replay stream is about to be destroyed

@@ -13,6 +13,8 @@
 //              copied, counted from the running byte count.
 //   k_state    folds the batch into the trace's resident state.
 #include "scl_internal.cuh"
+#include <algorithm>
+
 #include "scl_launch.h"
 
 namespace scl {
@@ -541,13 +543,13 @@ __global__ void k_state(LaunchPost a) {
 }
 
 // ---------------------------------------------------------------- reset / scores
-__global__ void k_reset(DevTrace *traces, LineRow *lines, uint32_t trace, uint32_t n_lines, int64_t F0,
-                        uint64_t phase) {
-    unsigned long long *rows = reinterpret_cast<unsigned long long *>(lines + (uint64_t)trace * n_lines);
-    const uint64_t nw = (uint64_t)n_lines * (sizeof(LineRow) / 8);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x)
-        rows[i] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+__global__ void k_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
+                        int64_t F0, uint64_t phase) {
+    unsigned long long *rows = reinterpret_cast<unsigned long long *>(lines + (uint64_t)trace0 * n_lines);
+    const uint64_t nw = (uint64_t)ntr * n_lines * (sizeof(LineRow) / 8);
+    const uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = i0; i < nw; i += stride) rows[i] = 0;
+    for (uint64_t k = i0; k < ntr; k += stride) {
         DevTrace t;
         t.c = t.A = t.F = t.A_py = t.F_py = 0;
         t.footprint = F0;
@@ -556,7 +558,7 @@ __global__ void k_reset(DevTrace *traces, LineRow *lines, uint32_t trace, uint32
         t.tracked_line = t.tracked_valid = t.tracked_reclaimed = t.pad0 = 0;
         t.n_events = t.n_copies = t.n_samples = 0;
         t.copy_counter = phase;
-        traces[trace] = t;
+        traces[trace0 + k] = t;
     }
 }
 
@@ -639,13 +641,13 @@ cudaError_t launch_state(const LaunchPost &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace, uint32_t n_lines, int64_t F0,
-                         uint64_t phase, cudaStream_t s) {
-    const uint64_t nw = (uint64_t)n_lines * (sizeof(LineRow) / 8);
-    int blocks = (int)((nw + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
+cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
+                         int64_t F0, uint64_t phase, cudaStream_t s) {
+    const uint64_t nw = (uint64_t)ntr * n_lines * (sizeof(LineRow) / 8);
+    uint64_t blocks = (std::max<uint64_t>(nw, ntr) + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    k_reset<<<blocks, 256, 0, s>>>(traces, lines, trace, n_lines, F0, phase);
+    k_reset<<<(int)blocks, 256, 0, s>>>(traces, lines, trace0, ntr, n_lines, F0, phase);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libscl.so")
 
 SCL_OK, SCL_EINVAL, SCL_ENOMEM, SCL_ECUDA, SCL_ETIMEOUT, SCL_EOVERFLOW, SCL_ERANGE = 0, -1, -2, -3, -4, -5, -6
+SCL_ALL_TRACES = 0xFFFFFFFF
 _NAMES = {-1: "SCL_EINVAL", -2: "SCL_ENOMEM", -3: "SCL_ECUDA", -4: "SCL_ETIMEOUT", -5: "SCL_EOVERFLOW",
           -6: "SCL_ERANGE", -7: "SCL_EINTERNAL"}
 
@@ -30,7 +31,7 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_replay_batch_host", "scl_sync", "scl_samples", "scl_line_stats", "scl_leak_scores",
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
-           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats")
+           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve")
 
 
 class SclError(RuntimeError):
@@ -60,6 +61,24 @@ class scl_config(ctypes.Structure):
 class scl_segment(ctypes.Structure):
     _fields_ = [("trace_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ev", scl_events),
                 ("cp", scl_copies)]
+
+
+class scl_request(ctypes.Structure):
+    _fields_ = [("trace_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("arrival_ns", ctypes.c_uint64),
+                ("ev", scl_events), ("cp", scl_copies)]
+
+
+class scl_serve_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32), ("realtime", ctypes.c_uint32)]
+
+
+class scl_serve_summary(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("events", ctypes.c_uint64),
+                ("staging_bytes", ctypes.c_uint64), ("wall_s", ctypes.c_double)]
+
+
+REQUEST_RESULT_DTYPE = np.dtype([("done_ns", "<u8"), ("latency_ns", "<u8"), ("batch", "<u4"),
+                                 ("reserved", "<u4")])
 
 
 class scl_tuning(ctypes.Structure):
@@ -122,6 +141,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scl_profile_reset": ([P], I),
             "scl_selftest_wait": ([P, U64, P], I),
             "scl_batch_stats": ([P, P], I),
+            "scl_graph_enable": ([P, I], I),
+            "scl_serve": ([P, P, U32, P, P, P], I),
             "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -308,6 +329,32 @@ def scl_autotune(ctx: Context, segs, stream=None) -> tuple[scl_tuning, float]:
     _check(ctx, load().scl_autotune(ctx.handle, arr, len(segs), _stream(stream), ctypes.byref(best),
                                     ctypes.byref(ms)))
     return best, ms.value
+
+
+def scl_graph_enable(ctx: Context, on: bool = True) -> None:
+    _check(ctx, load().scl_graph_enable(ctx.handle, int(on)))
+
+
+def request(trace_id: int, arrival_ns: int, delta, addr, line, is_python, csize=None, cline=None,
+            cpy=None) -> scl_request:
+    """Descriptor of one serving request; arrays are host numpy arrays (kept alive by the caller)."""
+    r = scl_request()
+    r.trace_id = trace_id
+    r.arrival_ns = int(arrival_ns)
+    r.ev = scl_events(_ptr(delta), _ptr(addr), _ptr(line), _ptr(is_python), 0 if delta is None else len(delta))
+    r.cp = scl_copies(_ptr(csize), _ptr(cline), _ptr(cpy), 0 if csize is None else len(csize))
+    return r
+
+
+def scl_serve(ctx: Context, reqs, hbm_budget: int = 0, max_batch: int = 0, realtime: bool = False):
+    """Serve the requests; returns (per-request results as REQUEST_RESULT_DTYPE, summary dict)."""
+    arr = (scl_request * max(1, len(reqs)))(*reqs)
+    opts = scl_serve_opts(hbm_budget, max_batch, int(realtime))
+    out = np.zeros(max(1, len(reqs)), REQUEST_RESULT_DTYPE)
+    sm = scl_serve_summary()
+    _check(ctx, load().scl_serve(ctx.handle, arr, len(reqs), ctypes.byref(opts), out.ctypes.data,
+                                 ctypes.byref(sm)))
+    return out[:len(reqs)], {k: getattr(sm, k) for k, _ in scl_serve_summary._fields_}
 
 
 def scl_profile_enable(ctx: Context, on: bool = True) -> None:

@@ -37,6 +37,33 @@ def test_struct_layouts_match_header():
     assert scl.TRACE_INFO_DTYPE.itemsize == 112
 
 
+def test_struct_layouts_match_c_compiler(tmp_path):
+    """sizeof of every ABI struct as gcc lays it out from include/scl.h == the binding's."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    pairs = {"scl_config": ctypes.sizeof(scl.scl_config), "scl_segment": ctypes.sizeof(scl.scl_segment),
+             "scl_events": ctypes.sizeof(scl.scl_events), "scl_copies": ctypes.sizeof(scl.scl_copies),
+             "scl_tuning": ctypes.sizeof(scl.scl_tuning), "scl_request": ctypes.sizeof(scl.scl_request),
+             "scl_serve_opts": ctypes.sizeof(scl.scl_serve_opts),
+             "scl_serve_summary": ctypes.sizeof(scl.scl_serve_summary),
+             "scl_request_result": scl.REQUEST_RESULT_DTYPE.itemsize,
+             "scl_sample": scl.SAMPLE_DTYPE.itemsize, "scl_line_stat": scl.LINE_STAT_DTYPE.itemsize,
+             "scl_leak_score": scl.LEAK_DTYPE.itemsize, "scl_trace_info": scl.TRACE_INFO_DTYPE.itemsize,
+             "scl_batch_info": scl.BATCH_INFO_DTYPE.itemsize}
+    inc = os.path.join(ROOT, "include")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "scl.h"\nint main(void){\n' +
+                   "".join(f'printf("{k} %zu\\n", sizeof({k}));\n' for k in pairs) + "return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for k, v in pairs.items():
+        assert int(got[k]) == v, (k, got[k], v)
+
+
 def test_config_defaults_without_gpu():
     cfg = scl.config()
     assert cfg.threshold == 10_485_767 and cfg.copy_multiple == 2 and cfg.n_lines == 256

@@ -194,3 +194,47 @@ def test_bad_descriptors_rejected_on_host():
     d = torch.zeros(4097, dtype=torch.int64, device="cuda")
     with pytest.raises(scl.SclError):
         scl.scl_replay_batch(ctx, [scl.segment(0, d[1:], d[1:], d[1:], d[1:], n=4096)])   # misaligned
+
+
+def test_graph_replay_of_identical_batches():
+    import torch
+    tr = tg.plain_trace(200_000, seed=16, leak_lines=(1,))
+    ctx = gpu_ctx(1_048_573, unit=16384)
+    scl.scl_graph_enable(ctx, True)
+    stream = torch.cuda.Stream()
+    seg, keep = scl.trace_segment(0, tr)
+    with torch.cuda.stream(stream):
+        for _ in range(3):   # capture once, relaunch twice
+            scl.scl_trace_reset(ctx, 0, stream)
+            scl.scl_replay_batch(ctx, [seg], stream)
+    scl.scl_sync(ctx)
+    assert_same(ctx, 0, oracle_of(tr, 1_048_573))
+    # a different plan is captured anew
+    tr2 = tg.plain_trace(50_000, seed=17)
+    seg2, keep2 = scl.trace_segment(0, tr2)
+    scl.scl_replay_batch(ctx, [seg2], stream)
+    scl.scl_sync(ctx)
+    o = oracle.Oracle(1_048_573)
+    for t in (tr, tr2):
+        o.replay_events(t.delta, t.addr, t.line, t.is_python)
+    o.replay_copies(np.concatenate([tr.csize, tr2.csize]), np.concatenate([tr.cline, tr2.cline]),
+                    np.concatenate([tr.cpy, tr2.cpy]))
+    assert_same(ctx, 0, o)
+
+
+def test_autotune_restores_state_and_keeps_results_exact():
+    tr = tg.plain_trace(400_000, seed=18, leak_lines=(0,))
+    a, b = tr.slice(0, 150_000, 0, 15_000), tr.slice(150_000, tr.n, 15_000, len(tr.csize))
+    ctx = gpu_ctx(1_048_573)
+    keep = replay(ctx, [(0, a)])
+    before = scl.scl_state_export(ctx, 0)
+    seg, kb = scl.trace_segment(0, b)
+    best, ms = scl.scl_autotune(ctx, [seg])
+    assert ms > 0 and best.final_warps in (10, 14) and best.ext_events in (16384, 32768)
+    assert scl.scl_state_export(ctx, 0) == before
+    t = scl.scl_tuning_get(ctx)
+    assert (t.unit_events, t.final_warps, t.warps_per_block, t.ext_events) == \
+        (best.unit_events, best.final_warps, best.warps_per_block, best.ext_events)
+    scl.scl_replay_batch(ctx, [seg])
+    scl.scl_sync(ctx)
+    assert_same(ctx, 0, oracle_of(tr, 1_048_573), samples=False)
