@@ -77,6 +77,20 @@ def aggregate(times_ms, events):
     return sum(events) / (t / 1e3), t
 
 
+def job_throughput(ms, events, device="cpu"):
+    """(events/s, slowest ms) of the whole job: under torch.distributed, the events of every
+    rank (sum) over the slowest rank's time (max); alone, this rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return aggregate([ms], [events])
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(events)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return aggregate([float(t.item())], [float(e.item())])
+
+
 def make_trace(workload: str, rank: int, n_override: int = 0):
     from paper_2212_07597_gb300 import tracegen as tg
     if workload == "long_256m":
@@ -89,42 +103,80 @@ def make_trace(workload: str, rank: int, n_override: int = 0):
 
 
 class Clocks:
-    """nvidia-smi clock / throttle sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi clock / throttle sampling (every 50 ms) around the timed region.
+
+    Each sample carries nvidia-smi's own timestamp, so the samples inside the timed
+    region are told apart from those of the warm-up just before it."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.t0 = self.t1 = None
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def _rows(self):
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        except OSError:
+            pass
+        return rows
+
+    def warm(self, step, sync, max_s=3.0):
+        """Run untimed steps until the sampler has produced samples (it starts slowly)."""
+        t = time.time()
+        while self.p is not None and len(self._rows()) < 2 and time.time() - t < max_s:
+            step()
+            sync()
+
+    def start(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.p is None:
             return None
+        time.sleep(0.06)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except Exception:
             self.p.kill()
         self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = self._rows()
         os.unlink(self.f.name)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        import datetime
+
+        def when(r):
+            try:
+                return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                return None
+        inside = [r for r in rows if self.t0 and when(r) is not None and self.t0 <= when(r) <= self.t1 + 0.05]
+        use = inside or rows
+        num = lambda x: x.replace(".", "", 1).isdigit()
+        sm = [float(r[2]) for r in use if num(r[2])]
+        mx = [float(r[3]) for r in rows if num(r[3])]
+        reasons = sorted({self.NAMES[i] for r in use for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "samples_in_timed_region": len(inside),
+                "basis": "timed region" if inside else "warm-up just before the timed region (region shorter "
+                                                        "than the sampling period)"}
 
 
 def source_hash() -> str:
@@ -322,23 +374,23 @@ def run_batched(args):
         step()
     scl.scl_sync(ctx)
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.warm(step, torch.cuda.synchronize)
     barrier()
+    if clocks:
+        clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     barrier()
+    if clocks:
+        clocks.end()
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     scl.scl_sync(ctx)
-    times = [ms]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = [float(t.item())]
-    value, tmax = aggregate(times, [n_tot * args.steps] * ws)
+    value, tmax = job_throughput(ms, n_tot * args.steps, dev)
     bstats = scl.scl_batch_stats(ctx)
 
     # per-kernel times (profiling replaces the graph by plain launches) for the roofline
@@ -492,6 +544,7 @@ def run_serving(args):
     for i, p in enumerate(owner):
         k = int(nxt[p])
         nxt[p] += 1
+        p = int(p)
         a = p * n_p + k * L
         b0, b1 = p * m_p + k * L // 10, p * m_p + (k + 1) * L // 10
         r = scl.scl_request()
@@ -516,7 +569,11 @@ def run_serving(args):
     for _ in range(max(3, args.warmup)):
         serve(False)
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.warm(lambda: serve(False), torch.cuda.synchronize)
     barrier()
+    if clocks:
+        clocks.start()
     # saturation: every request present at the start; host-to-device copies inside
     walls, batches = [], []
     for _ in range(args.steps):
@@ -532,16 +589,12 @@ def run_serving(args):
         rt_walls.append(sm["wall_s"])
         rt_batches.append(sm["batches"])
     barrier()
+    if clocks:
+        clocks.end()
     clk = clocks.stop() if clocks else None
     lat = np.concatenate(lat) / 1e6
     wall = sum(walls)
-    times = [wall * 1e3]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([wall * 1e3], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = [float(t.item())]
-    value, tmax = aggregate(times, [N * args.steps] * ws)
+    value, tmax = job_throughput(wall * 1e3, N * args.steps, "cuda")
 
     # per-kernel times of one saturated pass for the roofline (profiling on)
     scl.scl_profile_reset(ctx)
@@ -634,26 +687,32 @@ def main():
         scl.scl_trace_reset(ctx, 0, stream)
         scl.scl_replay_batch(ctx, [seg], stream)
 
-    for _ in range(args.warmup):
-        step()
-    scl.scl_sync(ctx)
-    scl.scl_profile_reset(ctx)
-    scl.scl_profile_enable(ctx, True)
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-
     def barrier():
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
 
+    for _ in range(args.warmup):
+        step()
+    scl.scl_sync(ctx)
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.warm(step, torch.cuda.synchronize)
+    scl.scl_sync(ctx)
+    scl.scl_profile_reset(ctx)
+    scl.scl_profile_enable(ctx, True)
     barrier()
+    if clocks:
+        clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     barrier()
+    if clocks:
+        clocks.end()
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     scl.scl_profile_enable(ctx, False)
@@ -661,13 +720,7 @@ def main():
     scl.scl_sync(ctx)
     bstats = scl.scl_batch_stats(ctx)
 
-    times = [ms]
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = [float(t.item())]
-    value, tmax = aggregate(times, [n * args.steps] * ws) if ws > 1 else (n * args.steps / (ms / 1e3), ms)
+    value, tmax = job_throughput(ms, n * args.steps, dev)
 
     # dominant kernel and its roofline
     launches = sum(c for _, c in ktimes.values())

@@ -439,65 +439,89 @@ __global__ void __launch_bounds__(NT) k_copy_scan(LaunchPost a) {
 
 constexpr int CPT = COPY_TILE / NT;   // memcpy events per thread
 
-// Section 3.5 per tile: the copy counter before the tile (from k_copy_scan) plus the
-// running byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
-// Each thread owns CPT consecutive memcpys (sizes staged through shared memory, padded
-// against bank conflicts) and carries the remainder mod T_c, so a division is needed
-// only for a memcpy of at least 8 T_c.
-__global__ void __launch_bounds__(NT) k_copy_apply(LaunchPost a) {
-    extern __shared__ __align__(16) unsigned long long chist[];   // [n_lines][4]: samples py0, py1, bytes py0, py1
-    __shared__ unsigned long long ssz[COPY_TILE + COPY_TILE / CPT];
-    __shared__ int64_t sh[NT / 32 + 1];
-    const CopyTile C = a.ctiles[blockIdx.x];
-    const BTrace &B = a.bts[C.bt];
-    const bool use_smem = a.n_lines <= (uint32_t)SMEM_LINES_MAX;
-    if (use_smem)
-        for (uint32_t i = threadIdx.x; i < a.n_lines * 4; i += NT) chist[i] = 0;
-    for (uint32_t j = threadIdx.x; j < COPY_TILE; j += NT) ssz[j + j / CPT] = j < C.len ? C.size[j] : 0ull;
-    __syncthreads();
-    const unsigned long long Tc = a.Tc;
-    const uint32_t j0 = threadIdx.x * CPT;
-    const unsigned long long *mine = &ssz[j0 + threadIdx.x];
-    unsigned long long loc = 0;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) loc += mine[k];
-    int64_t tot;
-    const uint64_t ex = (uint64_t)block_excl_sum((int64_t)loc, sh, &tot);
-    const uint64_t start = a.ctile_sum[blockIdx.x] + ex;   // bytes counted before this thread's first memcpy
-    unsigned long long rem = start % Tc;
-    LineRow *grow = a.lines + (uint64_t)B.trace * a.n_lines;
-    for (int k = 0; k < CPT; ++k) {
-        const uint32_t j = j0 + k;
-        if (j >= C.len) break;
-        const unsigned long long sz = mine[k];
-        unsigned long long q;
-        if (sz >= 8 * Tc) {
-            q = (rem + sz) / Tc;
-            rem = (rem + sz) % Tc;
-        } else {
-            rem += sz;
-            q = 0;
-            while (rem >= Tc) { rem -= Tc; ++q; }
-        }
-        if (!q) continue;
-        const uint32_t line = C.line[j];
-        if (line >= a.n_lines) { set_error(a.err, E_RANGE, line, j); continue; }
-        const int f = C.py[j] ? 1 : 0;
-        if (use_smem) {
-            atomicAdd(&chist[line * 4 + f], q);
-            atomicAdd(&chist[line * 4 + 2 + f], q * Tc);
-        } else {
-            atomicAdd(&grow[line].copy_samples[f], q);
-            atomicAdd(&grow[line].copy_bytes[f], q * Tc);
+constexpr uint32_t COPY_SMEM_LINES = 4096;   // per-line copy counts kept in shared memory up to this L
+
+// add a block's per-(line, flag) copy sample counts to the trace's rows and clear them;
+// copy bytes are samples * T_c, so only the counts are kept
+__device__ __forceinline__ void copy_flush(unsigned long long *hist, uint32_t n_lines, LineRow *row,
+                                           unsigned long long Tc) {
+    for (uint32_t i = threadIdx.x; i < 2 * n_lines; i += NT) {
+        const unsigned long long v = hist[i];
+        if (v) {
+            const uint32_t l = i >> 1, f = i & 1;
+            atomicAdd(&row[l].copy_samples[f], v);
+            atomicAdd(&row[l].copy_bytes[f], v * Tc);
+            hist[i] = 0;
         }
     }
-    if (use_smem) {
-        __syncthreads();
-        for (uint32_t l = threadIdx.x; l < a.n_lines; l += NT) {
-            const unsigned long long *h = &chist[l * 4];
-            if (h[0]) { atomicAdd(&grow[l].copy_samples[0], h[0]); atomicAdd(&grow[l].copy_bytes[0], h[2]); }
-            if (h[1]) { atomicAdd(&grow[l].copy_samples[1], h[1]); atomicAdd(&grow[l].copy_bytes[1], h[3]); }
+}
+
+// Section 3.5: the copy counter before each tile (from k_copy_scan) plus the running
+// byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
+// Each block takes a contiguous range of tiles, so it meets few traces; its counts stay
+// in shared memory and reach the trace's rows once per trace it meets.  Each thread owns
+// CPT consecutive memcpys of a tile (sizes staged through shared memory, padded against
+// bank conflicts) and carries the remainder mod T_c, so a division is needed only for a
+// memcpy of at least 8 T_c.
+__global__ void __launch_bounds__(NT) k_copy_apply(LaunchPost a) {
+    extern __shared__ __align__(16) unsigned long long chist[];   // [n_lines][2]: samples, by flag
+    __shared__ unsigned long long ssz[COPY_TILE + COPY_TILE / CPT];
+    __shared__ int64_t sh[NT / 32 + 1];
+    const bool use_smem = a.n_lines <= COPY_SMEM_LINES;
+    const int t0 = (int)((int64_t)blockIdx.x * a.nctiles / gridDim.x);
+    const int t1 = (int)((int64_t)(blockIdx.x + 1) * a.nctiles / gridDim.x);
+    if (use_smem)
+        for (uint32_t i = threadIdx.x; i < 2 * a.n_lines; i += NT) chist[i] = 0;
+    const unsigned long long Tc = a.Tc;
+    int cur = -1;   // batch trace whose counts the table holds
+    for (int t = t0; t < t1; ++t) {
+        const CopyTile C = a.ctiles[t];
+        __syncthreads();   // the previous tile's sizes and counts are done with
+        if (use_smem && cur >= 0 && (int)C.bt != cur) {
+            copy_flush(chist, a.n_lines, a.lines + (uint64_t)a.bts[cur].trace * a.n_lines, Tc);
+            __syncthreads();
         }
+        cur = (int)C.bt;
+        for (uint32_t j = threadIdx.x; j < COPY_TILE; j += NT) ssz[j + j / CPT] = j < C.len ? C.size[j] : 0ull;
+        __syncthreads();
+        const uint32_t j0 = threadIdx.x * CPT;
+        const unsigned long long *mine = &ssz[j0 + threadIdx.x];
+        unsigned long long loc = 0;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) loc += mine[k];
+        int64_t tot;
+        const uint64_t ex = (uint64_t)block_excl_sum((int64_t)loc, sh, &tot);
+        const uint64_t start = a.ctile_sum[t] + ex;   // bytes counted before this thread's first memcpy
+        unsigned long long rem = start % Tc;
+        LineRow *grow = a.lines + (uint64_t)a.bts[C.bt].trace * a.n_lines;
+        for (int k = 0; k < CPT; ++k) {
+            const uint32_t j = j0 + k;
+            if (j >= C.len) break;
+            const unsigned long long sz = mine[k];
+            unsigned long long q;
+            if (sz >= 8 * Tc) {
+                q = (rem + sz) / Tc;
+                rem = (rem + sz) % Tc;
+            } else {
+                rem += sz;
+                q = 0;
+                while (rem >= Tc) { rem -= Tc; ++q; }
+            }
+            if (!q) continue;
+            const uint32_t line = C.line[j];
+            if (line >= a.n_lines) { set_error(a.err, E_RANGE, line, j); continue; }
+            const int f = C.py[j] ? 1 : 0;
+            if (use_smem) {
+                atomicAdd(&chist[line * 2 + f], q);
+            } else {
+                atomicAdd(&grow[line].copy_samples[f], q);
+                atomicAdd(&grow[line].copy_bytes[f], q * Tc);
+            }
+        }
+    }
+    if (use_smem && cur >= 0) {
+        __syncthreads();
+        copy_flush(chist, a.n_lines, a.lines + (uint64_t)a.bts[cur].trace * a.n_lines, Tc);
     }
 }
 
@@ -628,10 +652,17 @@ cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s) {
 
 cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s) {
     if (!a.nctiles) return cudaSuccess;
-    const size_t smem = a.n_lines <= (uint32_t)SMEM_LINES_MAX ? (size_t)a.n_lines * 4 * 8 : 0;
+    const bool sm_table = a.n_lines <= COPY_SMEM_LINES;
+    const size_t smem = sm_table ? (size_t)a.n_lines * 2 * 8 : 0;
     cudaError_t e = cudaFuncSetAttribute(k_copy_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem ? smem : 1));
     if (e != cudaSuccess) return e;
-    k_copy_apply<<<a.nctiles, NT, smem, s>>>(a);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_copy_apply, NT, smem)) != cudaSuccess) return e;
+    // one wave of blocks, each a contiguous range of tiles
+    const int grid = std::max(1, std::min(a.nctiles, sms * std::max(1, per_sm)));
+    k_copy_apply<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 

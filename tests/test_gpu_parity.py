@@ -98,6 +98,18 @@ def test_many_traces_one_batch():
         assert_same(ctx, i, oracle_of(tr, 1_048_573, n_lines=64))
 
 
+@pytest.mark.parametrize("n_lines", [1024, 4096, 5000])
+def test_wide_line_spaces_many_copy_tiles(n_lines):
+    # more copy tiles than one wave of copy blocks, so blocks span several tiles and traces;
+    # 4,096 lines is the largest shared-memory table, 5,000 takes the global-memory path
+    lens = [1_700_000] * 10 + [3, 50_001]
+    trs = [tg.plain_trace(n, seed=21, trace=i, n_lines=n_lines) for i, n in enumerate(lens)]
+    ctx = gpu_ctx(T0, n_lines=n_lines, max_traces=len(lens), log_cap=1 << 16)
+    keep = replay(ctx, list(enumerate(trs)))
+    for i, tr in enumerate(trs):
+        assert_same(ctx, i, oracle_of(tr, T0, n_lines=n_lines))
+
+
 def test_initial_footprint_rule1_and_phase():
     tr = tg.plain_trace(120_000, seed=8, p_malloc=0.5)
     kw = dict(initial_footprint=5 * tg.GIB, leak_rule=1, copy_phase=12345, copy_multiple=3)
