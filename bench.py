@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 # algorithmic bytes each kernel must read per unit it processes
 ALG_BYTES = {
-    "sketch": 9.0,        # delta (8) + is_python (1) per event: candidate counters and unit totals
+    "sketch": 8.0,        # delta per event: the candidate counters (warm-up re-reads are overhead, not counted)
     "final": 17.0,        # delta (8) + addr (8) + is_python (1) per event: the exact replay
     "copy_apply": 13.0,   # size (8) + line (4) + is_python (1) per memcpy event
     "copy_sum": 8.0,      # size per memcpy event
@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--procs", type=int, default=0, help="serving: processes (default 512)")
     p.add_argument("--segs", type=int, default=0, help="serving: segments per process (default 16)")
     p.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
+    p.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -186,8 +187,11 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, events: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+def traffic_for(kernel: str, units: int, streamed: int = 0):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json), if it
+    was taken on the current kernels: bytes per unit x units, where a unit is an event
+    (exact replay), a memcpy (copy kernels), or for the sketch an event streamed through
+    it (its unit plus its warm-up, `streamed`)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -198,7 +202,7 @@ def traffic_for(kernel: str, events: int):
     k = d.get("kernels", {}).get(kernel)
     if not k or d.get("source_hash") != source_hash():
         return None
-    return k["dram_bytes_per_event"] * events
+    return k["dram_bytes_per_unit"] * (streamed if k.get("unit") == "streamed event" else units)
 
 
 def oracle_replay(tr, meta):
@@ -373,7 +377,7 @@ def run_batched(args):
     for _ in range(max(3, args.warmup)):
         step()
     scl.scl_sync(ctx)
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
     if clocks:
         clocks.warm(step, torch.cuda.synchronize)
     barrier()
@@ -568,7 +572,7 @@ def run_serving(args):
 
     for _ in range(max(3, args.warmup)):
         serve(False)
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
     if clocks:
         clocks.warm(lambda: serve(False), torch.cuda.synchronize)
     barrier()
@@ -696,7 +700,7 @@ def main():
     for _ in range(args.warmup):
         step()
     scl.scl_sync(ctx)
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
     if clocks:
         clocks.warm(step, torch.cuda.synchronize)
     scl.scl_sync(ctx)
@@ -800,7 +804,8 @@ def main():
                 "hbm_gbs_path": path_gbs,
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src,
-                             "traffic": traffic_for(dom, per_launch_units),
+                             "traffic": traffic_for(dom, per_launch_units,
+                                                    n + max(0, bstats["units"] - 1) * 32768),
                              "alg_bytes_per_unit": ALG_BYTES[dom]},
                 "kernels_ms_per_step": {k: v[0] / max(1, v[1]) * (v[1] / args.steps) for k, v in ktimes.items()},
                 "gpu_launches": launches,

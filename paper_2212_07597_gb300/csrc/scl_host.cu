@@ -47,7 +47,7 @@ struct scl_ctx {
     uint64_t last_units = 0;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
-    DevBuf plan, usum, cand, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
+    DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
     void *h_plan = nullptr;
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
@@ -219,6 +219,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         k.nbt = (int)nbt;
         k.usum = static_cast<UnitSum *>(c->usum.p);
         k.cand = static_cast<Cand *>(c->cand.p);
+        k.lists = static_cast<SRes *>(c->lists.p);
         k.match = static_cast<uint8_t *>(c->match.p);
         k.uwalk = static_cast<Walk *>(c->uwalk.p);
         k.utrue = static_cast<UnitTrue *>(c->utrue.p);
@@ -290,6 +291,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         f.nunits = nunits;
         f.utrue = a.utrue;
         f.uplan = a.uplan;
+        f.lists = static_cast<const SRes *>(c->lists.p);
         f.recs = a.recs;
         f.uout = a.uout;
         f.T = cfg.threshold;
@@ -368,7 +370,7 @@ void scl_replay_free(scl_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
+    for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->lists, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
                       &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
@@ -517,7 +519,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     std::vector<BTrace> bts(nbt);
     std::vector<CompactGroup> cgroups;
     std::vector<CopyTile> ctiles;
-    uint64_t rec_total = 0;
+    uint64_t rec_total = 0, lst_total = 0;
     for (uint32_t bi = 0; bi < nbt; ++bi) {
         const uint32_t b = order[bi];
         BTrace &B = bts[bi];
@@ -541,9 +543,14 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 U.rec_cap = (uint32_t)std::min<uint64_t>((U.len >> shift) + 64, 0xffffffffu);
                 U.trace = B.trace;
                 U.bt = bi;
+                // reset lists: one reset per 32 events covers the thresholds worth listing;
+                // a run with more resets leaves its unit to the crossing search
+                U.lst0 = lst_total;
+                U.lst_cap = (uint32_t)((U.len >> 5) + 64);
                 units.push_back(U);
                 gidx += U.len;
                 rec_total += U.rec_cap;
+                lst_total += (uint64_t)NL * U.lst_cap;
             }
             for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
                 CopyTile T;
@@ -595,6 +602,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;
     if ((r = ensure(c, c->usum, sizeof(UnitSum) * nu1, s, "unit sums"))) return r;
     if ((r = ensure(c, c->cand, sizeof(Cand) * K * nu1, s, "candidates"))) return r;
+    if ((r = ensure(c, c->lists, sizeof(SRes) * std::max<uint64_t>(1, lst_total), s, "reset lists"))) return r;
     if ((r = ensure(c, c->match, sizeof(uint8_t) * K * nu1, s, "candidate matches"))) return r;
     if ((r = ensure(c, c->uwalk, sizeof(Walk) * nu1, s, "walks"))) return r;
     if ((r = ensure(c, c->utrue, sizeof(UnitTrue) * nu1, s, "true trajectories"))) return r;
@@ -620,7 +628,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
             for (size_t i = 0; i < n; ++i) sig = (sig ^ b[i]) * 1099511628211ull;
         };
         mix(hp, blob);
-        const void *ptrs[] = {c->plan.p, c->usum.p, c->cand.p, c->match.p, c->uwalk.p, c->utrue.p, c->umode.p,
+        const void *ptrs[] = {c->plan.p, c->usum.p, c->cand.p, c->lists.p, c->match.p, c->uwalk.p, c->utrue.p, c->umode.p,
                               c->uexp.p, c->uplan.p, c->uout.p, c->pref.p, c->recs.p, c->btres.p, c->ctsum.p};
         mix(ptrs, sizeof ptrs);
         mix(&c->tune, sizeof c->tune);

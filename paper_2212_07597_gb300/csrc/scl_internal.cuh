@@ -64,7 +64,8 @@ struct Unit {
     uint32_t trace;       // resident trace slot
     uint32_t bt;          // index of the trace within the batch
     uint32_t first, last; // first / last unit of its trace in this batch
-    uint32_t pad;
+    uint32_t lst_cap;     // reset-list slots per candidate run of the unit
+    uint64_t lst0;        // first reset-list slot of the unit (NL lists of lst_cap)
 };
 
 struct BTrace {           // one per trace present in the batch
@@ -93,6 +94,16 @@ struct UnitSum {          // lane-independent facts of a unit
 
 constexpr int RM = 32;    // leading resets kept per candidate, to let a walk merge into it
 
+// ---- reset lists: every reset of up to NL distinct candidate runs per unit, so the
+// exact replay of a unit whose true run has a complete list needs no crossing search
+constexpr int NL = 4;
+constexpr uint32_t NO_LIST = 0xffffffffu;
+struct SRes {
+    uint32_t pos;         // unit offset of the reset
+    uint32_t pad;
+    int64_t P;            // unit-local prefix sum of deltas up to and including pos
+};
+
 struct Cand {             // candidate k of unit u
     int64_t c0;           // its counter at the unit's first event
     int64_t c;            // its counter after the unit
@@ -103,6 +114,8 @@ struct Cand {             // candidate k of unit u
     int64_t tmax;         // largest prefix at a growth reset of index >= RM (INT64_MIN: none)
     uint32_t pos[RM];     // positions of its first RM resets
     int64_t gp[RM];       // their prefixes if growth resets, else INT64_MIN
+    uint32_t list;        // reset list holding all n resets (< NL), or NO_LIST
+    uint32_t pad;
 };
 
 struct Walk {             // one unit walked by k_chain from an exact counter
@@ -122,6 +135,8 @@ struct UnitTrue {         // the true trajectory through a unit (k_chain)
     uint32_t n;           // samples in the unit
     int64_t exit_c;       // counter after the unit
     int64_t exit_last;    // trace index of the last reset up to the unit's end (-1: none)
+    uint32_t list;        // reset list of the true run (NO_LIST: the exact replay searches)
+    uint32_t pad;
 };
 
 struct UnitPlan {         // per unit, from k_scan

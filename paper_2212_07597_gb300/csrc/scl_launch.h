@@ -13,6 +13,7 @@ struct LaunchSketch {
     int nbt;
     UnitSum *usum;
     Cand *cand;
+    SRes *lists;
     uint8_t *match;
     Walk *uwalk;
     UnitTrue *utrue;
@@ -33,6 +34,7 @@ struct LaunchFinal {
     int nunits;
     const UnitTrue *utrue;
     const UnitPlan *uplan;
+    const SRes *lists;
     FRec *recs;
     UnitOut *uout;
     int64_t T;

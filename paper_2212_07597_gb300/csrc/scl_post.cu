@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(NT) k_copy_scan(LaunchPost a) {
 
 constexpr int CPT = COPY_TILE / NT;   // memcpy events per thread
 
-constexpr uint32_t COPY_SMEM_LINES = 4096;   // per-line copy counts kept in shared memory up to this L
+constexpr uint32_t COPY_SMEM_LINES = 1024;   // per-line copy counts kept in shared memory up to this L
 
 // add a block's per-(line, flag) copy sample counts to the trace's rows and clear them;
 // copy bytes are samples * T_c, so only the counts are kept
@@ -458,8 +458,9 @@ __device__ __forceinline__ void copy_flush(unsigned long long *hist, uint32_t n_
 
 // Section 3.5: the copy counter before each tile (from k_copy_scan) plus the running
 // byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
-// Each block takes a contiguous range of tiles, so it meets few traces; its counts stay
-// in shared memory and reach the trace's rows once per trace it meets.  Each thread owns
+// With L <= 1,024 each block takes a contiguous range of tiles, so it meets few traces;
+// its counts stay in shared memory and reach the trace's rows once per trace it meets.
+// Larger line spaces count in global memory, one tile per block.  Each thread owns
 // CPT consecutive memcpys of a tile (sizes staged through shared memory, padded against
 // bank conflicts) and carries the remainder mod T_c, so a division is needed only for a
 // memcpy of at least 8 T_c.
@@ -660,8 +661,9 @@ cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s) {
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_copy_apply, NT, smem)) != cudaSuccess) return e;
-    // one wave of blocks, each a contiguous range of tiles
-    const int grid = std::max(1, std::min(a.nctiles, sms * std::max(1, per_sm)));
+    // with the table: one wave of blocks, each a contiguous range of tiles; without it
+    // (global counts): one tile per block, many blocks in flight
+    const int grid = sm_table ? std::max(1, std::min(a.nctiles, sms * std::max(1, per_sm))) : a.nctiles;
     k_copy_apply<<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -8,7 +8,10 @@
 //   - the filled slot's host->device copies go on the copy stream, and the replay of
 //     the batch (scl_replay_batch) waits for them on the compute stream, so the next
 //     batch's copies overlap the current batch's kernels (continuous batching: whatever
-//     arrived while the device was busy forms the next batch);
+//     arrived while the device was busy forms the next batch).  Arrays in pinned (or
+//     device) memory are gathered into the slot by one kernel per batch that reads them
+//     through their device addresses, instead of one copy call per array; pageable
+//     arrays are copied with cudaMemcpyAsync;
 //   - a slot is reused only after the event recorded behind its replay has completed,
 //     which is also when its requests' completion times are taken.
 // Segments of one process keep their arrival order: they are replayed in that order
@@ -25,6 +28,62 @@
 namespace {
 
 constexpr int NSLOT = 3;
+constexpr int NCOL = 7;   // event delta, addr, line, flag; memcpy size, line, flag
+
+struct GatherJob {
+    const void *src;   // device-accessible address
+    void *dst;
+    uint64_t bytes;
+};
+
+// one block per job at a time; 16-byte vectors (four in flight per thread) when both
+// ends and the size allow, else the widest element that does
+__global__ void __launch_bounds__(256) k_gather(const GatherJob *__restrict__ jobs, int njobs) {
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+        const GatherJob J = jobs[j];
+        const uintptr_t al = reinterpret_cast<uintptr_t>(J.src) | reinterpret_cast<uintptr_t>(J.dst) | J.bytes;
+        const uint64_t nt = blockDim.x;
+        if ((al & 15) == 0) {
+            const uint4 *src = static_cast<const uint4 *>(J.src);
+            uint4 *dst = static_cast<uint4 *>(J.dst);
+            const uint64_t nv = J.bytes / 16;
+            uint64_t i = threadIdx.x;
+            for (; i + 3 * nt < nv; i += 4 * nt) {
+                const uint4 r0 = src[i], r1 = src[i + nt], r2 = src[i + 2 * nt], r3 = src[i + 3 * nt];
+                dst[i] = r0;
+                dst[i + nt] = r1;
+                dst[i + 2 * nt] = r2;
+                dst[i + 3 * nt] = r3;
+            }
+            for (; i < nv; i += nt) dst[i] = src[i];
+        } else if ((al & 7) == 0) {
+            const uint64_t *src = static_cast<const uint64_t *>(J.src);
+            uint64_t *dst = static_cast<uint64_t *>(J.dst);
+            for (uint64_t i = threadIdx.x; i < J.bytes / 8; i += nt) dst[i] = src[i];
+        } else if ((al & 3) == 0) {
+            const uint32_t *src = static_cast<const uint32_t *>(J.src);
+            uint32_t *dst = static_cast<uint32_t *>(J.dst);
+            for (uint64_t i = threadIdx.x; i < J.bytes / 4; i += nt) dst[i] = src[i];
+        } else {
+            const uint8_t *src = static_cast<const uint8_t *>(J.src);
+            uint8_t *dst = static_cast<uint8_t *>(J.dst);
+            for (uint64_t i = threadIdx.x; i < J.bytes; i += nt) dst[i] = src[i];
+        }
+    }
+}
+
+// The address through which the device reads host array p, or nullptr when p is pageable
+// (or unknown) and must be copied by the copy engine.
+const void *device_view(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) return at.devicePointer;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+    return nullptr;
+}
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -36,6 +95,7 @@ size_t request_bytes(const scl_request &r) {
 struct Slot {
     void *dev = nullptr;
     size_t cap = 0, used = 0;
+    GatherJob *hjobs = nullptr, *djobs = nullptr;   // pinned table and its device copy
     std::vector<uint32_t> reqs;
     std::vector<scl_segment> segs;
     cudaEvent_t copied = nullptr, done = nullptr;
@@ -87,6 +147,8 @@ extern "C" int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, cons
     auto cleanup = [&]() {
         for (auto &sl : slots) {
             if (sl.dev) cudaFree(sl.dev);
+            if (sl.djobs) cudaFree(sl.djobs);
+            if (sl.hjobs) cudaFreeHost(sl.hjobs);
             if (sl.copied) cudaEventDestroy(sl.copied);
             if (sl.done) cudaEventDestroy(sl.done);
         }
@@ -99,7 +161,12 @@ extern "C" int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, cons
         return SCL_ECUDA;
     }
     for (auto &sl : slots) {
-        if (cudaMalloc(&sl.dev, slot_cap) != cudaSuccess) { cleanup(); return SCL_ENOMEM; }
+        if (cudaMalloc(&sl.dev, slot_cap) != cudaSuccess ||
+            cudaMalloc(&sl.djobs, sizeof(GatherJob) * NCOL * max_batch) != cudaSuccess ||
+            cudaMallocHost(&sl.hjobs, sizeof(GatherJob) * NCOL * max_batch) != cudaSuccess) {
+            cleanup();
+            return scl_ctx_fail(ctx, SCL_ENOMEM, "serve: staging slots");
+        }
         sl.cap = slot_cap;
         cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
@@ -134,18 +201,27 @@ extern "C" int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, cons
             else if (q != cudaErrorNotReady) rc = SCL_ECUDA;
         }
     };
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, scl_ctx_device(ctx)) != cudaSuccess) sms = 1;
     auto dispatch = [&](Slot &sl) -> int {
-        // copies on the copy stream, replay on the compute stream behind them
+        // pinned or device arrays: one gather kernel on the copy stream; pageable: copy calls
         char *p = static_cast<char *>(sl.dev);
+        int nj = 0;
         for (size_t k = 0; k < sl.reqs.size(); ++k) {
             const scl_request &r = reqs[sl.reqs[k]];
             scl_segment g;
             memset(&g, 0, sizeof g);
             g.trace_id = r.trace_id;
+            bool bad = false;
             auto put = [&](const void *src, size_t bytes) -> void * {
                 char *dst = p;
-                if (bytes && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess) return nullptr;
                 p += al256(bytes);
+                if (!bytes) return dst;
+                if (const void *dv = device_view(src)) {
+                    sl.hjobs[nj++] = GatherJob{dv, dst, bytes};
+                } else if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess) {
+                    bad = true;
+                }
                 return dst;
             };
             g.ev.n = r.ev.n;
@@ -157,11 +233,15 @@ extern "C" int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, cons
             g.cp.size = static_cast<const uint64_t *>(put(r.cp.size, r.cp.n * 8));
             g.cp.line = static_cast<const uint32_t *>(put(r.cp.line, r.cp.n * 4));
             g.cp.is_python = static_cast<const uint8_t *>(put(r.cp.is_python, r.cp.n));
-            if (!g.ev.delta || !g.ev.addr || !g.ev.line || !g.ev.is_python || !g.cp.size || !g.cp.line ||
-                !g.cp.is_python)
-                return SCL_ECUDA;
+            if (bad) return scl_ctx_fail(ctx, SCL_ECUDA, "serve: host-to-device copy");
             sl.segs.push_back(g);
             events += r.ev.n;
+        }
+        if (nj) {
+            if (cudaMemcpyAsync(sl.djobs, sl.hjobs, sizeof(GatherJob) * nj, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                return scl_ctx_fail(ctx, SCL_ECUDA, "serve: gather table upload");
+            k_gather<<<std::min(nj, sms * 8), 256, 0, cs>>>(sl.djobs, nj);
+            if (cudaGetLastError() != cudaSuccess) return scl_ctx_fail(ctx, SCL_ECUDA, "serve: gather launch");
         }
         if (cudaEventRecord(sl.copied, cs) != cudaSuccess) return SCL_ECUDA;
         if (cudaStreamWaitEvent(ks, sl.copied, 0) != cudaSuccess) return SCL_ECUDA;

@@ -64,8 +64,9 @@ using SketchRing = Ring<false, 4, 256, 8>;
 using ChainRing = Ring<false, 16, 512, 16>;   // a lone walker: 512-event steps, 8k events in flight
 
 __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
-                                                    Cand *cand, const DevTrace *traces, int64_t T, uint32_t warmup,
-                                                    unsigned *queue, ErrWord *err, unsigned long long spin) {
+                                                    Cand *cand, SRes *lists, const DevTrace *traces, int64_t T,
+                                                    uint32_t warmup, unsigned *queue, ErrWord *err,
+                                                    unsigned long long spin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     SketchRing &sm = reinterpret_cast<SketchRing *>(smem_raw)[warp];
@@ -108,6 +109,10 @@ __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ uni
         const unsigned same = __match_any_sync(FULL, (unsigned long long)c);
         const int leader = __ffs(same) - 1;
         const bool active = leader == lane;
+        // the first NL distinct runs record every reset (for the exact replay)
+        const uint32_t rank = (uint32_t)__popc(__ballot_sync(FULL, active) & ((1u << lane) - 1u));
+        const uint32_t myslot = active && rank < (uint32_t)NL ? rank : NO_LIST;
+        SRes *L = myslot != NO_LIST ? lists + U.lst0 + (uint64_t)myslot * U.lst_cap : nullptr;
         Cand *C = cand + (size_t)u * K + lane;
         uint32_t n = 0;
         int32_t last = -1;
@@ -129,6 +134,13 @@ __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ uni
                     } else if (growth && Pl > tmax) {
                         tmax = Pl;
                         targ = pos;
+                    }
+                    if (L && n < U.lst_cap) {
+                        SRes q;
+                        q.pos = pos;
+                        q.pad = 0;
+                        q.P = Pl;
+                        L[n] = q;
                     }
                     ++n;
                     last = (int32_t)pos;
@@ -159,6 +171,12 @@ __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ uni
         C->garg = __shfl_sync(FULL, garg, leader);
         C->tmax = __shfl_sync(FULL, tmax, leader);
         C->targ = __shfl_sync(FULL, targ, leader);
+        {
+            const uint32_t ls = __shfl_sync(FULL, myslot, leader);
+            const uint32_t nl = __shfl_sync(FULL, n, leader);
+            C->list = ls != NO_LIST && nl <= U.lst_cap ? ls : NO_LIST;
+            C->pad = 0;
+        }
         if (lane == 0) {
             UnitSum S;   // window totals are filled by k_totals, for the units that need them
             S.total = P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = umin; S.maxQ = umax;
@@ -195,15 +213,29 @@ struct ChainSmem {
 };
 
 // Walk unit U from counter c (one warp, through the bulk-copy ring) until one of its
-// resets is among the first RM resets of a candidate of the unit -- from there the run
-// is that candidate's -- or to the unit's end.  Lane j holds candidate j's positions.
-__device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const Cand *cu, int64_t c, int64_t T,
-                          int lane, unsigned long long spin, ErrWord *err) {
+// resets is also a reset of a candidate of the unit -- from there the run is that
+// candidate's -- or to the unit's end.  Lane j holds candidate j's first RM resets; lane
+// s < NL also follows reset list s (every reset of a candidate run, in order), so merges
+// after a candidate's first RM resets are found too.
+__device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const Cand *cu, const SRes *lists,
+                          int64_t c, int64_t T, int lane, unsigned long long spin, ErrWord *err) {
     Walk W;
     W.last = -1; W.n = 0; W.gmax = INT64_MIN; W.garg = 0; W.into = -1;
     uint32_t mypos[RM];
 #pragma unroll
     for (int r = 0; r < RM; ++r) mypos[r] = cu[lane].pos[r];
+    // list s: its owner (a candidate carrying it), length, and the next listed reset
+    const uint32_t mylist = cu[lane].list;
+    int owner = -1;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const unsigned o = __ballot_sync(FULL, mylist == (uint32_t)q);
+        if (lane == q) owner = o ? __ffs(o) - 1 : -1;
+    }
+    const SRes *Ls = lists + U.lst0 + (uint64_t)(lane < NL ? lane : 0) * U.lst_cap;
+    const uint32_t lcount = owner >= 0 ? cu[owner].n : 0;
+    uint32_t lp = 0;
+    uint32_t lnext = lcount ? Ls[0].pos : 0xffffffffu;
     int64_t P = 0;
     int mj = -1;
     uint32_t mi = 0;
@@ -236,6 +268,18 @@ __device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const
                 mi = (uint32_t)__shfl_sync(FULL, hit, mj);
                 return true;
             }
+            bool leq = false;
+            if (lane < NL && lcount) {
+                while (lnext < pos) lnext = ++lp < lcount ? Ls[lp].pos : 0xffffffffu;
+                leq = lnext == pos;
+            }
+            const unsigned m2 = __ballot_sync(FULL, leq);
+            if (m2) {
+                const int sl = __ffs(m2) - 1;
+                mj = __shfl_sync(FULL, owner, sl);
+                mi = __shfl_sync(FULL, lp, sl);
+                return true;
+            }
             b = -Qr;
             after = r;
         }
@@ -248,10 +292,28 @@ __device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const
         // the rest of the unit follows candidate mj from its reset mi on
         const Cand &Cj = cu[mj];
         W.n += Cj.n - (mi + 1);
-        int64_t sg = Cj.tmax;
-        uint32_t sa = Cj.targ;
-        for (int q = RM - 1; q > (int)mi; --q)
-            if (Cj.gp[q] != INT64_MIN && Cj.gp[q] >= sg) { sg = Cj.gp[q]; sa = Cj.pos[q]; }
+        int64_t sg = INT64_MIN;
+        uint32_t sa = 0;
+        if (mi + 1 < (uint32_t)RM || Cj.list == NO_LIST) {
+            sg = Cj.tmax;
+            sa = Cj.targ;
+            for (int q = RM - 1; q > (int)mi; --q)
+                if (Cj.gp[q] != INT64_MIN && Cj.gp[q] >= sg) { sg = Cj.gp[q]; sa = Cj.pos[q]; }
+        } else {
+            // the largest prefix at a growth reset after mi, from the list: the counter at
+            // reset r > 0 is P_r - P_(r-1)
+            const SRes *Lj = lists + U.lst0 + (uint64_t)Cj.list * U.lst_cap;
+            for (uint32_t r = mi + 1 + lane; r < Cj.n; r += 32) {
+                const SRes q = Lj[r];
+                if (q.P - Lj[r - 1].P > 0 && (q.P > sg || (q.P == sg && q.pos < sa))) { sg = q.P; sa = q.pos; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int64_t og = __shfl_xor_sync(FULL, sg, o);
+                const uint32_t oa = __shfl_xor_sync(FULL, sa, o);
+                if (og > sg || (og == sg && og != INT64_MIN && oa < sa)) { sg = og; sa = oa; }
+            }
+        }
         if (sg != INT64_MIN && sg > W.gmax) { W.gmax = sg; W.garg = sa; }
         W.last = Cj.last;
         W.c = Cj.c;
@@ -266,6 +328,7 @@ __device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const
 // MODE_TRANSPARENT / MODE_WALKED: an explicit counter (uexp) entered.
 __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, const BTrace *__restrict__ bts, int nbt,
                                              const UnitSum *__restrict__ usum, const Cand *__restrict__ cand,
+                                             const SRes *__restrict__ lists,
                                              const uint8_t *__restrict__ match, Walk *uwalk, UnitTrue *utrue,
                                              uint32_t *umode, int64_t *uexp, int64_t T, ErrWord *err,
                                              unsigned long long spin, unsigned long long *stats) {
@@ -329,7 +392,7 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
                 ec += S.total;
                 continue;
             }
-            const Walk W = walk_unit(sm.ring, phase, units[u], cand + (size_t)u * K, ec, T, lane, spin, err);
+            const Walk W = walk_unit(sm.ring, phase, units[u], cand + (size_t)u * K, lists, ec, T, lane, spin, err);
             if (lane == 0) {
                 uwalk[u] = W;
                 sm.mode[i] = (uint16_t)MODE_WALKED;
@@ -343,41 +406,41 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
         for (uint32_t i = lane; i < cn; i += 32) umode[B.u0 + c0 + i] = sm.mode[i];
         __syncwarp();
     }
-    __syncwarp();
-    // ---- phase B: every unit's true run from its entering mode
-    for (uint32_t i = lane; i < B.nu; i += 32) {
-        const uint32_t u = B.u0 + i;
-        const Unit &U = units[u];
-        const uint32_t md = umode[u];
-        UnitTrue Tu;
-        Tu.entry_last = -1;
-        if (md < (uint32_t)K) {
-            const Cand &C = cand[(size_t)u * K + md];
-            Tu.entry_c = C.c0; Tu.n = C.n; Tu.gmax = C.gmax; Tu.garg = C.garg; Tu.exit_c = C.c;
-            Tu.exit_last = C.last >= 0 ? (int64_t)(U.gidx0 + (uint32_t)C.last) : -1;
-        } else if (md == MODE_TRANSPARENT) {
-            Tu.entry_c = uexp[u]; Tu.n = 0; Tu.gmax = INT64_MIN; Tu.garg = 0;
-            Tu.exit_c = uexp[u] + usum[u].total; Tu.exit_last = -1;
-        } else {
-            const Walk &W = uwalk[u];
-            Tu.entry_c = uexp[u]; Tu.n = W.n; Tu.gmax = W.gmax; Tu.garg = W.garg; Tu.exit_c = W.c;
-            Tu.exit_last = W.last >= 0 ? (int64_t)(U.gidx0 + (uint32_t)W.last) : -1;
-        }
-        utrue[u] = Tu;
-    }
 }
 
 // ---------------------------------------------------------------- k_totals
-// Sum of mallocs, python mallocs and python deltas over a unit whose true run takes no
-// sample: such units lie inside one open window, whose totals k_scan assembles from
-// them.  Units that do sample are never needed whole and keep zeros.
-__global__ void k_totals(const Unit *__restrict__ units, int nunits, const UnitTrue *__restrict__ utrue,
-                         UnitSum *usum) {
+// One warp per unit.  First the unit's true run from its entering mode (k_chain):
+// a candidate's, an explicit counter that takes no sample, or k_chain's walk.  Then,
+// for a unit whose true run takes no sample, the sum of mallocs, python mallocs and
+// python deltas over it: such units lie inside one open window, whose totals k_scan
+// assembles from them.  Units that do sample are never needed whole and keep zeros.
+__global__ void k_totals(const Unit *__restrict__ units, int nunits, const Cand *__restrict__ cand,
+                         const uint32_t *__restrict__ umode, const Walk *__restrict__ uwalk,
+                         const int64_t *__restrict__ uexp, UnitTrue *utrue, UnitSum *usum) {
     const int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (u >= nunits) return;
-    if (utrue[u].n != 0) return;
     const Unit U = units[u];
+    const uint32_t md = umode[u];
+    UnitTrue Tu;
+    Tu.entry_last = -1;
+    Tu.list = NO_LIST;
+    Tu.pad = 0;
+    if (md < (uint32_t)K) {
+        const Cand &C = cand[(size_t)u * K + md];
+        Tu.entry_c = C.c0; Tu.n = C.n; Tu.gmax = C.gmax; Tu.garg = C.garg; Tu.exit_c = C.c;
+        Tu.list = C.list;
+        Tu.exit_last = C.last >= 0 ? (int64_t)(U.gidx0 + (uint32_t)C.last) : -1;
+    } else if (md == MODE_TRANSPARENT) {
+        Tu.entry_c = uexp[u]; Tu.n = 0; Tu.gmax = INT64_MIN; Tu.garg = 0;
+        Tu.exit_c = uexp[u] + usum[u].total; Tu.exit_last = -1;
+    } else {
+        const Walk &W = uwalk[u];
+        Tu.entry_c = uexp[u]; Tu.n = W.n; Tu.gmax = W.gmax; Tu.garg = W.garg; Tu.exit_c = W.c;
+        Tu.exit_last = W.last >= 0 ? (int64_t)(U.gidx0 + (uint32_t)W.last) : -1;
+    }
+    if (lane == 0) utrue[u] = Tu;
+    if (Tu.n != 0) return;
     int64_t a = 0, ap = 0, sp = 0;
     for (uint64_t e = lane; e < U.len; e += 32) {
         const int64_t x = U.delta[e];
@@ -393,7 +456,7 @@ __global__ void k_totals(const Unit *__restrict__ units, int nunits, const UnitT
 
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s) {
-    k_totals<<<(a.nunits + 7) / 8, 256, 0, s>>>(a.units, a.nunits, a.utrue, a.usum);
+    k_totals<<<(a.nunits + 7) / 8, 256, 0, s>>>(a.units, a.nunits, a.cand, a.umode, a.uwalk, a.uexp, a.utrue, a.usum);
     return cudaGetLastError();
 }
 
@@ -401,8 +464,8 @@ cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s) {
     const size_t smem = sizeof(SketchRing) * a.warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.traces, a.T,
-                                                            a.warmup, a.queue, a.err, a.spin);
+    k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.lists, a.traces,
+                                                            a.T, a.warmup, a.queue, a.err, a.spin);
     return cudaGetLastError();
 }
 
@@ -417,7 +480,7 @@ cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s) {
     const size_t smem = sizeof(ChainSmem);
     cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chain<<<a.nbt, 32, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.match, a.uwalk, a.utrue, a.umode,
+    k_chain<<<a.nbt, 32, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.lists, a.match, a.uwalk, a.utrue, a.umode,
                                     a.uexp, a.T, a.err, a.spin, a.stats);
     return cudaGetLastError();
 }

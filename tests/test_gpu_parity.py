@@ -250,3 +250,27 @@ def test_autotune_restores_state_and_keeps_results_exact():
     scl.scl_replay_batch(ctx, [seg])
     scl.scl_sync(ctx)
     assert_same(ctx, 0, oracle_of(tr, 1_048_573), samples=False)
+
+
+@pytest.mark.parametrize("T", tg.SWEEP_THRESHOLDS)
+def test_sweep_families_one_batch(T):
+    # the threshold sweep's four families (plain with 4 GiB mallocs, adversarial +-(T-1),
+    # malloc-only 4 KiB, free-heavy with address reuse), two traces each, in one batch
+    n = 120_000
+    trs = [tg.sweep_trace(i, T, n=n) for i in range(8)]
+    shift = 0 if T == 1 else 4
+    ctx = gpu_ctx(T, max_traces=len(trs), shift=shift, log_cap=n + 1, unit=16384)
+    keep = replay(ctx, list(enumerate(trs)))
+    for i, tr in enumerate(trs):
+        assert_same(ctx, i, oracle_of(tr, T))
+
+
+def test_long_trace_all_samples_exact():
+    # the long-trace generators (five leaking lines, a ramp) at 2^25 events, default tuning
+    tr = tg.long_trace(1 << 25)
+    ctx = gpu_ctx(T0, log_cap=1 << 20)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T0))
+    # the warm-up candidates carry the true counter into almost every unit
+    st = scl.scl_batch_stats(ctx)
+    assert st["walked"] <= max(4, st["units"] // 8), st

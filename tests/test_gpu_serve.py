@@ -16,9 +16,11 @@ T0 = tg.T_PLAIN
 NL = 1024
 
 
-def _workload(n_proc, n_seg, seg_len, seed=7, mean_gap_ns=20_000):
+def _workload(n_proc, n_seg, seg_len, seed=7, mean_gap_ns=20_000, pinned=False):
     """Processes cut into seg_len-event requests; request order = Poisson arrival order,
-    the process of each arrival drawn at random (seeded), its segments in order."""
+    the process of each arrival drawn at random (seeded), its segments in order.  With
+    pinned, the request arrays live in page-locked host memory (gathered by a kernel),
+    else in pageable memory (copied by the copy engine)."""
     procs = [tg.serving_process(p, n_seg * seg_len, seed=seed, n_lines=NL) for p in range(n_proc)]
     rng = np.random.default_rng(seed)
     owner = rng.permutation(np.repeat(np.arange(n_proc), n_seg))
@@ -31,14 +33,20 @@ def _workload(n_proc, n_seg, seg_len, seed=7, mean_gap_ns=20_000):
         m0, m1 = k * seg_len // 10, (k + 1) * seg_len // 10
         s = procs[p].slice(k * seg_len, (k + 1) * seg_len, m0, m1)
         arrays = [np.ascontiguousarray(x) for x in (s.delta, s.addr, s.line, s.is_python, s.csize, s.cline, s.cpy)]
+        if pinned:
+            import torch
+            arrays = [torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else
+                                       x.view(np.int32) if x.dtype == np.uint32 else x).pin_memory().numpy()
+                      for x in arrays]
         keep.append(arrays)
         reqs.append(scl.request(int(p), int(arr[i]), *arrays))
     return procs, reqs, keep, owner
 
 
-def test_alone_equals_in_the_mix_and_oracle():
+@pytest.mark.parametrize("pinned", [False, True])
+def test_alone_equals_in_the_mix_and_oracle(pinned):
     n_proc, n_seg, seg_len = 24, 4, 16384
-    procs, reqs, keep, owner = _workload(n_proc, n_seg, seg_len)
+    procs, reqs, keep, owner = _workload(n_proc, n_seg, seg_len, pinned=pinned)
     mix = gpu_ctx(T0, n_lines=NL, max_traces=n_proc, log_cap=1 << 16, unit=16384)
     res, summ = scl.scl_serve(mix, reqs, max_batch=8, realtime=True)
     assert summ["requests"] == len(reqs) and summ["events"] == n_proc * n_seg * seg_len
