@@ -241,6 +241,7 @@ typedef struct {
     uint64_t explicit_entries;  /* units entered with a counter no candidate carried */
     uint64_t transparent;       /* ... of which held no sample (skipped in O(1)) */
     uint64_t unit_events;       /* tuned events per unit (0: sized per batch) */
+    uint64_t walked_events;     /* events the chain's walks covered before merging (or to the unit end) */
 } scl_batch_info;
 int scl_batch_stats(scl_ctx *ctx, scl_batch_info *out);
 

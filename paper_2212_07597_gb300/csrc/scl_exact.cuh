@@ -1,0 +1,237 @@
+// scl_exact.cuh -- the exact replay of one unit from a known entering state (one warp).
+//
+// Per event (Sections 3.2-3.4): c <- c + delta and the open window's totals A, F,
+// A_py, F_py grow; a free compares its address with the tracked block; when
+// |c| >= T a sample closes the window (kind, totals, footprint, line and flag of
+// the triggering event), and a growth sample whose footprint beats the high-water
+// mark sets a new mark and starts tracking the sampled block.
+//
+// 256 events per step.  delta, the python flag and the address are staged through the
+// bulk-copy ring; the line id is read only at the events that trigger a sample.  When
+// the unit's resets are known in advance (a reset list from k_sketch) no crossing
+// search runs; otherwise each step's prefix sums locate the crossings.
+//
+// Used by k_final for every unit whose entry k_chain resolved, and by k_sketch for the
+// first unit of each trace in a batch, whose entry is the trace's resident state; that
+// caller also wants the facts k_sketch records for a candidate run (FIRST = true).
+#pragma once
+#include "scl_stage.cuh"
+
+namespace scl {
+
+struct ExactIn {                 // the state entering the unit
+    int64_t c;                   // counter
+    int64_t wA, wApy, wSpy;      // this lane's share of the open-window totals so far
+    int64_t mark;                // high-water mark
+    int64_t fpb;                 // footprint before the unit
+    uint32_t tk;                 // tracked block: 0 none, 1/2 entering (see UnitPlan), 3 own sample
+    uint64_t taddr;
+    const SRes *list;            // the unit's resets in order, or nullptr: search
+    uint32_t nres;               // resets listed
+    int64_t exit_c;              // counter after the unit (with a list)
+};
+
+struct ExactRun {                // FIRST only: the run's facts, as k_sketch records them
+    Cand *C0;                    // lane 0 writes the first RM reset positions and growth
+                                 // prefixes here (the unit's candidate 0)
+    int64_t gmax, tmax;          // largest prefix at a growth reset (all / index >= RM)
+    uint32_t garg, targ;
+    int32_t last;                // last reset position (-1: none)
+    int64_t P;                   // unit total
+    int64_t umax, umin;          // extremes of the unit-local prefix
+};
+
+// Replays unit U; writes its records to out[0 .. cap) and returns false if a wait timed
+// out.  n (records taken), enter_hit and the state after the unit are returned.
+template <bool FIRST, class RingT>
+__device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const ExactIn &in0, FRec *out, uint32_t cap,
+                           int64_t T, unsigned long long spin, ErrWord *err, int lane, uint32_t &n_out,
+                           UnitOut &O, ExactRun *R) {
+    constexpr int E = RingT::kE, STEP = 32 * E;
+    int64_t accA = in0.wA, accApy = in0.wApy, accSpy = in0.wSpy;
+    int64_t c = in0.c;
+    int64_t P = 0;
+    int64_t mark = in0.mark;
+    const int64_t fpb = in0.fpb;
+    uint32_t tk = in0.tk;
+    uint64_t taddr = in0.taddr;
+    uint32_t tslot = 0;
+    uint32_t enter_hit = 0;
+    uint32_t n = 0;
+    // FIRST: the run's facts (lane-uniform except the extremes, reduced at the end)
+    int64_t gmax = INT64_MIN, tmax = INT64_MIN, umax = INT64_MIN, umin = INT64_MAX;
+    uint32_t garg = 0, targ = 0;
+    int32_t last = -1;
+
+    auto hit_tracked = [&]() {
+        if (tk == 3) {
+            if (lane == 0 && tslot < cap) out[tslot].recl = 1;
+        } else {
+            enter_hit = 1;
+        }
+    };
+    auto add_events = [&](const StepIn<E> &in, int after, int upto, int64_t &sA, int64_t &sApy, int64_t &sSpy) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int pos = lane * E + k;
+            if (pos > after && pos <= upto) {
+                const int64_t x = in.d[k];
+                const int64_t ps = x > 0 ? x : 0;
+                sA += ps;
+                if (py_of(in, k)) { sApy += ps; sSpy += x; }
+            }
+        }
+    };
+    auto frees_hit = [&](const StepIn<E> &in, int after, int upto) -> bool {
+        bool h = false;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int pos = lane * E + k;
+            h |= pos > after && pos <= upto && in.d[k] < 0 && in.a[k] == taddr;
+        }
+        return __any_sync(FULL, h);
+    };
+    // every event of the step joins the open window (no sample in it)
+    auto whole_step = [&](const StepIn<E> &in) {
+        bool h = false;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int64_t x = in.d[k];
+            h |= x < 0 && in.a[k] == taddr;
+            const int64_t ps = x > 0 ? x : 0;
+            accA += ps;
+            if (py_of(in, k)) { accApy += ps; accSpy += x; }
+        }
+        if (tk && __any_sync(FULL, h)) hit_tracked();
+    };
+    // the sample at step position r (frees up to it already tested): counter cr there,
+    // unit-local prefix Pr there
+    auto close = [&](const StepIn<E> &in, int after, int r, uint32_t rel0, int64_t cr, int64_t Pr) {
+        int64_t sA = accA, sApy = accApy, sSpy = accSpy;
+        add_events(in, after, r, sA, sApy, sSpy);
+        const int64_t wA = warp_sum(sA), wApy = warp_sum(sApy), wSpy = warp_sum(sSpy);
+        const int fl = r / E, kf = r % E;
+        uint64_t av = in.a[0];
+        uint32_t pyv = py_of(in, 0);
+#pragma unroll
+        for (int k = 1; k < E; ++k)
+            if (k == kf) { av = in.a[k]; pyv = py_of(in, k); }
+        av = __shfl_sync(FULL, av, fl);
+        pyv = __shfl_sync(FULL, pyv, fl);
+        const int64_t fp = fpb + Pr;
+        const bool growth = cr > 0;
+        const bool hwm = growth && fp > mark;
+        const uint32_t rel = rel0 + (uint32_t)r;
+        if (lane == 0 && n < cap) {
+            FRec Rr;
+            Rr.rel = rel;
+            Rr.line = U.line[rel];
+            Rr.kind = growth ? 1 : -1;
+            Rr.is_hwm = hwm ? 1 : 0;
+            Rr.recl = 0;
+            Rr.py = pyv ? 1 : 0;
+            Rr.pad = 0;
+            Rr.A = wA; Rr.F = wA - cr; Rr.A_py = wApy; Rr.F_py = wApy - wSpy; Rr.P = Pr;
+            out[n] = Rr;
+        }
+        if (FIRST) {
+            if (lane == 0 && n < (uint32_t)RM) { R->C0->pos[n] = rel; R->C0->gp[n] = growth ? Pr : INT64_MIN; }
+            if (growth && n >= (uint32_t)RM && Pr > tmax) { tmax = Pr; targ = rel; }
+            if (growth && Pr > gmax) { gmax = Pr; garg = rel; }
+            last = (int32_t)rel;
+        }
+        if (hwm) { mark = fp; tk = 3; taddr = av; tslot = n; }
+        ++n;
+        accA = accApy = accSpy = 0;
+    };
+
+    bool ok;
+    if (!FIRST && in0.list) {
+        // ---- the resets are known: no crossing search
+        const SRes *Ls = in0.list;
+        const uint32_t nres = in0.nres;
+        uint32_t ri = 0;
+        uint32_t npos = 0xffffffffu;
+        int64_t nP = 0;
+        if (nres) { const SRes q = Ls[0]; npos = q.pos; nP = q.P; }
+        int64_t cst = c, Pprev = 0;   // counter at the open window's start, prefix there
+        auto kstep = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+            if (npos >= rel0 + (uint32_t)STEP) {
+                whole_step(in);
+                return false;
+            }
+            int after = -1;
+            while (npos < rel0 + (uint32_t)STEP) {
+                if (npos < rel0 + (uint32_t)(after + 1)) {   // positions must increase
+                    if (lane == 0) set_error(err, E_INTERNAL, 12, (unsigned long long)U.gidx0);
+                    npos = 0xffffffffu;
+                    break;
+                }
+                const int r = (int)(npos - rel0);
+                if (tk && frees_hit(in, after, r)) hit_tracked();
+                close(in, after, r, rel0, cst + (nP - Pprev), nP);
+                cst = 0;
+                Pprev = nP;
+                after = r;
+                if (++ri < nres) {
+                    const SRes q = Ls[ri];
+                    npos = q.pos;
+                    nP = q.P;
+                } else {
+                    npos = 0xffffffffu;
+                }
+            }
+            if (tk && frees_hit(in, after, STEP)) hit_tracked();
+            add_events(in, after, STEP, accA, accApy, accSpy);
+            return false;
+        };
+        ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, kstep);
+        c = in0.exit_c;
+    } else {
+        // ---- search for the crossings from the entry counter
+        auto step = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+            StepPrefix<E> sp;
+            step_prefix(in, lane, sp, sm.xq);
+            if (FIRST) {
+                umax = P + sp.lmax > umax ? P + sp.lmax : umax;
+                umin = P + sp.lmin < umin ? P + sp.lmin : umin;
+            }
+            if (__ballot_sync(FULL, c + sp.lmax >= T || c + sp.lmin <= -T) == 0) {
+                whole_step(in);
+                c += sp.tot;
+                P += sp.tot;
+                return false;
+            }
+            int64_t b = c;
+            int after = -1;
+            while (true) {
+                int64_t Qr;
+                const int r = first_cross(sp, sm.xq, lane, b, T, after, Qr);
+                // frees up to and including the sample's event see the block tracked so far
+                if (tk && frees_hit(in, after, r < 0 ? STEP : r)) hit_tracked();
+                if (r < 0) break;
+                close(in, after, r, rel0, b + Qr, P + Qr);
+                b = -Qr;
+                after = r;
+            }
+            add_events(in, after, STEP, accA, accApy, accSpy);
+            c = b + sp.tot;
+            P += sp.tot;
+            return false;
+        };
+        ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, step);
+    }
+    const int64_t a = warp_sum(accA), ap = warp_sum(accApy), spy = warp_sum(accSpy);
+    O.count = n;
+    O.enter_hit = enter_hit;
+    O.c = c; O.A = a; O.F = a - c; O.Apy = ap; O.Fpy = ap - spy;
+    n_out = n;
+    if (FIRST) {
+        R->gmax = gmax; R->garg = garg; R->tmax = tmax; R->targ = targ; R->last = last; R->P = P;
+        R->umax = warp_max(umax);
+        R->umin = warp_min(umin);
+    }
+    return ok;
+}
+
+}  // namespace scl

@@ -204,7 +204,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     }
     CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * q.nbt, s), "memset");
     CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
-    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 4, s), "memset");
+    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 5, s), "memset");
 
     const Unit *d_units = reinterpret_cast<const Unit *>(dp + q.o_units);
     const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + q.o_bts);
@@ -220,6 +220,8 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         k.usum = static_cast<UnitSum *>(c->usum.p);
         k.cand = static_cast<Cand *>(c->cand.p);
         k.lists = static_cast<SRes *>(c->lists.p);
+        k.recs = static_cast<FRec *>(c->recs.p);
+        k.uout = static_cast<UnitOut *>(c->uout.p);
         k.match = static_cast<uint8_t *>(c->match.p);
         k.uwalk = static_cast<Walk *>(c->uwalk.p);
         k.utrue = static_cast<UnitTrue *>(c->utrue.p);
@@ -416,8 +418,8 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMalloc(&c->errw, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaMalloc(&c->scores, sizeof(scl_leak_score) * L);
     if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(unsigned) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(unsigned long long) * 4);
-    if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(unsigned long long) * 5);
+    if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * 5);
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -740,13 +742,15 @@ int scl_line_stats(scl_ctx *c, uint32_t trace, scl_line_stat *out, uint32_t cap,
     std::vector<LineRow> rows(L);
     CK(cudaMemcpy(rows.data(), c->lines + (uint64_t)trace * L, sizeof(LineRow) * L, cudaMemcpyDeviceToHost),
        "read line stats");
+    // copy bytes are samples * T_c (Section 3.5): formed here, not kept on the device
+    const uint64_t Tc = (uint64_t)c->cfg.copy_multiple * (uint64_t)c->cfg.threshold;
     for (uint32_t l = 0; l < L; ++l) {
         scl_line_stat &o = out[l];
         const LineRow &x = rows[l];
         o.n_growth = x.n_growth; o.n_shrink = x.n_shrink;
         o.A = x.A; o.F = x.F; o.A_py = x.A_py; o.F_py = x.F_py; o.net = x.net;
         o.copy_samples[0] = x.copy_samples[0]; o.copy_samples[1] = x.copy_samples[1];
-        o.copy_bytes[0] = x.copy_bytes[0]; o.copy_bytes[1] = x.copy_bytes[1];
+        o.copy_bytes[0] = x.copy_samples[0] * Tc; o.copy_bytes[1] = x.copy_samples[1] * Tc;
     }
     return SCL_OK;
 }
@@ -881,7 +885,7 @@ int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
     if (!c || !out) return SCL_EINVAL;
     int r = sync_and_check(c);
     if (r) return r;
-    unsigned long long v[4];
+    unsigned long long v[5];
     CK(cudaMemcpy(v, c->stats, sizeof v, cudaMemcpyDeviceToHost), "read batch stats");
     memset(out, 0, sizeof *out);
     out->units = c->last_units;
@@ -890,6 +894,7 @@ int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
     out->explicit_entries = v[2];
     out->transparent = v[3];
     out->unit_events = c->tune.unit_events;
+    out->walked_events = v[4];
     return SCL_OK;
 }
 

@@ -38,7 +38,7 @@ struct DevTrace {                   // one per trace slot
 struct LineRow {                    // one per (trace, line); same field order as scl_line_stat + leak pair
     unsigned long long n_growth, n_shrink;
     long long A, F, A_py, F_py, net;
-    unsigned long long copy_samples[2], copy_bytes[2];
+    unsigned long long copy_samples[2], copy_bytes[2];   // copy_bytes unused (samples * T_c at query)
     unsigned long long mallocs, frees;
 };
 constexpr int LINE_WORDS = 13;
@@ -125,6 +125,7 @@ struct Walk {             // one unit walked by k_chain from an exact counter
     int64_t gmax;
     uint32_t garg;
     int32_t into;         // candidate of the unit the walk merged into (-1: none)
+    uint32_t walked;      // events walked (to the merge, or the whole unit)
 };
 
 struct UnitTrue {         // the true trajectory through a unit (k_chain)
@@ -232,6 +233,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// an mbarrier whose memory is about to hold something else (no operation may be pending)
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init() {

@@ -14,6 +14,8 @@ struct LaunchSketch {
     UnitSum *usum;
     Cand *cand;
     SRes *lists;
+    FRec *recs;          // first units: their records and outputs (k_sketch replays them exactly)
+    UnitOut *uout;
     uint8_t *match;
     Walk *uwalk;
     UnitTrue *utrue;
@@ -25,7 +27,7 @@ struct LaunchSketch {
     unsigned *queue;     // [0] sketch, [2] final
     ErrWord *err;
     unsigned long long spin;
-    unsigned long long *stats;   // [walked, walked and merged, explicit entries, transparent]
+    unsigned long long *stats;   // [walked, walked and merged, explicit entries, transparent, events walked]
     int blocks, warps_per_block, num_sms;
 };
 

@@ -439,90 +439,61 @@ __global__ void __launch_bounds__(NT) k_copy_scan(LaunchPost a) {
 
 constexpr int CPT = COPY_TILE / NT;   // memcpy events per thread
 
-constexpr uint32_t COPY_SMEM_LINES = 1024;   // per-line copy counts kept in shared memory up to this L
+constexpr uint32_t COPY_HOT_LINES = 1024;   // lines counted in shared memory per tile
 
-// add a block's per-(line, flag) copy sample counts to the trace's rows and clear them;
-// copy bytes are samples * T_c, so only the counts are kept
-__device__ __forceinline__ void copy_flush(unsigned long long *hist, uint32_t n_lines, LineRow *row,
-                                           unsigned long long Tc) {
-    for (uint32_t i = threadIdx.x; i < 2 * n_lines; i += NT) {
-        const unsigned long long v = hist[i];
-        if (v) {
-            const uint32_t l = i >> 1, f = i & 1;
-            atomicAdd(&row[l].copy_samples[f], v);
-            atomicAdd(&row[l].copy_bytes[f], v * Tc);
-            hist[i] = 0;
-        }
-    }
-}
-
-// Section 3.5: the copy counter before each tile (from k_copy_scan) plus the running
-// byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
-// With L <= 1,024 each block takes a contiguous range of tiles, so it meets few traces;
-// its counts stay in shared memory and reach the trace's rows once per trace it meets.
-// Larger line spaces count in global memory, one tile per block.  Each thread owns
-// CPT consecutive memcpys of a tile (sizes staged through shared memory, padded against
-// bank conflicts) and carries the remainder mod T_c, so a division is needed only for a
-// memcpy of at least 8 T_c.
+// Section 3.5 per tile: the copy counter before the tile (from k_copy_scan) plus the
+// running byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
+// Only the sample counts are kept (copy bytes = samples * T_c, formed by the query).
+// Counts of lines below 1,024 -- with skewed line use, nearly all of them -- gather in
+// shared memory and reach the trace's rows once per tile; higher lines count in global
+// memory directly.  Each thread owns CPT consecutive memcpys (sizes staged through shared
+// memory, padded against bank conflicts) and carries the remainder mod T_c, so a division
+// is needed only once per thread and for a memcpy of at least 8 T_c.
 __global__ void __launch_bounds__(NT) k_copy_apply(LaunchPost a) {
-    extern __shared__ __align__(16) unsigned long long chist[];   // [n_lines][2]: samples, by flag
+    extern __shared__ __align__(16) unsigned long long chist[];   // [hot lines][2]: samples, by flag
     __shared__ unsigned long long ssz[COPY_TILE + COPY_TILE / CPT];
     __shared__ int64_t sh[NT / 32 + 1];
-    const bool use_smem = a.n_lines <= COPY_SMEM_LINES;
-    const int t0 = (int)((int64_t)blockIdx.x * a.nctiles / gridDim.x);
-    const int t1 = (int)((int64_t)(blockIdx.x + 1) * a.nctiles / gridDim.x);
-    if (use_smem)
-        for (uint32_t i = threadIdx.x; i < 2 * a.n_lines; i += NT) chist[i] = 0;
+    const CopyTile C = a.ctiles[blockIdx.x];
+    const BTrace &B = a.bts[C.bt];
+    const uint32_t hot = a.n_lines < COPY_HOT_LINES ? a.n_lines : COPY_HOT_LINES;
+    for (uint32_t i = threadIdx.x; i < 2 * hot; i += NT) chist[i] = 0;
+    for (uint32_t j = threadIdx.x; j < COPY_TILE; j += NT) ssz[j + j / CPT] = j < C.len ? C.size[j] : 0ull;
+    __syncthreads();
     const unsigned long long Tc = a.Tc;
-    int cur = -1;   // batch trace whose counts the table holds
-    for (int t = t0; t < t1; ++t) {
-        const CopyTile C = a.ctiles[t];
-        __syncthreads();   // the previous tile's sizes and counts are done with
-        if (use_smem && cur >= 0 && (int)C.bt != cur) {
-            copy_flush(chist, a.n_lines, a.lines + (uint64_t)a.bts[cur].trace * a.n_lines, Tc);
-            __syncthreads();
-        }
-        cur = (int)C.bt;
-        for (uint32_t j = threadIdx.x; j < COPY_TILE; j += NT) ssz[j + j / CPT] = j < C.len ? C.size[j] : 0ull;
-        __syncthreads();
-        const uint32_t j0 = threadIdx.x * CPT;
-        const unsigned long long *mine = &ssz[j0 + threadIdx.x];
-        unsigned long long loc = 0;
+    const uint32_t j0 = threadIdx.x * CPT;
+    const unsigned long long *mine = &ssz[j0 + threadIdx.x];
+    unsigned long long loc = 0;
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) loc += mine[k];
-        int64_t tot;
-        const uint64_t ex = (uint64_t)block_excl_sum((int64_t)loc, sh, &tot);
-        const uint64_t start = a.ctile_sum[t] + ex;   // bytes counted before this thread's first memcpy
-        unsigned long long rem = start % Tc;
-        LineRow *grow = a.lines + (uint64_t)a.bts[C.bt].trace * a.n_lines;
-        for (int k = 0; k < CPT; ++k) {
-            const uint32_t j = j0 + k;
-            if (j >= C.len) break;
-            const unsigned long long sz = mine[k];
-            unsigned long long q;
-            if (sz >= 8 * Tc) {
-                q = (rem + sz) / Tc;
-                rem = (rem + sz) % Tc;
-            } else {
-                rem += sz;
-                q = 0;
-                while (rem >= Tc) { rem -= Tc; ++q; }
-            }
-            if (!q) continue;
-            const uint32_t line = C.line[j];
-            if (line >= a.n_lines) { set_error(a.err, E_RANGE, line, j); continue; }
-            const int f = C.py[j] ? 1 : 0;
-            if (use_smem) {
-                atomicAdd(&chist[line * 2 + f], q);
-            } else {
-                atomicAdd(&grow[line].copy_samples[f], q);
-                atomicAdd(&grow[line].copy_bytes[f], q * Tc);
-            }
+    for (int k = 0; k < CPT; ++k) loc += mine[k];
+    int64_t tot;
+    const uint64_t ex = (uint64_t)block_excl_sum((int64_t)loc, sh, &tot);
+    const uint64_t start = a.ctile_sum[blockIdx.x] + ex;   // bytes counted before this thread's first memcpy
+    unsigned long long rem = start % Tc;
+    LineRow *grow = a.lines + (uint64_t)B.trace * a.n_lines;
+    for (int k = 0; k < CPT; ++k) {
+        const uint32_t j = j0 + k;
+        if (j >= C.len) break;
+        const unsigned long long sz = mine[k];
+        unsigned long long q;
+        if (sz >= 8 * Tc) {
+            q = (rem + sz) / Tc;
+            rem = (rem + sz) % Tc;
+        } else {
+            rem += sz;
+            q = 0;
+            while (rem >= Tc) { rem -= Tc; ++q; }
         }
+        if (!q) continue;
+        const uint32_t line = C.line[j];
+        if (line >= a.n_lines) { set_error(a.err, E_RANGE, line, j); continue; }
+        const int f = C.py[j] ? 1 : 0;
+        if (line < hot) atomicAdd(&chist[2 * line + f], q);
+        else atomicAdd(&grow[line].copy_samples[f], q);
     }
-    if (use_smem && cur >= 0) {
-        __syncthreads();
-        copy_flush(chist, a.n_lines, a.lines + (uint64_t)a.bts[cur].trace * a.n_lines, Tc);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < 2 * hot; i += NT) {
+        const unsigned long long v = chist[i];
+        if (v) atomicAdd(&grow[i >> 1].copy_samples[i & 1], v);
     }
 }
 
@@ -653,18 +624,10 @@ cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s) {
 
 cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s) {
     if (!a.nctiles) return cudaSuccess;
-    const bool sm_table = a.n_lines <= COPY_SMEM_LINES;
-    const size_t smem = sm_table ? (size_t)a.n_lines * 2 * 8 : 0;
+    const size_t smem = (size_t)std::min(a.n_lines, COPY_HOT_LINES) * 2 * 8;
     cudaError_t e = cudaFuncSetAttribute(k_copy_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem ? smem : 1));
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_copy_apply, NT, smem)) != cudaSuccess) return e;
-    // with the table: one wave of blocks, each a contiguous range of tiles; without it
-    // (global counts): one tile per block, many blocks in flight
-    const int grid = sm_table ? std::max(1, std::min(a.nctiles, sms * std::max(1, per_sm))) : a.nctiles;
-    k_copy_apply<<<grid, NT, smem, s>>>(a);
+    k_copy_apply<<<a.nctiles, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 

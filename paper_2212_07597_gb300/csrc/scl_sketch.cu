@@ -20,8 +20,8 @@
 // k_chain   one warp per trace: follows the true candidate from unit to unit through
 //           the match table in shared memory; where no candidate carries the true
 //           counter it walks the unit itself.
+#include "scl_exact.cuh"
 #include "scl_launch.h"
-#include "scl_stage.cuh"
 
 namespace scl {
 
@@ -61,15 +61,17 @@ __device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, i
 
 // ---------------------------------------------------------------- k_sketch
 using SketchRing = Ring<false, 4, 256, 8>;
+using FirstRing = Ring<true, 2, 256, 8>;       // the first unit of a trace: its exact replay
+constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing) > sizeof(FirstRing) ? sizeof(SketchRing) : sizeof(FirstRing);
 using ChainRing = Ring<false, 16, 512, 16>;   // a lone walker: 512-event steps, 8k events in flight
 
 __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
-                                                    Cand *cand, SRes *lists, const DevTrace *traces, int64_t T,
-                                                    uint32_t warmup, unsigned *queue, ErrWord *err,
-                                                    unsigned long long spin) {
+                                                    Cand *cand, SRes *lists, FRec *recs, UnitOut *uout,
+                                                    const DevTrace *traces, int64_t T, uint32_t warmup,
+                                                    unsigned *queue, ErrWord *err, unsigned long long spin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SketchRing &sm = reinterpret_cast<SketchRing *>(smem_raw)[warp];
+    SketchRing &sm = *reinterpret_cast<SketchRing *>(smem_raw + (size_t)warp * SKETCH_WARP_SMEM);
     ring_init(sm, lane);
     uint32_t phase = 0;
     while (true) {
@@ -81,8 +83,55 @@ __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ uni
         bool ok = true;
         int64_t c;
         if (U.first) {
-            c = traces[U.trace].c;   // the exact counter: every lane runs it, lane 0 leads
-        } else {
+            // The trace's resident state is this unit's exact entry: replay it exactly now
+            // (k_final skips it) and record the run as every lane's candidate.
+            ring_release(sm, lane);
+            FirstRing &fr = *reinterpret_cast<FirstRing *>(&sm);
+            ring_init(fr, lane);
+            uint32_t fphase = 0;
+            const DevTrace st = traces[U.trace];
+            ExactIn in0;
+            in0.c = st.c;
+            in0.wA = lane == 0 ? st.A : 0;
+            in0.wApy = lane == 0 ? st.A_py : 0;
+            in0.wSpy = lane == 0 ? st.A_py - st.F_py : 0;
+            in0.mark = st.hwm;
+            in0.fpb = st.footprint;
+            in0.tk = st.tracked_valid ? 2u : 0u;   // as k_scan plans a trace's first unit
+            in0.taddr = st.tracked_addr;
+            in0.list = nullptr;
+            in0.nres = 0;
+            in0.exit_c = 0;
+            ExactRun R;
+            R.C0 = cand + (size_t)u * K;
+            UnitOut O;
+            uint32_t n = 0;
+            ok = exact_unit<true>(fr, fphase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R);
+            if (!ok) break;   // a wait timed out: leave (the ring may not be reusable)
+            ring_release(fr, lane);
+            ring_init(sm, lane);
+            phase = 0;
+            Cand *C = cand + (size_t)u * K + lane;
+            if (lane == 0)
+                for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
+            __syncwarp();
+            if (lane != 0) {
+                const Cand *C0 = R.C0;
+                for (int r = 0; r < RM; ++r) { C->pos[r] = C0->pos[r]; C->gp[r] = C0->gp[r]; }
+            }
+            C->c0 = st.c; C->c = O.c; C->last = R.last; C->n = n;
+            C->gmax = R.gmax; C->garg = R.garg; C->tmax = R.tmax; C->targ = R.targ;
+            C->list = NO_LIST; C->pad = 0;
+            if (lane == 0) {
+                UnitSum S;   // window totals are filled by k_totals, for the units that need them
+                S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = R.umin; S.maxQ = R.umax;
+                usum[u] = S;
+                uout[u] = O;
+                if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);
+            }
+            continue;
+        }
+        {
             // warm-up over the tail of the previous unit of the trace; candidates whose
             // counters become equal run on as one (the lowest lane leads)
             c = candidate_entry(lane, T);
@@ -221,6 +270,7 @@ __device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const
                           int64_t c, int64_t T, int lane, unsigned long long spin, ErrWord *err) {
     Walk W;
     W.last = -1; W.n = 0; W.gmax = INT64_MIN; W.garg = 0; W.into = -1;
+    W.walked = (uint32_t)U.len;
     uint32_t mypos[RM];
 #pragma unroll
     for (int r = 0; r < RM; ++r) mypos[r] = cu[lane].pos[r];
@@ -266,6 +316,7 @@ __device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const
             if (m) {
                 mj = __ffs(m) - 1;
                 mi = (uint32_t)__shfl_sync(FULL, hit, mj);
+                W.walked = pos + 1;
                 return true;
             }
             bool leq = false;
@@ -278,6 +329,7 @@ __device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const
                 const int sl = __ffs(m2) - 1;
                 mj = __shfl_sync(FULL, owner, sl);
                 mi = __shfl_sync(FULL, lp, sl);
+                W.walked = pos + 1;
                 return true;
             }
             b = -Qr;
@@ -398,6 +450,7 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
                 sm.mode[i] = (uint16_t)MODE_WALKED;
                 atomicAdd(&stats[0], 1ull);
                 if (W.into >= 0) atomicAdd(&stats[1], 1ull);
+                atomicAdd(&stats[4], (unsigned long long)W.walked);
             }
             ec = W.c;
             if (W.into >= 0) { k = (uint32_t)W.into; expl = false; }
@@ -461,11 +514,11 @@ cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s) {
 }
 
 cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s) {
-    const size_t smem = sizeof(SketchRing) * a.warps_per_block;
+    const size_t smem = SKETCH_WARP_SMEM * a.warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.lists, a.traces,
-                                                            a.T, a.warmup, a.queue, a.err, a.spin);
+    k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.lists, a.recs,
+                                                            a.uout, a.traces, a.T, a.warmup, a.queue, a.err, a.spin);
     return cudaGetLastError();
 }
 
@@ -486,7 +539,7 @@ cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s) {
 }
 
 int sketch_occupancy(int warps_per_block, int *blocks_per_sm) {
-    const size_t smem = sizeof(SketchRing) * warps_per_block;
+    const size_t smem = SKETCH_WARP_SMEM * warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sketch, 32 * warps_per_block, smem);

@@ -51,6 +51,16 @@ __device__ __forceinline__ void ring_init(RingT &sm, int lane) {
     __syncwarp();
 }
 
+// Invalidate a ring's barriers before its shared memory is used as another ring (the
+// walk that used it has drained every copy).
+template <class RingT>
+__device__ __forceinline__ void ring_release(RingT &sm, int lane) {
+    __syncwarp();
+    if (lane == 0)
+        for (int s = 0; s < RingT::kNS; ++s) mbar_inval(&sm.bar[s]);
+    __syncwarp();
+}
+
 // One step's events for this lane: EL consecutive events at tile offset e0.
 template <int EL>
 struct StepIn {
