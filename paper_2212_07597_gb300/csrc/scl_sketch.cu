@@ -17,9 +17,10 @@
 //           counter instead.  All lanes advance together, 128 events per step.
 // k_match   for each unit and each candidate k of the previous unit: the candidate of
 //           this unit whose start counter equals k's end counter, if any.
-// k_chain   one warp per trace: follows the true candidate from unit to unit through
+// k_chain   one block per trace: follows the true candidate from unit to unit through
 //           the match table in shared memory; where no candidate carries the true
-//           counter it walks the unit itself.
+//           counter the block walks the unit itself (helper warps summarise the steps
+//           ahead of the warp that runs the counter).
 #include "scl_exact.cuh"
 #include "scl_launch.h"
 
@@ -63,7 +64,6 @@ __device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, i
 using SketchRing = Ring<false, 4, 256, 8>;
 using FirstRing = Ring<true, 2, 256, 8>;       // the first unit of a trace: its exact replay
 constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing) > sizeof(FirstRing) ? sizeof(SketchRing) : sizeof(FirstRing);
-using ChainRing = Ring<false, 16, 512, 16>;   // a lone walker: 512-event steps, 8k events in flight
 
 __global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
                                                     Cand *cand, SRes *lists, FRec *recs, UnitOut *uout,
@@ -250,177 +250,269 @@ __global__ void k_match(const Unit *__restrict__ units, int nunits, const Cand *
 }
 
 // ---------------------------------------------------------------- k_chain
-constexpr int CHAIN_CHUNK = 4096;   // units per shared-memory chunk (with a 66 KB walker ring)
+constexpr int CHAIN_CHUNK = 1024;   // units per shared-memory chunk of the match table
+constexpr int CW = 8;               // warps per chain block: warp 0 runs the counter, the rest help
+constexpr int WE = 16;              // events per lane per walk step
+constexpr int WSTEP = 32 * WE;      // events per walk step
+constexpr int NSLOT = 8;            // walk steps summarised ahead of the counter
+constexpr int LCAP = 2048;          // reset-list positions staged in shared memory per list
 
 constexpr uint32_t MODE_TRANSPARENT = 0x100u;   // explicit counter entering, no reset in the unit
 constexpr uint32_t MODE_WALKED = 0x200u;        // explicit counter entering, walked here (uwalk)
 
+// one walk step, summarised by a helper warp: the step's prefix sums at every event,
+// each lane's extremes over its WE prefixes, the step total and the step extremes
+struct WalkSlot {
+    int64_t xq[32 * WE];
+    int64_t lmax[32], lmin[32];
+    int64_t tot, qmax, qmin;
+    volatile int32_t ready;   // index of the step held (-1: none)
+    int32_t pad;
+};
+
 struct ChainSmem {
     uint8_t m[CHAIN_CHUNK][K];
     uint16_t mode[CHAIN_CHUNK];
-    ChainRing ring;
+    WalkSlot slot[NSLOT];
+    uint32_t lpos[NL][LCAP];     // the unit's reset lists (positions), for the merge test
+    Walk wres;                   // the walk's result, for every warp
+    volatile int32_t consumed;   // walk steps the counter has finished
+    volatile int32_t stop;       // the counter is done (or a wait gave up)
 };
 
-// Walk unit U from counter c (one warp, through the bulk-copy ring) until one of its
-// resets is also a reset of a candidate of the unit -- from there the run is that
-// candidate's -- or to the unit's end.  Lane j holds candidate j's first RM resets; lane
-// s < NL also follows reset list s (every reset of a candidate run, in order), so merges
-// after a candidate's first RM resets are found too.
-__device__ Walk walk_unit(ChainRing &ring, uint32_t &phase, const Unit &U, const Cand *cu, const SRes *lists,
-                          int64_t c, int64_t T, int lane, unsigned long long spin, ErrWord *err) {
-    Walk W;
-    W.last = -1; W.n = 0; W.gmax = INT64_MIN; W.garg = 0; W.into = -1;
-    W.walked = (uint32_t)U.len;
-    uint32_t mypos[RM];
-#pragma unroll
-    for (int r = 0; r < RM; ++r) mypos[r] = cu[lane].pos[r];
-    // list s: its owner (a candidate carrying it), length, and the next listed reset
+// Walk unit U from counter c until one of its resets is also a reset of a candidate of the
+// unit -- from there the run is that candidate's -- or to the unit's end.  The whole block
+// takes part: warps 1.. load the unit's steps and write their prefix summaries to the slot
+// ring; warp 0 runs the counter over the summaries, locating crossings in the stored
+// prefixes.  Lane j of warp 0 holds candidate j's first RM resets; lane s < NL also follows
+// reset list s (every reset of a candidate run, in order).  Every wait is bounded.
+__device__ Walk walk_coop(ChainSmem &sm, const Unit &U, const Cand *cu, const SRes *lists, int64_t c, int64_t T,
+                          int warp, int lane, unsigned long long spin, ErrWord *err) {
+    const uint32_t nsteps = (uint32_t)((U.len + WSTEP - 1) / WSTEP);
+    if (threadIdx.x == 0) { sm.consumed = 0; sm.stop = 0; }
+    if (threadIdx.x < NSLOT) sm.slot[threadIdx.x].ready = -1;
+    // list q: its owner (a candidate carrying it) and its positions, staged once
     const uint32_t mylist = cu[lane].list;
     int owner = -1;
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
         const unsigned o = __ballot_sync(FULL, mylist == (uint32_t)q);
-        if (lane == q) owner = o ? __ffs(o) - 1 : -1;
+        const int oq = o ? __ffs(o) - 1 : -1;
+        if (lane == q) owner = oq;
+        if (oq >= 0) {
+            const uint32_t nq = cu[oq].n < (uint32_t)LCAP ? cu[oq].n : (uint32_t)LCAP;
+            const SRes *Lq = lists + U.lst0 + (uint64_t)q * U.lst_cap;
+            for (uint32_t i = threadIdx.x; i < nq; i += 32 * CW) sm.lpos[q][i] = Lq[i].pos;
+        }
     }
-    const SRes *Ls = lists + U.lst0 + (uint64_t)(lane < NL ? lane : 0) * U.lst_cap;
-    const uint32_t lcount = owner >= 0 ? cu[owner].n : 0;
-    uint32_t lp = 0;
-    uint32_t lnext = lcount ? Ls[0].pos : 0xffffffffu;
-    int64_t P = 0;
-    int mj = -1;
-    uint32_t mi = 0;
-    auto step = [&](const StepIn<16> &in, uint32_t rel0) -> bool {
-        StepPrefix<16> sp;
-        step_prefix(in, lane, sp, ring.xq);
-        if (__ballot_sync(FULL, c + sp.lmax >= T || c + sp.lmin <= -T) == 0) {
-            c += sp.tot;
-            P += sp.tot;
-            return false;
-        }
-        int64_t b = c;
-        int after = -1;
-        while (true) {
-            int64_t Qr;
-            const int r = first_cross(sp, ring.xq, lane, b, T, after, Qr);
-            if (r < 0) break;
-            const uint32_t pos = rel0 + (uint32_t)r;
-            const int64_t Pl = P + Qr;
-            if (b + Qr > 0 && Pl > W.gmax) { W.gmax = Pl; W.garg = pos; }
-            ++W.n;
-            W.last = (int32_t)pos;
-            int hit = -1;
+    __syncthreads();
+    if (warp != 0) {
+        // ---- helpers: steps warp-1, warp-1 + (CW-1), ...; the next step's deltas load
+        // while the current one is summarised
+        const bool vec = (reinterpret_cast<uintptr_t>(U.delta) & 15u) == 0;
+        auto load = [&](uint32_t s, int64_t (&d)[WE]) {
+            const uint64_t e0 = (uint64_t)s * WSTEP + (uint64_t)lane * WE;
+            if (vec && e0 + WE <= U.len) {
+                const longlong2 *src = reinterpret_cast<const longlong2 *>(U.delta + e0);
 #pragma unroll
-            for (int q = 0; q < RM; ++q)
-                if (mypos[q] == pos) hit = q;
-            const unsigned m = __ballot_sync(FULL, hit >= 0);
-            if (m) {
-                mj = __ffs(m) - 1;
-                mi = (uint32_t)__shfl_sync(FULL, hit, mj);
-                W.walked = pos + 1;
-                return true;
-            }
-            bool leq = false;
-            if (lane < NL && lcount) {
-                while (lnext < pos) lnext = ++lp < lcount ? Ls[lp].pos : 0xffffffffu;
-                leq = lnext == pos;
-            }
-            const unsigned m2 = __ballot_sync(FULL, leq);
-            if (m2) {
-                const int sl = __ffs(m2) - 1;
-                mj = __shfl_sync(FULL, owner, sl);
-                mi = __shfl_sync(FULL, lp, sl);
-                W.walked = pos + 1;
-                return true;
-            }
-            b = -Qr;
-            after = r;
-        }
-        c = b + sp.tot;
-        P += sp.tot;
-        return false;
-    };
-    ring_walk<false>(ring, U, 0, U.len, phase, spin, err, lane, step);
-    if (mj >= 0) {
-        // the rest of the unit follows candidate mj from its reset mi on
-        const Cand &Cj = cu[mj];
-        W.n += Cj.n - (mi + 1);
-        int64_t sg = INT64_MIN;
-        uint32_t sa = 0;
-        if (mi + 1 < (uint32_t)RM || Cj.list == NO_LIST) {
-            sg = Cj.tmax;
-            sa = Cj.targ;
-            for (int q = RM - 1; q > (int)mi; --q)
-                if (Cj.gp[q] != INT64_MIN && Cj.gp[q] >= sg) { sg = Cj.gp[q]; sa = Cj.pos[q]; }
-        } else {
-            // the largest prefix at a growth reset after mi, from the list: the counter at
-            // reset r > 0 is P_r - P_(r-1)
-            const SRes *Lj = lists + U.lst0 + (uint64_t)Cj.list * U.lst_cap;
-            for (uint32_t r = mi + 1 + lane; r < Cj.n; r += 32) {
-                const SRes q = Lj[r];
-                if (q.P - Lj[r - 1].P > 0 && (q.P > sg || (q.P == sg && q.pos < sa))) { sg = q.P; sa = q.pos; }
-            }
+                for (int q = 0; q < WE / 2; ++q) { const longlong2 v = src[q]; d[2 * q] = v.x; d[2 * q + 1] = v.y; }
+            } else {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const int64_t og = __shfl_xor_sync(FULL, sg, o);
-                const uint32_t oa = __shfl_xor_sync(FULL, sa, o);
-                if (og > sg || (og == sg && og != INT64_MIN && oa < sa)) { sg = og; sa = oa; }
+                for (int q = 0; q < WE; ++q) d[q] = e0 + q < U.len ? U.delta[e0 + q] : 0;
             }
+        };
+        int64_t cur[WE], nxt[WE];
+        uint32_t s = (uint32_t)(warp - 1);
+        if (s < nsteps) load(s, cur);
+        for (; s < nsteps; s += CW - 1) {
+            if (s + (CW - 1) < nsteps) load(s + (CW - 1), nxt);
+            // the slot is free once the counter has finished step s - NSLOT
+            bool go = true;
+            for (unsigned long long it = 0;; ++it) {
+                if (sm.stop) { go = false; break; }
+                if ((int32_t)s < sm.consumed + NSLOT) break;
+                if (it > spin) {
+                    if (lane == 0) set_error(err, E_TIMEOUT, 13, (unsigned long long)s);
+                    go = false;
+                    break;
+                }
+            }
+            if (!__all_sync(FULL, go)) break;
+            __threadfence_block();
+            WalkSlot &sl = sm.slot[s % NSLOT];
+            StepIn<WE> in;
+#pragma unroll
+            for (int q = 0; q < WE; ++q) { in.d[q] = cur[q]; in.a[q] = 0; }
+            in.pw[0] = in.pw[1] = 0;
+            StepPrefix<WE> sp;
+            step_prefix(in, lane, sp, sl.xq);
+            sl.lmax[lane] = sp.lmax;
+            sl.lmin[lane] = sp.lmin;
+            const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
+            if (lane == 0) { sl.tot = sp.tot; sl.qmax = qmax; sl.qmin = qmin; }
+            __syncwarp();
+            __threadfence_block();
+            if (lane == 0) sl.ready = (int32_t)s;
+#pragma unroll
+            for (int q = 0; q < WE; ++q) cur[q] = nxt[q];
         }
-        if (sg != INT64_MIN && sg > W.gmax) { W.gmax = sg; W.garg = sa; }
-        W.last = Cj.last;
-        W.c = Cj.c;
-        W.into = mj;
     } else {
-        W.c = c;
+        // ---- the counter
+        Walk W;
+        W.last = -1; W.n = 0; W.gmax = INT64_MIN; W.garg = 0; W.into = -1;
+        W.walked = (uint32_t)U.len;
+        uint32_t mypos[RM];
+#pragma unroll
+        for (int r = 0; r < RM; ++r) mypos[r] = cu[lane].pos[r];
+        const SRes *Ls = lists + U.lst0 + (uint64_t)(lane < NL ? lane : 0) * U.lst_cap;
+        const uint32_t lcount = owner >= 0 ? cu[owner].n : 0;
+        const uint32_t *lsm = sm.lpos[lane < NL ? lane : 0];
+        uint32_t lp = 0;
+        uint32_t lnext = lcount ? lsm[0] : 0xffffffffu;
+        int64_t P = 0;
+        int mj = -1;
+        uint32_t mi = 0;
+        for (uint32_t s = 0; s < nsteps && mj < 0; ++s) {
+            WalkSlot &sl = sm.slot[s % NSLOT];
+            bool got = false;
+            for (unsigned long long it = 0; it <= spin; ++it)
+                if (sl.ready == (int32_t)s) { got = true; break; }
+            if (!__all_sync(FULL, got)) {
+                if (lane == 0) set_error(err, E_TIMEOUT, 14, (unsigned long long)s);
+                break;
+            }
+            __threadfence_block();
+            const int64_t tot = sl.tot;
+            const uint32_t rel0 = s * WSTEP;
+            if (c + sl.qmax >= T || c + sl.qmin <= -T) {
+                StepPrefix<WE> sp;
+                sp.lmax = sl.lmax[lane];
+                sp.lmin = sl.lmin[lane];
+                int64_t b = c;
+                int after = -1;
+                while (true) {
+                    int64_t Qr;
+                    const int r = first_cross(sp, sl.xq, lane, b, T, after, Qr);
+                    if (r < 0) break;
+                    const uint32_t pos = rel0 + (uint32_t)r;
+                    const int64_t Pl = P + Qr;
+                    if (b + Qr > 0 && Pl > W.gmax) { W.gmax = Pl; W.garg = pos; }
+                    ++W.n;
+                    W.last = (int32_t)pos;
+                    int hit = -1;
+#pragma unroll
+                    for (int q = 0; q < RM; ++q)
+                        if (mypos[q] == pos) hit = q;
+                    const unsigned m = __ballot_sync(FULL, hit >= 0);
+                    if (m) {
+                        mj = __ffs(m) - 1;
+                        mi = (uint32_t)__shfl_sync(FULL, hit, mj);
+                        W.walked = pos + 1;
+                        break;
+                    }
+                    bool leq = false;
+                    if (lane < NL && lcount) {
+                        while (lnext < pos)
+                            lnext = ++lp < lcount ? (lp < (uint32_t)LCAP ? lsm[lp] : Ls[lp].pos) : 0xffffffffu;
+                        leq = lnext == pos;
+                    }
+                    const unsigned m2 = __ballot_sync(FULL, leq);
+                    if (m2) {
+                        const int slx = __ffs(m2) - 1;
+                        mj = __shfl_sync(FULL, owner, slx);
+                        mi = __shfl_sync(FULL, lp, slx);
+                        W.walked = pos + 1;
+                        break;
+                    }
+                    b = -Qr;
+                    after = r;
+                }
+                c = b + tot;
+            } else {
+                c += tot;
+            }
+            P += tot;
+            __syncwarp();
+            if (lane == 0) { __threadfence_block(); sm.consumed = (int32_t)(s + 1); }
+        }
+        if (lane == 0) sm.stop = 1;
+        if (mj >= 0) {
+            // the rest of the unit follows candidate mj from its reset mi on
+            const Cand &Cj = cu[mj];
+            W.n += Cj.n - (mi + 1);
+            int64_t sg = INT64_MIN;
+            uint32_t sa = 0;
+            if (mi + 1 < (uint32_t)RM || Cj.list == NO_LIST) {
+                sg = Cj.tmax;
+                sa = Cj.targ;
+                for (int q = RM - 1; q > (int)mi; --q)
+                    if (Cj.gp[q] != INT64_MIN && Cj.gp[q] >= sg) { sg = Cj.gp[q]; sa = Cj.pos[q]; }
+            } else {
+                // the largest prefix at a growth reset after mi, from the list: the counter at
+                // reset r > 0 is P_r - P_(r-1)
+                const SRes *Lj = lists + U.lst0 + (uint64_t)Cj.list * U.lst_cap;
+                for (uint32_t r = mi + 1 + lane; r < Cj.n; r += 32) {
+                    const SRes q = Lj[r];
+                    if (q.P - Lj[r - 1].P > 0 && (q.P > sg || (q.P == sg && q.pos < sa))) { sg = q.P; sa = q.pos; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int64_t og = __shfl_xor_sync(FULL, sg, o);
+                    const uint32_t oa = __shfl_xor_sync(FULL, sa, o);
+                    if (og > sg || (og == sg && og != INT64_MIN && oa < sa)) { sg = og; sa = oa; }
+                }
+            }
+            if (sg != INT64_MIN && sg > W.gmax) { W.gmax = sg; W.garg = sa; }
+            W.last = Cj.last;
+            W.c = Cj.c;
+            W.into = mj;
+        } else {
+            W.c = c;
+        }
+        if (lane == 0) sm.wres = W;
     }
-    return W;
+    __syncthreads();
+    return sm.wres;
 }
 
 // entering mode per unit: j < K: the true run is candidate j of the unit;
 // MODE_TRANSPARENT / MODE_WALKED: an explicit counter (uexp) entered.
-__global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, const BTrace *__restrict__ bts, int nbt,
-                                             const UnitSum *__restrict__ usum, const Cand *__restrict__ cand,
-                                             const SRes *__restrict__ lists,
-                                             const uint8_t *__restrict__ match, Walk *uwalk, UnitTrue *utrue,
-                                             uint32_t *umode, int64_t *uexp, int64_t T, ErrWord *err,
-                                             unsigned long long spin, unsigned long long *stats) {
+// One block per trace; every warp follows the same chain (so all take part in walks),
+// warp 0 writes the results.
+__global__ void __launch_bounds__(32 * CW) k_chain(const Unit *__restrict__ units, const BTrace *__restrict__ bts,
+                                                  int nbt, const UnitSum *__restrict__ usum,
+                                                  const Cand *__restrict__ cand, const SRes *__restrict__ lists,
+                                                  const uint8_t *__restrict__ match, Walk *uwalk, UnitTrue *utrue,
+                                                  uint32_t *umode, int64_t *uexp, int64_t T, ErrWord *err,
+                                                  unsigned long long spin, unsigned long long *stats) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ChainSmem &sm = *reinterpret_cast<ChainSmem *>(smem_raw);
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x;
     if (b >= nbt) return;
     const BTrace B = bts[b];
     if (B.nu == 0) return;
-    ring_init(sm.ring, lane);
-    uint32_t phase = 0;
-    // ---- phase A: the entering mode of every unit
-    if (lane == 0) umode[B.u0] = 0;   // lane 0 of the first unit ran the exact counter
-    uint32_t k = 0;                   // the true run leaves the previous unit on candidate k...
-    bool expl = false;                // ...or as the explicit counter ec
+    const bool lead = threadIdx.x == 0;
+    if (lead) umode[B.u0] = 0;   // the first unit was replayed from the exact counter
+    uint32_t k = 0;              // the true run leaves the previous unit on candidate k...
+    bool expl = false;           // ...or as the explicit counter ec
     int64_t ec = 0;
     for (uint32_t c0 = 1; c0 < B.nu; c0 += CHAIN_CHUNK) {
         const uint32_t cn = B.nu - c0 < (uint32_t)CHAIN_CHUNK ? B.nu - c0 : (uint32_t)CHAIN_CHUNK;
-        {   // cn rows of K bytes, contiguous in global memory: 16-byte loads, 8 in flight per lane
+        __syncthreads();
+        {   // cn rows of K bytes, contiguous in global memory: 16-byte loads
             const uint4 *src = reinterpret_cast<const uint4 *>(match + (size_t)(B.u0 + c0) * K);
             uint4 *dst = reinterpret_cast<uint4 *>(&sm.m[0][0]);
             const uint32_t nv = cn * K / 16;
-            uint32_t v = lane;
-            for (; v + 7 * 32 < nv; v += 8 * 32) {
-                uint4 r[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) r[q] = src[v + q * 32];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[v + q * 32] = r[q];
-            }
-            for (; v < nv; v += 32) dst[v] = src[v];
+            for (uint32_t v = threadIdx.x; v < nv; v += 32 * CW) dst[v] = src[v];
         }
-        __syncwarp();
+        __syncthreads();
         for (uint32_t i = 0; i < cn; ++i) {
             const uint32_t u = B.u0 + c0 + i;
             if (!expl) {
                 const uint8_t j = sm.m[i][k];
                 if (j != NO_MATCH) {   // the common case: the true run carries on as candidate j
-                    if (lane == 0) sm.mode[i] = j;
+                    if (lead) sm.mode[i] = j;
                     k = j;
                     continue;
                 }
@@ -430,22 +522,22 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
             // explicit counter: does a candidate of this unit start with it?
             const bool eq = cand[(size_t)u * K + lane].c0 == ec;
             const unsigned mm = __ballot_sync(FULL, eq);
-            if (lane == 0) uexp[u] = ec;
+            if (lead) uexp[u] = ec;
             if (mm) {
                 k = __ffs(mm) - 1;
                 expl = false;
-                if (lane == 0) sm.mode[i] = (uint16_t)k;
+                if (lead) sm.mode[i] = (uint16_t)k;
                 continue;
             }
             const UnitSum S = usum[u];
-            if (lane == 0) atomicAdd(&stats[2], 1ull);
+            if (lead) atomicAdd(&stats[2], 1ull);
             if (ec + S.maxQ < T && ec + S.minQ > -T) {
-                if (lane == 0) { sm.mode[i] = (uint16_t)MODE_TRANSPARENT; atomicAdd(&stats[3], 1ull); }
+                if (lead) { sm.mode[i] = (uint16_t)MODE_TRANSPARENT; atomicAdd(&stats[3], 1ull); }
                 ec += S.total;
                 continue;
             }
-            const Walk W = walk_unit(sm.ring, phase, units[u], cand + (size_t)u * K, lists, ec, T, lane, spin, err);
-            if (lane == 0) {
+            const Walk W = walk_coop(sm, units[u], cand + (size_t)u * K, lists, ec, T, warp, lane, spin, err);
+            if (lead) {
                 uwalk[u] = W;
                 sm.mode[i] = (uint16_t)MODE_WALKED;
                 atomicAdd(&stats[0], 1ull);
@@ -455,9 +547,8 @@ __global__ void __launch_bounds__(32) k_chain(const Unit *__restrict__ units, co
             ec = W.c;
             if (W.into >= 0) { k = (uint32_t)W.into; expl = false; }
         }
-        __syncwarp();
-        for (uint32_t i = lane; i < cn; i += 32) umode[B.u0 + c0 + i] = sm.mode[i];
-        __syncwarp();
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < cn; i += 32 * CW) umode[B.u0 + c0 + i] = sm.mode[i];
     }
 }
 
@@ -533,8 +624,8 @@ cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s) {
     const size_t smem = sizeof(ChainSmem);
     cudaError_t e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chain<<<a.nbt, 32, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.lists, a.match, a.uwalk, a.utrue, a.umode,
-                                    a.uexp, a.T, a.err, a.spin, a.stats);
+    k_chain<<<a.nbt, 32 * CW, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.lists, a.match, a.uwalk, a.utrue,
+                                         a.umode, a.uexp, a.T, a.err, a.spin, a.stats);
     return cudaGetLastError();
 }
 
