@@ -236,7 +236,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         k.stats = c->stats;
         k.num_sms = c->num_sms;
         // spread the units over all SMs: fewer warps per block when units are few
-        k.warps_per_block = std::max(1, std::min((int)c->tune.warps_per_block,
+        k.warps_per_block = std::max(1, std::min(std::min((int)c->tune.warps_per_block, SKETCH_MAX_WARPS),
                                                  (nunits + c->num_sms - 1) / c->num_sms));
         int bps = 0;
         if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
@@ -439,7 +439,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     }
     c->h_events.assign(NTr, 0);
     c->tune.unit_events = cfg.unit_events;   // 0: sized per batch
-    c->tune.warps_per_block = 16;
+    c->tune.warps_per_block = SKETCH_MAX_WARPS;
     c->tune.ext_events = 0;
     c->tune.final_warps = 14;
     *out = c;
@@ -965,7 +965,7 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     int rc = copy_state(true) == cudaSuccess ? SCL_OK : SCL_ECUDA;
     const uint32_t units[] = {0, 65536, 131072, 262144};
     const uint32_t fwarps[] = {10, 14};
-    const uint32_t swarps[] = {8, 16};
+    const uint32_t swarps[] = {8, (uint32_t)SKETCH_MAX_WARPS};
     const uint32_t warm[] = {16384, 32768};
     for (uint32_t ue : units)
         for (uint32_t fw : fwarps)

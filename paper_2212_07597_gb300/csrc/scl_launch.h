@@ -6,6 +6,8 @@
 
 namespace scl {
 
+constexpr int SKETCH_MAX_WARPS = 16;   // k_sketch warps per block (its launch bound)
+
 struct LaunchSketch {
     const Unit *units;
     int nunits;

@@ -65,7 +65,7 @@ using SketchRing = Ring<false, 4, 256, 8>;
 using FirstRing = Ring<true, 2, 256, 8>;       // the first unit of a trace: its exact replay
 constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing) > sizeof(FirstRing) ? sizeof(SketchRing) : sizeof(FirstRing);
 
-__global__ void __launch_bounds__(32 * 16) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
+__global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
                                                     Cand *cand, SRes *lists, FRec *recs, UnitOut *uout,
                                                     const DevTrace *traces, int64_t T, uint32_t warmup,
                                                     unsigned *queue, ErrWord *err, unsigned long long spin) {
