@@ -52,6 +52,10 @@ struct scl_ctx {
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
     bool plan_pending = false;
+    // the copy-volume pass (Section 3.5) shares nothing with the event path: it runs on a
+    // side stream between a fork after the sketch and a join before the state fold
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // tuning
     scl_tuning tune{};
     // graph replay of repeated identical batches
@@ -211,6 +215,31 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
 
     const int nunits = q.nunits;
     const uint32_t nbt = q.nbt;
+    LaunchPost a;
+    a.units = d_units;
+    a.nunits = nunits;
+    a.bts = d_bts;
+    a.nbt = (int)nbt;
+    a.usum = static_cast<const UnitSum *>(c->usum.p);
+    a.utrue = static_cast<const UnitTrue *>(c->utrue.p);
+    a.uplan = static_cast<UnitPlan *>(c->uplan.p);
+    a.uout = static_cast<UnitOut *>(c->uout.p);
+    a.btres = static_cast<BTraceRes *>(c->btres.p);
+    a.recs = static_cast<FRec *>(c->recs.p);
+    a.pref = static_cast<int64_t *>(c->pref.p);
+    a.traces = c->traces;
+    a.lines = c->lines;
+    a.log = c->log;
+    a.log_cap = cfg.sample_log_capacity;
+    a.n_lines = cfg.n_lines;
+    a.T = cfg.threshold;
+    a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
+    a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
+    a.ngroups = q.ngroups;
+    a.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
+    a.nctiles = q.nctiles;
+    a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
+    a.err = c->errw;
     if (nunits) {
         LaunchSketch k;
         k.units = d_units;
@@ -245,6 +274,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
             Prof p(c, s, "sketch");
             CK(launch_sketch(k, s), "launch sketch");
         }
+        CK(cudaEventRecord(c->ev_fork, s), "fork event");
         {
             Prof p(c, s, "match");
             CK(launch_match(k, s), "launch match");
@@ -258,31 +288,22 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
             CK(launch_totals(k, s), "launch totals");
         }
     }
-    LaunchPost a;
-    a.units = d_units;
-    a.nunits = nunits;
-    a.bts = d_bts;
-    a.nbt = (int)nbt;
-    a.usum = static_cast<const UnitSum *>(c->usum.p);
-    a.utrue = static_cast<const UnitTrue *>(c->utrue.p);
-    a.uplan = static_cast<UnitPlan *>(c->uplan.p);
-    a.uout = static_cast<UnitOut *>(c->uout.p);
-    a.btres = static_cast<BTraceRes *>(c->btres.p);
-    a.recs = static_cast<FRec *>(c->recs.p);
-    a.pref = static_cast<int64_t *>(c->pref.p);
-    a.traces = c->traces;
-    a.lines = c->lines;
-    a.log = c->log;
-    a.log_cap = cfg.sample_log_capacity;
-    a.n_lines = cfg.n_lines;
-    a.T = cfg.threshold;
-    a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
-    a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
-    a.ngroups = q.ngroups;
-    a.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
-    a.nctiles = q.nctiles;
-    a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
-    a.err = c->errw;
+    // ---- the copy-volume pass, on the side stream (after the sketch when there is one)
+    if (!nunits) CK(cudaEventRecord(c->ev_fork, s), "fork event");
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork the copy pass");
+    {
+        Prof p(c, c->side, "copy_sum");
+        CK(launch_copy_sum(a, c->side), "launch copy sum");
+    }
+    {
+        Prof p(c, c->side, "copy_scan");
+        CK(launch_copy_scan(a, c->side), "launch copy scan");
+    }
+    {
+        Prof p(c, c->side, "copy_apply");
+        CK(launch_copy_apply(a, c->side), "launch copy apply");
+    }
+    CK(cudaEventRecord(c->ev_join, c->side), "join event");
     {
         Prof p(c, s, "scan");
         CK(launch_scan(a, s), "launch scan");
@@ -319,18 +340,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         Prof p(c, s, "epi");
         CK(launch_epi(a, s), "launch epi");
     }
-    {
-        Prof p(c, s, "copy_sum");
-        CK(launch_copy_sum(a, s), "launch copy sum");
-    }
-    {
-        Prof p(c, s, "copy_scan");
-        CK(launch_copy_scan(a, s), "launch copy scan");
-    }
-    {
-        Prof p(c, s, "copy_apply");
-        CK(launch_copy_apply(a, s), "launch copy apply");
-    }
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0), "join the copy pass");
     {
         Prof p(c, s, "state");
         CK(launch_state(a, s), "launch state");
@@ -384,6 +394,9 @@ void scl_replay_free(scl_ctx *c) {
     cudaFree(c->stats);
     if (c->h_plan) cudaFreeHost(c->h_plan);
     if (c->plan_done) cudaEventDestroy(c->plan_done);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     delete c;
 }
@@ -422,6 +435,9 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * 5);
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         int r = cuda_fail(c, e, "context allocation");
         fprintf(stderr, "scl_replay_init: %s\n", c->err.c_str());
