@@ -207,13 +207,13 @@ __device__ __forceinline__ int64_t warp_sum(int64_t v) {
     return v;
 }
 
+// Warp-wide signed 64-bit max: the high words (signed) by one warp reduction, then the low
+// words (unsigned) of the lanes holding that high word by a second one.
 __device__ __forceinline__ int64_t warp_max(int64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        int64_t t = __shfl_xor_sync(FULL, v, o);
-        v = t > v ? t : v;
-    }
-    return v;
+    const int hi = (int)(v >> 32);
+    const int mh = __reduce_max_sync(FULL, hi);
+    const unsigned ml = __reduce_max_sync(FULL, hi == mh ? (unsigned)v : 0u);
+    return (int64_t)(((uint64_t)(uint32_t)mh << 32) | ml);
 }
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {

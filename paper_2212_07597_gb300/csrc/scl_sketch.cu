@@ -61,7 +61,7 @@ __device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, i
 }
 
 // ---------------------------------------------------------------- k_sketch
-using SketchRing = Ring<false, 4, 256, 8>;
+using SketchRing = Ring<false, 2, 512, 8>;   // two steps per tile: half the ring waits
 using FirstRing = Ring<true, 2, 256, 8>;       // the first unit of a trace: its exact replay
 constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing) > sizeof(FirstRing) ? sizeof(SketchRing) : sizeof(FirstRing);
 

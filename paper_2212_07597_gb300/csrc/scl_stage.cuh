@@ -225,13 +225,12 @@ __device__ __forceinline__ void step_prefix(const StepIn<EL> &in, int lane, Step
     }
 }
 
+// Warp-wide signed 64-bit min, as warp_max.
 __device__ __forceinline__ int64_t warp_min(int64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        int64_t t = __shfl_xor_sync(FULL, v, o);
-        v = t < v ? t : v;
-    }
-    return v;
+    const int hi = (int)(v >> 32);
+    const int mh = __reduce_min_sync(FULL, hi);
+    const unsigned ml = __reduce_min_sync(FULL, hi == mh ? (unsigned)v : 0xffffffffu);
+    return (int64_t)(((uint64_t)(uint32_t)mh << 32) | ml);
 }
 
 // First step position after `after` where counter base b + Q crosses +-T; -1 if none.
