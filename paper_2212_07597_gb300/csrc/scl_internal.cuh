@@ -261,6 +261,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy (cp.async, L2 only), and an arrival on an
+// mbarrier that fires when all of this thread's earlier cp.async copies have landed
+// (.noinc: the barrier counts these arrivals among its expected ones).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Staged 8-byte columns hold each lane's 8 events (64 bytes, one "row") with their four
+// 16-byte chunks permuted: chunk c of row r sits at chunk c ^ ((r >> 1) & 3).  A quarter
+// warp loading one chunk per lane then touches eight distinct bank groups.
+__device__ __forceinline__ int swz_chunk(int r, int c) { return c ^ ((r >> 1) & 3); }
+__device__ __forceinline__ int swz8(int i) {   // element i of a tile -> its staged position
+    const int r = i >> 3, k = i & 7;
+    return (r << 3) | (swz_chunk(r, k >> 1) << 1) | (k & 1);
+}
+
 // Bounded wait for phase `parity` of the barrier, called by all 32 lanes of a warp.
 // Every lane polls (so each observes the phase completion); the answer is agreed by
 // vote, so all lanes return the same value.  False if `limit` polls passed.

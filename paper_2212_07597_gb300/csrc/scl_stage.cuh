@@ -1,11 +1,13 @@
-// scl_stage.cuh -- per-warp shared-memory ring fed by cp.async.bulk, and the warp
-// walk loop over one unit's events built on it.
+// scl_stage.cuh -- per-warp shared-memory ring fed by asynchronous copies, and the
+// warp walk loop over one unit's events built on it.
 //
 // A unit's columns are read in tiles of TILE events; NST tiles are in flight per
-// warp.  Full tiles of 16-byte aligned columns go through one bulk copy per column
-// completing on the stage's mbarrier; partial or unaligned tiles are copied by the
-// lanes.  Every wait is bounded; whatever happens, no bulk copy is left in flight
-// when the walk returns.
+// warp.  Full tiles of 16-byte aligned columns arrive as 16-byte cp.async copies issued
+// by all lanes (each lane's copies then arrive on the stage's mbarrier); the 8-byte
+// columns are written in the chunk-permuted layout of swz8, so the lanes' 16-byte loads
+// of their own 8 events are free of bank conflicts.  Partial or unaligned tiles are
+// copied by the lanes with plain loads into the same layout.  Every wait is bounded;
+// whatever happens, no copy is left in flight when the walk returns.
 #pragma once
 #include "scl_internal.cuh"
 
@@ -44,8 +46,9 @@ template <class RingT>
 __device__ __forceinline__ void ring_init(RingT &sm, int lane) {
     static_assert(sizeof(RingT) % 128 == 0, "rings laid end to end must stay aligned");
     static_assert(RingT::kTL % 16 == 0 && (RingT::kTL * 8) % 16 == 0, "bulk copies move 16-byte multiples");
+    static_assert(RingT::kE == 8, "the staged layout holds 8 events per lane");
     if (lane == 0) {
-        for (int s = 0; s < RingT::kNS; ++s) mbar_init(&sm.bar[s], 1);
+        for (int s = 0; s < RingT::kNS; ++s) mbar_init(&sm.bar[s], 32);   // one arrival per lane
         fence_mbar_init();
     }
     __syncwarp();
@@ -74,15 +77,16 @@ __device__ __forceinline__ uint32_t py_of(const StepIn<EL> &in, int k) {
     return (uint32_t)(in.pw[k >> 3] >> (8 * (k & 7))) & 0xffu;
 }
 
-// EL consecutive 64-bit values of this lane, as 16-byte shared loads.  (Quarter-warps
-// then touch each bank group several times; that costs shared-memory cycles, which are
-// spare here, rather than issue slots, which are not.)
+// The 8 consecutive 64-bit values of tile element e0 (a multiple of 8: one row of the
+// staged layout), as four 16-byte shared loads.
 template <int EL, class V>
-__device__ __forceinline__ void load_lane(const V *base, V (&out)[EL]) {
-    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(base);
+__device__ __forceinline__ void load_lane(const V *tile, uint32_t e0, V (&out)[EL]) {
+    static_assert(EL == 8, "one staged row per lane");
+    const int r = (int)(e0 >> 3);
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(tile + 8 * r);
 #pragma unroll
     for (int q = 0; q < EL / 2; ++q) {
-        const ulonglong2 v = src[q];
+        const ulonglong2 v = src[swz_chunk(r, q)];
         out[2 * q] = (V)v.x;
         out[2 * q + 1] = (V)v.y;
     }
@@ -108,27 +112,27 @@ __device__ bool ring_walk(RingT &sm, const Unit &U, uint64_t from, uint64_t limi
         const uint64_t t0 = t * TILE;
         const uint64_t cnt = limit - t0 < (uint64_t)TILE ? limit - t0 : (uint64_t)TILE;
         if (bulk && cnt == (uint64_t)TILE) {
-            if (lane == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(&sm.bar[s], TILE * (ADDR ? 17 : 8));
-                bulk_g2s(sm.d[s], U.delta + t0, TILE * 8, &sm.bar[s]);
-                if (ADDR) {
-                    bulk_g2s(sm.p(s), U.py + t0, TILE, &sm.bar[s]);
-                    bulk_g2s(sm.a(s), U.addr + t0, TILE * 8, &sm.bar[s]);
-                }
+            // 16-byte chunks j of the 8-byte columns land at their permuted places
+            for (int j = lane; j < TILE / 2; j += 32) {
+                const int r = j >> 2, cc = swz_chunk(r, j & 3);
+                cp_async16(&sm.d[s][8 * r + 2 * cc], U.delta + t0 + 2 * j);
+                if (ADDR) cp_async16(sm.a(s) + 8 * r + 2 * cc, U.addr + t0 + 2 * j);
             }
+            if (ADDR)
+                for (int j = lane; j < TILE / 16; j += 32) cp_async16(sm.p(s) + 16 * j, U.py + t0 + 16 * j);
+            cp_async_arrive(&sm.bar[s]);
             pending |= 1u << s;
         } else {
             for (uint32_t j = lane; j < (uint32_t)cnt; j += 32) {
-                sm.d[s][j] = U.delta[t0 + j];
+                const int js = swz8((int)j);
+                sm.d[s][js] = U.delta[t0 + j];
                 if (ADDR) {
                     sm.p(s)[j] = U.py[t0 + j];
-                    sm.a(s)[j] = U.addr[t0 + j];
+                    sm.a(s)[js] = U.addr[t0 + j];
                 }
             }
         }
     };
-
     for (uint64_t t = t_first; t < ntiles && t < t_first + NST; ++t) issue(t);
     bool ok = true;
     for (uint64_t t = t_first; t < ntiles; ++t) {
@@ -150,9 +154,9 @@ __device__ bool ring_walk(RingT &sm, const Unit &U, uint64_t from, uint64_t limi
         for (uint32_t b = b0; b < cnt; b += STEP) {
             const uint32_t e0 = b + lane * E;
             StepIn<E> in;
-            load_lane<E>(&sm.d[s][e0], in.d);
+            load_lane<E>(sm.d[s], e0, in.d);
             if (ADDR) {
-                load_lane<E>(sm.a(s) + e0, in.a);
+                load_lane<E>(sm.a(s), e0, in.a);
 #pragma unroll
                 for (int w = 0; w < (E + 7) / 8; ++w)
                     in.pw[w] = *reinterpret_cast<const unsigned long long *>(sm.p(s) + e0 + 8 * w);
@@ -217,10 +221,11 @@ __device__ __forceinline__ void step_prefix(const StepIn<EL> &in, int lane, Step
     sp.tot = __shfl_sync(FULL, incl, 31);
     sp.lmax = mx + sp.ex;
     sp.lmin = mn + sp.ex;
-    if (xq) {
+    if (xq) {   // EL == 8: the staged layout (lane = row); otherwise plain
         longlong2 *dst = reinterpret_cast<longlong2 *>(xq + lane * EL);
 #pragma unroll
-        for (int q = 0; q < EL / 2; ++q) dst[q] = make_longlong2(sp.ex + sp.lp[2 * q], sp.ex + sp.lp[2 * q + 1]);
+        for (int q = 0; q < EL / 2; ++q)
+            dst[EL == 8 ? swz_chunk(lane, q) : q] = make_longlong2(sp.ex + sp.lp[2 * q], sp.ex + sp.lp[2 * q + 1]);
         __syncwarp();
     }
 }
@@ -245,7 +250,7 @@ __device__ __forceinline__ int first_cross(const StepPrefix<EL> &sp, const int64
     while (m) {
         const int fl = __ffs(m) - 1;
         m &= m - 1;
-        const int64_t q = lane < EL ? xq[fl * EL + lane] : 0;
+        const int64_t q = lane < EL ? xq[EL == 8 ? swz8(fl * EL + lane) : fl * EL + lane] : 0;
         const unsigned h = __ballot_sync(FULL, lane < EL && fl * EL + lane > after && (q >= hi || q <= lo));
         if (h) {
             const int kf = __ffs(h) - 1;
