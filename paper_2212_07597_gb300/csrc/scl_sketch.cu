@@ -21,6 +21,8 @@
 //           the match table in shared memory; where no candidate carries the true
 //           counter the block walks the unit itself (helper warps summarise the steps
 //           ahead of the warp that runs the counter).
+#include <cstddef>
+
 #include "scl_exact.cuh"
 #include "scl_launch.h"
 
@@ -262,8 +264,8 @@ constexpr uint32_t MODE_WALKED = 0x200u;        // explicit counter entering, wa
 
 // one walk step, summarised by a helper warp: the step's prefix sums at every event,
 // each lane's extremes over its WE prefixes, the step total and the step extremes
-struct WalkSlot {
-    int64_t xq[32 * WE];
+struct alignas(16) WalkSlot {   // xq takes 16-byte stores
+    alignas(16) int64_t xq[32 * WE];
     int64_t lmax[32], lmin[32];
     int64_t tot, qmax, qmin;
     volatile int32_t ready;   // index of the step held (-1: none)
@@ -271,14 +273,22 @@ struct WalkSlot {
 };
 
 struct ChainSmem {
-    uint8_t m[CHAIN_CHUNK][K];
+    alignas(16) uint8_t m[CHAIN_CHUNK][K];   // 16-byte row loads
     uint16_t mode[CHAIN_CHUNK];
+    uint8_t endk[CW][K];         // per warp segment: the candidate leaving it, per entering one
+    uint32_t segk[CW];           // the true candidate entering each segment
+    uint32_t brk, kout;          // first row the matched run leaves the table; candidate then
     WalkSlot slot[NSLOT];
     uint32_t lpos[NL][LCAP];     // the unit's reset lists (positions), for the merge test
     Walk wres;                   // the walk's result, for every warp
     volatile int32_t consumed;   // walk steps the counter has finished
     volatile int32_t stop;       // the counter is done (or a wait gave up)
 };
+
+static_assert(offsetof(ChainSmem, slot) % 16 == 0 && sizeof(WalkSlot) % 16 == 0 &&
+                  offsetof(WalkSlot, xq) % 16 == 0,
+              "walk slots take 16-byte stores");
+static_assert(offsetof(ChainSmem, m) % 16 == 0, "match rows take 16-byte copies");
 
 // Walk unit U from counter c until one of its resets is also a reset of a candidate of the
 // unit -- from there the run is that candidate's -- or to the unit's end.  The whole block
@@ -364,6 +374,8 @@ __device__ Walk walk_coop(ChainSmem &sm, const Unit &U, const Cand *cu, const SR
         uint32_t mypos[RM];
 #pragma unroll
         for (int r = 0; r < RM; ++r) mypos[r] = cu[lane].pos[r];
+        // the first-RM test is needed only for candidate runs that have no reset list
+        const bool rm_needed = __any_sync(FULL, mylist == NO_LIST);
         const SRes *Ls = lists + U.lst0 + (uint64_t)(lane < NL ? lane : 0) * U.lst_cap;
         const uint32_t lcount = owner >= 0 ? cu[owner].n : 0;
         const uint32_t *lsm = sm.lpos[lane < NL ? lane : 0];
@@ -400,9 +412,11 @@ __device__ Walk walk_coop(ChainSmem &sm, const Unit &U, const Cand *cu, const SR
                     ++W.n;
                     W.last = (int32_t)pos;
                     int hit = -1;
+                    if (rm_needed) {
 #pragma unroll
-                    for (int q = 0; q < RM; ++q)
-                        if (mypos[q] == pos) hit = q;
+                        for (int q = 0; q < RM; ++q)
+                            if (mypos[q] == pos) hit = q;
+                    }
                     const unsigned m = __ballot_sync(FULL, hit >= 0);
                     if (m) {
                         mj = __ffs(m) - 1;
@@ -499,27 +513,76 @@ __global__ void __launch_bounds__(32 * CW) k_chain(const Unit *__restrict__ unit
     int64_t ec = 0;
     for (uint32_t c0 = 1; c0 < B.nu; c0 += CHAIN_CHUNK) {
         const uint32_t cn = B.nu - c0 < (uint32_t)CHAIN_CHUNK ? B.nu - c0 : (uint32_t)CHAIN_CHUNK;
-        __syncthreads();
-        {   // cn rows of K bytes, contiguous in global memory: 16-byte loads
-            const uint4 *src = reinterpret_cast<const uint4 *>(match + (size_t)(B.u0 + c0) * K);
-            uint4 *dst = reinterpret_cast<uint4 *>(&sm.m[0][0]);
-            const uint32_t nv = cn * K / 16;
-            for (uint32_t v = threadIdx.x; v < nv; v += 32 * CW) dst[v] = src[v];
-        }
-        __syncthreads();
-        for (uint32_t i = 0; i < cn; ++i) {
-            const uint32_t u = B.u0 + c0 + i;
+        uint32_t i = 0;
+        while (i < cn) {
             if (!expl) {
-                const uint8_t j = sm.m[i][k];
-                if (j != NO_MATCH) {   // the common case: the true run carries on as candidate j
-                    if (lead) sm.mode[i] = j;
-                    k = j;
-                    continue;
+                // ---- the matched run from row i on, resolved in parallel: each warp composes
+                // the match table over its segment of rows for all 32 entering candidates at
+                // once (in place: row r becomes "candidate at r" per entering candidate), then
+                // thread 0 chains the segments.
+                __syncthreads();
+                {   // rows i .. cn of K bytes, contiguous in global memory: 16-byte loads
+                    const uint4 *src = reinterpret_cast<const uint4 *>(match + (size_t)(B.u0 + c0 + i) * K);
+                    uint4 *dst = reinterpret_cast<uint4 *>(&sm.m[i][0]);
+                    const uint32_t nv = (cn - i) * K / 16;
+                    for (uint32_t v = threadIdx.x; v < nv; v += 32 * CW) dst[v] = src[v];
                 }
-                ec = cand[(size_t)(u - 1) * K + k].c;
+                __syncthreads();
+                const uint32_t per = (cn - i + CW - 1) / CW;
+                {
+                    const uint32_t a = i + warp * per, b = a + per < cn ? a + per : cn;
+                    uint32_t kk = (uint32_t)lane;
+                    for (uint32_t r = a; r < b; ++r) {
+                        const uint32_t nx = kk < (uint32_t)K ? sm.m[r][kk] : NO_MATCH;
+                        __syncwarp();
+                        sm.m[r][lane] = (uint8_t)nx;
+                        __syncwarp();
+                        kk = nx;
+                    }
+                    sm.endk[warp][lane] = (uint8_t)kk;
+                }
+                __syncthreads();
+                if (lead) {
+                    uint32_t kc = k, bseg = CW;
+                    for (int w = 0; w < CW; ++w) {
+                        sm.segk[w] = kc;
+                        if (i + w * per >= cn) continue;
+                        const uint32_t e = sm.endk[w][kc];
+                        if (e == NO_MATCH) { bseg = (uint32_t)w; break; }
+                        kc = e;
+                    }
+                    sm.kout = kc;
+                    sm.brk = bseg;   // segment of the break (CW: none)
+                }
+                __syncthreads();
+                const uint32_t bseg = sm.brk;
+                uint32_t brk = cn;
+                if (bseg < (uint32_t)CW) {   // the first row of that segment leaving the table
+                    const uint32_t a = i + bseg * per, b = a + per < cn ? a + per : cn;
+                    const uint32_t ks = sm.segk[bseg];
+                    for (uint32_t r0 = a; r0 < b; r0 += 32) {
+                        const unsigned hm = __ballot_sync(FULL, r0 + lane < b && sm.m[r0 + lane][ks] == NO_MATCH);
+                        if (hm) { brk = r0 + __ffs(hm) - 1; break; }
+                    }
+                }
+                for (uint32_t r = i + threadIdx.x; r < brk; r += 32 * CW)
+                    sm.mode[r] = sm.m[r][sm.segk[(r - i) / per]];
+                if (brk == cn) {
+                    k = sm.kout;
+                    i = cn;
+                    break;
+                }
+                // the run's candidate at row brk-1 matches nothing at row brk
+                {
+                    const uint32_t sg = (brk - i) / per, ks = sm.segk[sg];
+                    k = brk == i + sg * per ? ks : sm.m[brk - 1][ks];
+                }
+                i = brk;
+                ec = cand[(size_t)(B.u0 + c0 + i - 1) * K + k].c;
                 expl = true;
             }
-            // explicit counter: does a candidate of this unit start with it?
+            // ---- explicit counter at row i: does a candidate of this unit start with it?
+            const uint32_t u = B.u0 + c0 + i;
             const bool eq = cand[(size_t)u * K + lane].c0 == ec;
             const unsigned mm = __ballot_sync(FULL, eq);
             if (lead) uexp[u] = ec;
@@ -527,6 +590,7 @@ __global__ void __launch_bounds__(32 * CW) k_chain(const Unit *__restrict__ unit
                 k = __ffs(mm) - 1;
                 expl = false;
                 if (lead) sm.mode[i] = (uint16_t)k;
+                ++i;
                 continue;
             }
             const UnitSum S = usum[u];
@@ -534,6 +598,7 @@ __global__ void __launch_bounds__(32 * CW) k_chain(const Unit *__restrict__ unit
             if (ec + S.maxQ < T && ec + S.minQ > -T) {
                 if (lead) { sm.mode[i] = (uint16_t)MODE_TRANSPARENT; atomicAdd(&stats[3], 1ull); }
                 ec += S.total;
+                ++i;
                 continue;
             }
             const Walk W = walk_coop(sm, units[u], cand + (size_t)u * K, lists, ec, T, warp, lane, spin, err);
@@ -546,6 +611,7 @@ __global__ void __launch_bounds__(32 * CW) k_chain(const Unit *__restrict__ unit
             }
             ec = W.c;
             if (W.into >= 0) { k = (uint32_t)W.into; expl = false; }
+            ++i;
         }
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < cn; i += 32 * CW) umode[B.u0 + c0 + i] = sm.mode[i];
