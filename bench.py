@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--procs", type=int, default=0, help="serving: processes (default 512)")
     p.add_argument("--segs", type=int, default=0, help="serving: segments per process (default 16)")
     p.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
+    p.add_argument("--tune", action="store_true", help="long/plain: run the autotuner before timing")
     p.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -686,6 +687,11 @@ def main():
     ctx = scl.scl_replay_init(scl.config(threshold=meta["threshold"], n_lines=meta["n_lines"],
                                          sample_log_capacity=1 << 20))
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.tune:
+        best, best_ms = scl.scl_autotune(ctx, [seg], stream)
+        tuned = {"unit_events": best.unit_events, "sketch_warps": best.warps_per_block,
+                 "warmup_events": best.ext_events, "final_warps": best.final_warps, "ms": best_ms}
 
     def step():
         scl.scl_trace_reset(ctx, 0, stream)
@@ -808,6 +814,7 @@ def main():
                                                     n + max(0, bstats["units"] - 1) * 32768),
                              "alg_bytes_per_unit": ALG_BYTES[dom]},
                 "kernels_ms_per_step": {k: v[0] / max(1, v[1]) * (v[1] / args.steps) for k, v in ktimes.items()},
+                "tuning": tuned,
                 "gpu_launches": launches,
                 "batch": bstats,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "parity": parity}
