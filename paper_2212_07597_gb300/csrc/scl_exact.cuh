@@ -7,7 +7,8 @@
 // mark sets a new mark and starts tracking the sampled block.
 //
 // 256 events per step.  delta, the python flag and the address are staged through the
-// bulk-copy ring; the line id is read only at the events that trigger a sample.  When
+// copy ring; the line id of a sample is left to k_compact (which reads it for every
+// record in parallel, instead of this warp waiting on one load per sample).  When
 // the unit's resets are known in advance (a reset list from k_sketch) no crossing
 // search runs; otherwise each step's prefix sums locate the crossings.
 //
@@ -125,7 +126,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         if (lane == 0 && n < cap) {
             FRec Rr;
             Rr.rel = rel;
-            Rr.line = U.line[rel];
+            Rr.line = 0;   // filled in by k_compact
             Rr.kind = growth ? 1 : -1;
             Rr.is_hwm = hwm ? 1 : 0;
             Rr.recl = 0;
@@ -148,12 +149,22 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
     bool ok;
     if (!FIRST && in0.list) {
         // ---- the resets are known: no crossing search
+        // the list is read 32 entries at a time (lane j holds entry base + j), the next
+        // 32 loading while the current ones are used
         const SRes *Ls = in0.list;
         const uint32_t nres = in0.nres;
+        auto fetch = [&](uint32_t base, uint32_t &bp, int64_t &bP) {
+            const uint32_t i = base + (uint32_t)lane;
+            if (i < nres) { const SRes q = Ls[i]; bp = q.pos; bP = q.P; } else { bp = 0xffffffffu; bP = 0; }
+        };
+        uint32_t cpos, npos_b;
+        int64_t cP, nP_b;
+        fetch(0, cpos, cP);
+        fetch(32, npos_b, nP_b);
         uint32_t ri = 0;
-        uint32_t npos = 0xffffffffu;
-        int64_t nP = 0;
-        if (nres) { const SRes q = Ls[0]; npos = q.pos; nP = q.P; }
+        uint32_t npos = __shfl_sync(FULL, cpos, 0);
+        int64_t nP = __shfl_sync(FULL, cP, 0);
+        if (!nres) npos = 0xffffffffu;
         int64_t cst = c, Pprev = 0;   // counter at the open window's start, prefix there
         auto kstep = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
             if (npos >= rel0 + (uint32_t)STEP) {
@@ -174,9 +185,13 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                 Pprev = nP;
                 after = r;
                 if (++ri < nres) {
-                    const SRes q = Ls[ri];
-                    npos = q.pos;
-                    nP = q.P;
+                    if ((ri & 31u) == 0) {
+                        cpos = npos_b;
+                        cP = nP_b;
+                        fetch(ri + 32, npos_b, nP_b);
+                    }
+                    npos = __shfl_sync(FULL, cpos, (int)(ri & 31u));
+                    nP = __shfl_sync(FULL, cP, (int)(ri & 31u));
                 } else {
                     npos = 0xffffffffu;
                 }

@@ -293,11 +293,14 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
         Sample *log = a.log ? a.log + (uint64_t)U.trace * a.log_cap : nullptr;
         const uint64_t log_base = st.n_samples + Pn.sample_off;
         LineRow *grow = a.lines + (uint64_t)U.trace * a.n_lines;
-        const FRec *rec = a.recs + U.rec0;
+        FRec *rec = a.recs + U.rec0;
         const uint32_t cnt = O.count < U.rec_cap ? O.count : U.rec_cap;
         for (uint32_t j = lane; j < cnt; j += 32) {
             const FRec r = rec[j];
-            uint32_t line = r.line;
+            // the line of the sample's event (the replay leaves it to this pass); kept in the
+            // record for the leak epilogue and the state fold
+            uint32_t line = U.line[r.rel];
+            rec[j].line = line;
             bool line_ok = true;
             if (line >= a.n_lines) {
                 set_error(a.err, E_RANGE, line, U.gidx0 + r.rel);

@@ -112,11 +112,19 @@ __device__ bool ring_walk(RingT &sm, const Unit &U, uint64_t from, uint64_t limi
         const uint64_t t0 = t * TILE;
         const uint64_t cnt = limit - t0 < (uint64_t)TILE ? limit - t0 : (uint64_t)TILE;
         if (bulk && cnt == (uint64_t)TILE) {
-            // 16-byte chunks j of the 8-byte columns land at their permuted places
-            for (int j = lane; j < TILE / 2; j += 32) {
-                const int r = j >> 2, cc = swz_chunk(r, j & 3);
-                cp_async16(&sm.d[s][8 * r + 2 * cc], U.delta + t0 + 2 * j);
-                if (ADDR) cp_async16(sm.a(s) + 8 * r + 2 * cc, U.addr + t0 + 2 * j);
+            // 16-byte chunks j = lane + 32 i of the 8-byte columns land at their permuted
+            // places: row (lane >> 2) + 8 i, chunk swz_chunk(row, lane & 3), which does not
+            // depend on i -- one offset per lane, 64 elements further per i
+            const int off = 8 * (lane >> 2) + 2 * swz_chunk(lane >> 2, lane & 3);
+            const int64_t *gd = U.delta + t0 + 2 * lane;
+            int64_t *sd = &sm.d[s][off];
+#pragma unroll
+            for (int i = 0; i < TILE / 64; ++i) cp_async16(sd + 64 * i, gd + 64 * i);
+            if (ADDR) {
+                const uint64_t *ga = U.addr + t0 + 2 * lane;
+                uint64_t *sa = sm.a(s) + off;
+#pragma unroll
+                for (int i = 0; i < TILE / 64; ++i) cp_async16(sa + 64 * i, ga + 64 * i);
             }
             if (ADDR)
                 for (int j = lane; j < TILE / 16; j += 32) cp_async16(sm.p(s) + 16 * j, U.py + t0 + 16 * j);
