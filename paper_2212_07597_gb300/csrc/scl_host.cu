@@ -56,6 +56,11 @@ struct scl_ctx {
     // side stream between a fork after the sketch and a join before the state fold
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // host-to-device staging of scl_replay_batch_host: pieces spread over several copy
+    // streams (several copy engines at once), joined back before the replay
+    static constexpr int NCS = 4;
+    cudaStream_t cstream[NCS] = {};
+    cudaEvent_t cev[NCS + 1] = {};
     // tuning
     scl_tuning tune{};
     // graph replay of repeated identical batches
@@ -397,6 +402,10 @@ void scl_replay_free(scl_ctx *c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
+    for (int i = 0; i < scl_ctx::NCS; ++i)
+        if (c->cstream[i]) cudaStreamDestroy(c->cstream[i]);
+    for (int i = 0; i <= scl_ctx::NCS; ++i)
+        if (c->cev[i]) cudaEventDestroy(c->cev[i]);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     delete c;
 }
@@ -438,6 +447,10 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    for (int i = 0; i < scl_ctx::NCS && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&c->cstream[i], cudaStreamNonBlocking);
+    for (int i = 0; i <= scl_ctx::NCS && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&c->cev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         int r = cuda_fail(c, e, "context allocation");
         fprintf(stderr, "scl_replay_init: %s\n", c->err.c_str());
@@ -691,10 +704,20 @@ int scl_replay_batch_host(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, v
     if (r) return r;
     std::vector<scl_segment> dsegs(segs, segs + nsegs);
     char *p = static_cast<char *>(c->stage.p);
+    // the copies start after the stream's earlier work (which may still read the staging
+    // buffer); pieces of at most 64 MiB go round-robin over the copy streams
+    CK(cudaEventRecord(c->cev[scl_ctx::NCS], s), "staging fork");
+    for (int i = 0; i < scl_ctx::NCS; ++i) CK(cudaStreamWaitEvent(c->cstream[i], c->cev[scl_ctx::NCS], 0), "staging fork");
+    int next_cs = 0;
     auto put = [&](const void *src, size_t bytes) -> const void * {
         char *dst = p;
-        if (bytes) {
-            if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return nullptr;
+        constexpr size_t PIECE = size_t(64) << 20;
+        for (size_t o = 0; o < bytes; o += PIECE) {
+            const size_t b = bytes - o < PIECE ? bytes - o : PIECE;
+            if (cudaMemcpyAsync(dst + o, static_cast<const char *>(src) + o, b, cudaMemcpyHostToDevice,
+                                c->cstream[next_cs]) != cudaSuccess)
+                return nullptr;
+            next_cs = (next_cs + 1) % scl_ctx::NCS;
         }
         p += al256(bytes);
         return dst;
@@ -715,6 +738,10 @@ int scl_replay_batch_host(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, v
         d.cp.is_python = static_cast<const uint8_t *>(put(g.cp.is_python, g.cp.n));
         if (!d.ev.delta || !d.ev.addr || !d.ev.line || !d.ev.is_python || !d.cp.size || !d.cp.line || !d.cp.is_python)
             return fail(c, SCL_ECUDA, "host to device copy failed");
+    }
+    for (int i = 0; i < scl_ctx::NCS; ++i) {
+        CK(cudaEventRecord(c->cev[i], c->cstream[i]), "staging join");
+        CK(cudaStreamWaitEvent(s, c->cev[i], 0), "staging join");
     }
     return scl_replay_batch(c, dsegs.data(), nsegs, stream);
 }

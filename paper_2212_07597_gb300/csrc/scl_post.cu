@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(NT) k_copy_apply(LaunchPost a) {
         if (j >= C.len) break;
         const unsigned long long sz = mine[k];
         unsigned long long q;
-        if (sz >= 8 * Tc) {
+        if (sz / 8 >= Tc) {   // (8 * T_c could overflow for T_c above 2^61)
             q = (rem + sz) / Tc;
             rem = (rem + sz) % Tc;
         } else {

@@ -274,3 +274,34 @@ def test_long_trace_all_samples_exact():
     # the warm-up candidates carry the true counter into almost every unit
     st = scl.scl_batch_stats(ctx)
     assert st["walked"] <= max(4, st["units"] // 8), st
+
+
+def test_edge_cases_tiny_traces_one_line_huge_threshold():
+    # one line id only; traces of 0, 1 and 2 events; a threshold no trace reaches
+    ctx = gpu_ctx(1000, n_lines=1, max_traces=4)
+    d1 = np.array([5000], np.int64)                    # one malloc of 5 T: one growth sample
+    d2 = np.array([999, -999], np.int64)               # never reaches T
+    mk = lambda d: tg.Trace(d, np.arange(1, len(d) + 1, dtype=np.uint64) * 16, np.zeros(len(d), np.uint32),
+                            np.ones(len(d), np.uint8))
+    trs = [mk(d1), mk(d2), mk(np.zeros(0, np.int64))]
+    keep = replay(ctx, [(0, trs[0]), (1, trs[1]), (2, trs[2])])
+    for i, tr in enumerate(trs):
+        assert_same(ctx, i, oracle_of(tr, 1000, n_lines=1))
+    assert len(scl.scl_samples(ctx, 0)) == 1 and len(scl.scl_samples(ctx, 1)) == 0
+    scl.scl_replay_batch(ctx, [])                      # an empty batch is a no-op
+    scl.scl_sync(ctx)
+    big = gpu_ctx(1 << 61)   # T_c = 2 T must stay within int64
+    tr = tg.plain_trace(40_000, seed=31)
+    keep = replay(big, [(0, tr)])
+    assert_same(big, 0, oracle_of(tr, 1 << 61))
+    assert len(scl.scl_samples(big, 0)) == 0
+
+
+def test_host_entry_point_many_pieces_over_copy_streams():
+    # host arrays larger than one staging piece go over several copy streams
+    tr = tg.plain_trace(9_000_000, seed=33)
+    ctx = gpu_ctx(T0, log_cap=1 << 18)
+    seg = scl.segment(0, tr.delta, tr.addr, tr.line, tr.is_python, tr.csize, tr.cline, tr.cpy)
+    scl.scl_replay_batch_host(ctx, [seg])
+    scl.scl_sync(ctx)
+    assert_same(ctx, 0, oracle_of(tr, T0))
