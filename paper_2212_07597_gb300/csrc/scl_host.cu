@@ -54,8 +54,8 @@ struct scl_ctx {
     bool plan_pending = false;
     // the copy-volume pass (Section 3.5) shares nothing with the event path: it runs on a
     // side stream between a fork after the sketch and a join before the state fold
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side = nullptr, hi = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
     // host-to-device staging of scl_replay_batch_host: pieces spread over several copy
     // streams (several copy engines at once), joined back before the replay
     static constexpr int NCS = 4;
@@ -214,6 +214,12 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * q.nbt, s), "memset");
     CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
     CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 5, s), "memset");
+    // the kernels of the event path run on a high-priority stream forked from the caller's,
+    // so the copy-volume pass on the side stream takes only what they leave of the SMs
+    cudaStream_t s_user = s;
+    CK(cudaEventRecord(c->ev_in, s_user), "fork event");
+    s = c->hi;
+    CK(cudaStreamWaitEvent(s, c->ev_in, 0), "fork the event path");
 
     const Unit *d_units = reinterpret_cast<const Unit *>(dp + q.o_units);
     const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + q.o_bts);
@@ -350,6 +356,8 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         Prof p(c, s, "state");
         CK(launch_state(a, s), "launch state");
     }
+    CK(cudaEventRecord(c->ev_out, s), "join event");
+    CK(cudaStreamWaitEvent(s_user, c->ev_out, 0), "join the event path");
     return SCL_OK;
 }
 
@@ -402,6 +410,9 @@ void scl_replay_free(scl_ctx *c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->hi) cudaStreamDestroy(c->hi);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
     for (int i = 0; i < scl_ctx::NCS; ++i)
         if (c->cstream[i]) cudaStreamDestroy(c->cstream[i]);
     for (int i = 0; i <= scl_ctx::NCS; ++i)
@@ -445,6 +456,13 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     for (int i = 0; i < scl_ctx::NCS && e == cudaSuccess; ++i)
