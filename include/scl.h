@@ -170,8 +170,11 @@ const char *scl_last_error(const scl_ctx *ctx);
 int scl_replay_batch(scl_ctx *ctx, const scl_segment *segs, uint32_t nsegs, void *cuda_stream);
 
 /* Same as scl_replay_batch but the event arrays are in HOST memory: the library
- * copies them to its own device staging buffers on cuda_stream first (pinned
- * host memory makes those copies asynchronous). */
+ * copies them to its own device staging buffers on cuda_stream first, in pieces over
+ * several copy streams (pinned host memory makes those copies asynchronous).  An event
+ * line column in pinned, device-mapped memory is not copied: the kernels read it in
+ * place at the events that sample.  Host arrays must stay valid until the stream work
+ * of the call has finished. */
 int scl_replay_batch_host(scl_ctx *ctx, const scl_segment *segs, uint32_t nsegs, void *cuda_stream);
 
 /* Wait for the work of the last replay call; return the first recorded device error. */

@@ -11,6 +11,7 @@
 #include "../../include/scl.h"
 #include "scl_internal.cuh"
 #include "scl_launch.h"
+#include "scl_views.h"
 
 using namespace scl;
 
@@ -722,6 +723,7 @@ int scl_replay_batch_host(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, v
     if (r) return r;
     std::vector<scl_segment> dsegs(segs, segs + nsegs);
     char *p = static_cast<char *>(c->stage.p);
+    DeviceViews views;
     // the copies start after the stream's earlier work (which may still read the staging
     // buffer); pieces of at most 64 MiB go round-robin over the copy streams
     CK(cudaEventRecord(c->cev[scl_ctx::NCS], s), "staging fork");
@@ -749,7 +751,12 @@ int scl_replay_batch_host(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, v
             return fail(c, SCL_EINVAL, "segment %u: NULL memcpy array", i);
         d.ev.delta = static_cast<const int64_t *>(put(g.ev.delta, g.ev.n * 8));
         d.ev.addr = static_cast<const uint64_t *>(put(g.ev.addr, g.ev.n * 8));
-        d.ev.line = static_cast<const uint32_t *>(put(g.ev.line, g.ev.n * 4));
+        // event line ids are read only at the few events that sample (Section 3.3): a
+        // device-accessible (pinned) host column is read in place instead of copied
+        if (const void *lv = g.ev.n ? views.view(g.ev.line) : nullptr)
+            d.ev.line = static_cast<const uint32_t *>(lv);
+        else
+            d.ev.line = static_cast<const uint32_t *>(put(g.ev.line, g.ev.n * 4));
         d.ev.is_python = static_cast<const uint8_t *>(put(g.ev.is_python, g.ev.n));
         d.cp.size = static_cast<const uint64_t *>(put(g.cp.size, g.cp.n * 8));
         d.cp.line = static_cast<const uint32_t *>(put(g.cp.line, g.cp.n * 4));
