@@ -628,7 +628,7 @@ def run_serving(args):
             f"MISMATCH vs oracle on processes {[p for p, k in zip(pick, oks) if not k]}"
 
     if rank == 0:
-        h2d = 21 * N + 13 * M
+        h2d = 17 * N + 13 * M   # the event line column is read in place (pinned), not moved
         line = {"metric": "alloc/free events replayed per second (bit-exact)", "value": value, "unit": "events/s",
                 "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
                 "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -253,7 +253,8 @@ int scl_batch_stats(scl_ctx *ctx, scl_batch_info *out);
  * asynchronous copies), each with an offered arrival time; requests of one trace appear
  * in arrival order.  scl_serve admits arrived requests into a batch while its device
  * staging slot has room (three slots sized from the budget), copies a slot's arrays to
- * the device on a copy stream while the previous batch replays on a compute stream, and
+ * the device on a copy stream while the previous batch replays on a compute stream (a
+ * pinned event line column is read in place instead), and
  * replays each batch with scl_replay_batch; a trace's results equal those of replaying
  * its requests alone, in order.  The call returns when every request has been replayed
  * (then scl_sync's status). */

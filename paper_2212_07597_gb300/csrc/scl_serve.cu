@@ -11,7 +11,8 @@
 //     arrived while the device was busy forms the next batch).  Arrays in pinned (or
 //     device) memory are gathered into the slot by one kernel per batch that reads them
 //     through their device addresses, instead of one copy call per array; pageable
-//     arrays are copied with cudaMemcpyAsync;
+//     arrays are copied with cudaMemcpyAsync; a pinned event line column is not moved
+//     at all (the kernels read line ids in place, only at the events that sample);
 //   - a slot is reused only after the event recorded behind its replay has completed,
 //     which is also when its requests' completion times are taken.
 // Segments of one process keep their arrival order: they are replayed in that order
@@ -217,7 +218,13 @@ extern "C" int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, cons
             g.ev.n = r.ev.n;
             g.ev.delta = static_cast<const int64_t *>(put(r.ev.delta, r.ev.n * 8));
             g.ev.addr = static_cast<const uint64_t *>(put(r.ev.addr, r.ev.n * 8));
-            g.ev.line = static_cast<const uint32_t *>(put(r.ev.line, r.ev.n * 4));
+            // event line ids are read only where a sample fires: a pinned column is read in place
+            if (const void *lv = r.ev.n ? views.view(r.ev.line) : nullptr) {
+                g.ev.line = static_cast<const uint32_t *>(lv);
+                p += al256(r.ev.n * 4);
+            } else {
+                g.ev.line = static_cast<const uint32_t *>(put(r.ev.line, r.ev.n * 4));
+            }
             g.ev.is_python = static_cast<const uint8_t *>(put(r.ev.is_python, r.ev.n));
             g.cp.n = r.cp.n;
             g.cp.size = static_cast<const uint64_t *>(put(r.cp.size, r.cp.n * 8));
