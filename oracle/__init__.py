@@ -89,6 +89,9 @@ def _bind(path: str):
     lib.orc_replay_copies.restype = ctypes.c_int
     lib.orc_leak_score.argtypes = [ctypes.POINTER(_State), ctypes.c_uint32,
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.orc_rate_samples.argtypes = [P, P, P, ctypes.c_uint64, P, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_uint32, P, P]
+    lib.orc_rate_samples.restype = None
     return lib
 
 
@@ -175,6 +178,23 @@ class Oracle:
                     tracked_valid=s.tracked_valid, tracked_reclaimed=s.tracked_reclaimed,
                     tracked_addr=s.tracked_addr, tracked_line=s.tracked_line, tracked_idx=s.tracked_idx,
                     n_events=s.n_events, n_copies=s.n_copies, copy_counter=s.copy_counter)
+
+
+def rate_samples(delta, line, is_python, gaps, consumed=0, n_lines=256, lib_path=None):
+    """Rate-based sampling (Section 3.2's baseline) over one event stream: returns the
+    per-(line, flag) sample counts [n_lines, 2] and the state (samples, gaps used,
+    bytes of the next gap consumed, flags)."""
+    lib = _bind(lib_path) if lib_path else _load()
+    delta = np.ascontiguousarray(delta, dtype=np.int64)
+    line = np.ascontiguousarray(line, dtype=np.uint32)
+    is_python = np.ascontiguousarray(is_python, dtype=np.uint8)
+    gaps = np.ascontiguousarray(gaps, dtype=np.uint64)
+    counts = np.zeros(2 * n_lines, np.uint64)
+    state = np.zeros(4, np.uint64)
+    lib.orc_rate_samples(_ptr(delta, np.int64), _ptr(line, np.uint32), _ptr(is_python, np.uint8), len(delta),
+                         _ptr(gaps, np.uint64), len(gaps), int(consumed), n_lines, counts.ctypes.data,
+                         state.ctypes.data)
+    return counts.reshape(n_lines, 2), state
 
 
 def replay(delta, addr, line, is_python, threshold, n_lines=256, copies=None, **kw) -> Oracle:

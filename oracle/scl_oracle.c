@@ -145,3 +145,35 @@ void orc_leak_score(const orc_state *st, uint32_t line, int64_t *num, int64_t *d
         *num = *den - (f + 1);
     }
 }
+
+/* Section 3.2, rate-based sampling: a countdown of bytes to the next sampled byte,
+ * decremented by each allocation and free; each time it runs out, a sample, and the
+ * countdown restarts from the next gap.  Reading: every sampled byte is a sample, so an
+ * event spanning several sampled bytes takes several. */
+void orc_rate_samples(const int64_t *delta, const uint32_t *line, const uint8_t *is_python, uint64_t n,
+                      const uint64_t *gap, uint64_t n_gaps, uint64_t consumed, uint32_t n_lines,
+                      uint64_t *counts, uint64_t *state) {
+    memset(counts, 0, sizeof(uint64_t) * 2 * (size_t)n_lines);
+    uint64_t samples = 0, k = 0, flags = 0;
+    /* left = bytes until (and including) the next sampled byte */
+    uint64_t left = n_gaps ? gap[0] - consumed : 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const int64_t d = delta[i];
+        uint64_t b = d < 0 ? (uint64_t)0 - (uint64_t)d : (uint64_t)d;
+        while (b > 0) {
+            if (k >= n_gaps) { flags |= 1; break; }
+            if (b < left) { left -= b; b = 0; break; }
+            /* the sampled byte falls in this event */
+            b -= left;
+            if (line[i] < n_lines) counts[2 * (size_t)line[i] + (is_python[i] ? 1 : 0)] += 1;
+            else flags |= 2;
+            ++samples;
+            ++k;
+            left = k < n_gaps ? gap[k] : 0;
+        }
+    }
+    state[0] = samples;
+    state[1] = k;
+    state[2] = k < n_gaps ? gap[k] - left : 0;
+    state[3] = flags;
+}

@@ -76,4 +76,15 @@ int orc_replay_copies(orc_state *st, const uint64_t *size, const uint32_t *line,
 /* leak likelihood of one line as an unreduced fraction num/den */
 void orc_leak_score(const orc_state *st, uint32_t line, int64_t *num, int64_t *den);
 
+/* Rate-based sampling (Section 3.2, the baseline the threshold sampler is compared with):
+ * every byte allocated or freed is a Bernoulli trial; the sampled bytes sit at cumulative
+ * byte positions B_k = gap[0] - consumed + gap[1] + ... + gap[k] (gaps >= 1 are given).
+ * Event i, moving |delta[i]| bytes, takes one sample per B_k in its byte range, counted in
+ * counts[2 * line[i] + (is_python[i] != 0)].  state[0] = samples, state[1] = gaps used up,
+ * state[2] = bytes of the next gap consumed, state[3] = flags (1 gaps exhausted, 2 line id
+ * >= n_lines, 4 byte count overflow).  counts[2 * n_lines] is cleared first. */
+void orc_rate_samples(const int64_t *delta, const uint32_t *line, const uint8_t *is_python, uint64_t n,
+                      const uint64_t *gap, uint64_t n_gaps, uint64_t consumed, uint32_t n_lines,
+                      uint64_t *counts, uint64_t *state);
+
 #endif

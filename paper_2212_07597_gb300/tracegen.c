@@ -280,6 +280,22 @@ int tg_arrivals(uint64_t count, double mean_gap_ns, uint64_t seed, uint64_t *out
     return 0;
 }
 
+/* Gaps between sampled bytes of a rate-based sampler with one sample per `mean` bytes on
+ * average: each byte is a Bernoulli trial with p = 1/mean, so the gap (bytes from one
+ * sampled byte to the next, >= 1) is geometric: 1 + floor(ln(U) / ln(1 - p)) for U in (0, 1]. */
+int tg_gaps(uint64_t count, double mean, uint64_t seed, uint64_t *out) {
+    if (!(mean >= 1.0)) return -1;
+    uint64_t s = mix_seed(seed ^ 0x6A09E667F3BCC909ull, 0);
+    const double l1p = mean > 1.0 ? det_log(1.0 - 1.0 / mean) : -1.0;
+    for (uint64_t i = 0; i < count; ++i) {
+        const double u = 1.0 - u01(&s);   /* (0, 1] */
+        double g = mean > 1.0 ? det_log(u) / l1p : 0.0;
+        if (g > 9.0e18) g = 9.0e18;
+        out[i] = 1u + (uint64_t)g;
+    }
+    return 0;
+}
+
 /* test hooks for the deterministic helpers */
 double tg_det_exp(double y) { return det_exp(y); }
 double tg_det_log(double x) { return det_log(x); }

@@ -71,11 +71,13 @@ def _load():
             lib.tg_constant.argtypes = [U64, ctypes.c_int64, U32, U64, U64, P, P, P, P]
             lib.tg_lengths.argtypes = [U64, U64, U64, U64, P]
             lib.tg_arrivals.argtypes = [U64, ctypes.c_double, U64, P]
+            lib.tg_gaps.argtypes = [U64, ctypes.c_double, U64, P]
             lib.tg_det_exp.argtypes = [ctypes.c_double]
             lib.tg_det_exp.restype = ctypes.c_double
             lib.tg_det_log.argtypes = [ctypes.c_double]
             lib.tg_det_log.restype = ctypes.c_double
-            for f in ("tg_events", "tg_copies", "tg_adversarial", "tg_constant", "tg_lengths", "tg_arrivals"):
+            for f in ("tg_events", "tg_copies", "tg_adversarial", "tg_constant", "tg_lengths", "tg_arrivals",
+                      "tg_gaps"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -165,6 +167,14 @@ def lengths(count: int, lo: int, hi: int, seed: int = 0) -> np.ndarray:
 def arrivals_ns(count: int, mean_gap_ns: float, seed: int = 0) -> np.ndarray:
     out = np.empty(count, np.uint64)
     _load().tg_arrivals(count, mean_gap_ns, seed, out.ctypes.data)
+    return out
+
+
+def gaps(count: int, mean: float, seed: int = 0) -> np.ndarray:
+    """Geometric gaps (>= 1) between the sampled bytes of a rate-based sampler, mean `mean`."""
+    out = np.empty(count, np.uint64)
+    if _load().tg_gaps(count, float(mean), seed, out.ctypes.data):
+        raise ValueError("mean must be >= 1")
     return out
 
 

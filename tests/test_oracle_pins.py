@@ -329,6 +329,75 @@ def test_segmentation_invariance():
     assert o.state() == whole.state()
 
 
+# ------------------------------------------------------------------ rate-based sampling (Section 3.2)
+
+def _rate_brute(delta, line, py, gaps, consumed, n_lines):
+    """Byte by byte: expand every event into the bytes it moves and mark the bytes at the
+    cumulative gap positions (an independent restatement of the Bernoulli-per-byte model)."""
+    owner = []                                   # event index of every byte moved
+    for i, d in enumerate(delta):
+        owner += [i] * abs(int(d))
+    counts = [[0, 0] for _ in range(n_lines)]
+    pos, k, n = int(gaps[0]) - consumed if len(gaps) else None, 0, 0
+    while k < len(gaps) and pos <= len(owner):
+        i = owner[pos - 1]
+        counts[int(line[i])][1 if py[i] else 0] += 1
+        n += 1
+        k += 1
+        if k < len(gaps):
+            pos += int(gaps[k])
+    return counts, n, k
+
+
+def test_rate_sampler_against_bytes(lib_path=None):
+    rng = random.Random(5)
+    for _ in range(300):
+        n = rng.randint(0, 12)
+        delta = np.array([rng.randint(-9, 9) for _ in range(n)], np.int64)
+        line = np.array([rng.randint(0, 2) for _ in range(n)], np.uint32)
+        py = np.array([rng.randint(0, 1) for _ in range(n)], np.uint8)
+        total = int(np.abs(delta).sum())
+        gaps = np.array([rng.randint(1, 6) for _ in range(total + 2)], np.uint64)
+        consumed = rng.randint(0, int(gaps[0]) - 1)
+        counts, st = oracle.rate_samples(delta, line, py, gaps, consumed, n_lines=3, lib_path=lib_path)
+        want, nb, used = _rate_brute(delta, line, py, gaps, consumed, 3)
+        assert counts.tolist() == want and int(st[0]) == nb and int(st[1]) == used and int(st[3]) == 0
+        # bytes of the next gap consumed: total bytes minus the bytes up to the last sample
+        upto = consumed + total
+        done = int(gaps[:used].astype(object).sum()) if used else 0
+        assert int(st[2]) == upto - done
+
+
+@pytest.mark.parametrize("c,consumed", [(1, 0), (7, 3), (1_048_573, 12345)])
+def test_rate_sampler_closed_forms(c, consumed, lib_path=None):
+    # constant gaps c: one sample per c bytes, counted from `consumed` bytes into the first
+    # gap -- floor((consumed + S) / c) samples (with c = 1: every byte)
+    tr = tg.plain_trace(20_000, seed=9, n_lines=8)
+    S = int(np.abs(tr.delta).astype(object).sum())
+    K = (consumed + S) // c
+    gaps = np.full(K + 1, c, np.uint64)
+    counts, st = oracle.rate_samples(tr.delta, tr.line, tr.is_python, gaps, consumed, n_lines=8, lib_path=lib_path)
+    assert int(st[0]) == K and int(counts.sum()) == K and int(st[3]) == 0
+    assert int(st[2]) == (consumed + S) % c
+
+
+def test_rate_sampler_segments_and_exhaustion():
+    tr = tg.plain_trace(30_000, seed=11, n_lines=16)
+    gaps = tg.gaps(100_000, 1_000_000, seed=3)
+    whole, sw = oracle.rate_samples(tr.delta, tr.line, tr.is_python, gaps, 0, n_lines=16)
+    acc = np.zeros_like(whole)
+    k, used_bytes = 0, 0
+    for a_, b_ in ((0, 7_001), (7_001, 19_999), (19_999, tr.n)):
+        c_, st = oracle.rate_samples(tr.delta[a_:b_], tr.line[a_:b_], tr.is_python[a_:b_], gaps[k:], used_bytes,
+                                     n_lines=16)
+        acc += c_
+        k += int(st[1])
+        used_bytes = int(st[2])
+    assert np.array_equal(acc, whole) and k == int(sw[1]) and used_bytes == int(sw[2])
+    few, st = oracle.rate_samples(tr.delta, tr.line, tr.is_python, gaps[:3], 0, n_lines=16)
+    assert int(st[0]) == 3 and int(st[3]) & 1   # ran out of gaps
+
+
 # ------------------------------------------------------------------ mutants
 
 _MUTANTS = {
@@ -349,6 +418,9 @@ _MUTANTS = {
     "footprint_before_event": ("s.footprint = st->footprint;", "s.footprint = st->footprint - d;"),
     "line_of_previous_event": ("s.line = line[i];", "s.line = line[i > 0 ? i - 1 : 0];"),
     "hwm_start_zero": ("st->hwm = cfg->initial_footprint;", "st->hwm = 0;"),
+    "rate_sample_one_byte_late": ("if (b < left) { left -= b; b = 0; break; }", "if (b <= left) { left -= b; b = 0; break; }"),
+    "rate_one_sample_per_event": ("left = k < n_gaps ? gap[k] : 0;", "left = k < n_gaps ? gap[k] : 0; b = 0;"),
+    "rate_frees_not_counted": ("uint64_t b = d < 0 ? (uint64_t)0 - (uint64_t)d : (uint64_t)d;", "uint64_t b = d < 0 ? 0 : (uint64_t)d;"),
 }
 
 
@@ -361,6 +433,9 @@ def _pins_pass(lib_path) -> bool:
             test_golden_worked_scenarios(name, lib_path)
         for phase in (0, 12345):
             test_copy_sampler_closed_form(phase, lib_path)
+        test_rate_sampler_against_bytes(lib_path)
+        for c, consumed in ((1, 0), (7, 3)):
+            test_rate_sampler_closed_forms(c, consumed, lib_path)
     except AssertionError:
         return False
     return True
