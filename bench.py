@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
     p.add_argument("--tune", action="store_true", help="long/plain: run the autotuner before timing")
     p.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
+    p.add_argument("--no-rate", action="store_true", help="long/plain: skip the rate-based sampling comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -778,6 +779,34 @@ def main():
         e2e = {"value": n * ksteps * ws / el, "unit": "events/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": ksteps}
 
+    # the Table 2 comparison: rate-based sampling (one sample per T bytes moved on average,
+    # geometric gaps) over the same trace, against the threshold sampler's sample count
+    rate = None
+    if not args.no_rate:
+        from paper_2212_07597_gb300 import tracegen as tg
+        total_bytes = int(np.abs(tr.delta).sum(dtype=np.uint64))
+        T = meta["threshold"]
+        gaps = tg.gaps(int(total_bytes / T * 1.1) + 1024, T, seed=11 + rank)
+        gd = torch.from_numpy(gaps.view(np.int64)).to(dev)
+        d_delta, d_line, d_py = keep[0], keep[2], keep[3]
+        scl.scl_rate_samples(ctx, d_delta, d_line, d_py, gd, 0, stream)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        r0.record(stream)
+        for _ in range(reps):
+            rc, rs = scl.scl_rate_samples(ctx, d_delta, d_line, d_py, gd, 0, stream)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        rms = r0.elapsed_time(r1) / reps
+        step()
+        scl.scl_sync(ctx)
+        thr = scl.scl_trace_state(ctx, 0)["n_samples"]
+        rate = {"rate_samples": int(rs[0]), "threshold_samples": int(thr),
+                "ratio": int(rs[0]) / max(1, int(thr)), "gap_mean_bytes": T, "flags": int(rs[3]),
+                "ms": rms, "events_per_s": n / (rms / 1e3),
+                "note": "rate-based sampling (Section 3.2 baseline) on the same trace; ms includes "
+                        "the synchronising read-back of the counts"}
+
     # oracle on this host: timed baseline and exact check of the last GPU step
     cpu = None
     parity = None
@@ -819,7 +848,7 @@ def main():
                 "tuning": tuned,
                 "gpu_launches": launches,
                 "batch": bstats,
-                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "parity": parity}
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "rate_based": rate}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

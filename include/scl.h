@@ -289,6 +289,22 @@ typedef struct {
 int scl_serve(scl_ctx *ctx, const scl_request *reqs, uint32_t n, const scl_serve_opts *opts,
               scl_request_result *out, scl_serve_summary *summary);
 
+/* Rate-based sampling (Section 3.2): the conventional sampler the paper compares threshold
+ * sampling with (its Table 2).  Every byte allocated or freed is a Bernoulli trial; the
+ * sampled bytes sit at cumulative byte positions B_k = gap[0] - consumed + gap[1] + ... +
+ * gap[k], where gap[] (device, n_gaps values >= 1) are the caller's draws -- geometric with
+ * mean T for the paper's sampler -- and consumed (< gap[0]) is how far the previous call got
+ * into gap[0].  Event i of delta/line/is_python (device, n events) moves |delta[i]| bytes and
+ * takes one sample per B_k in its byte range (a large event can take several), counted in
+ * counts_out[2 * line + (is_python != 0)] (device, 2 * n_lines, cleared by the call).
+ * state_out (device, 4): samples taken, gaps used up (continue with gap + that count),
+ * bytes of the next gap consumed (the next call's `consumed`), flags (1: the gaps ran out
+ * before the bytes did, 2: a sampled event's line id >= n_lines, not counted, 4: the byte
+ * count passed 2^64).  Asynchronous on cuda_stream; scratch comes from the context. */
+int scl_rate_samples(scl_ctx *ctx, const int64_t *delta, const uint32_t *line, const uint8_t *is_python, uint64_t n,
+                     const uint64_t *gap, uint64_t n_gaps, uint64_t consumed, uint64_t *counts_out,
+                     uint64_t *state_out, void *cuda_stream);
+
 /* Failure-detection self test (no counterpart in the paper): launches one warp that
  * waits, with the same bounded wait the walker uses, on a barrier nothing arrives at.
  * The wait gives up after `limit` polls and the call returns SCL_ETIMEOUT; the

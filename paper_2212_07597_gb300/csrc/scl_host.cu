@@ -49,6 +49,7 @@ struct scl_ctx {
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
     DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
+    DevBuf rate;   // scratch of scl_rate_samples
     void *h_plan = nullptr;
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
@@ -397,7 +398,7 @@ void scl_replay_free(scl_ctx *c) {
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->lists, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
-                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage})
+                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
@@ -963,6 +964,23 @@ int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
     out->transparent = v[3];
     out->unit_events = c->tune.unit_events;
     out->walked_events = v[4];
+    return SCL_OK;
+}
+
+int scl_rate_samples(scl_ctx *c, const int64_t *delta, const uint32_t *line, const uint8_t *is_python, uint64_t n,
+                     const uint64_t *gap, uint64_t n_gaps, uint64_t consumed, uint64_t *counts_out,
+                     uint64_t *state_out, void *stream) {
+    if (!c) return SCL_EINVAL;
+    if ((n && (!delta || !line || !is_python)) || (n_gaps && !gap) || !counts_out || !state_out)
+        return fail(c, SCL_EINVAL, "rate samples: NULL array");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int r = ensure(c, c->rate, rate_scratch_bytes(n, n_gaps), s, "rate-sampling scratch");
+    if (r) return r;
+    CK(launch_rate(delta, line, is_python, n, gap, n_gaps, consumed, c->cfg.n_lines, counts_out, state_out, c->rate.p,
+                   s),
+       "launch rate sampling");
+    c->last_stream = s;
     return SCL_OK;
 }
 

@@ -106,6 +106,14 @@ cudaError_t launch_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines
 
 }  // namespace scl
 
+// rate-based sampling (scl_rate.cu): scratch bytes and the launch sequence
+namespace scl {
+size_t rate_scratch_bytes(uint64_t n, uint64_t ng);
+cudaError_t launch_rate(const int64_t *delta, const uint32_t *line, const uint8_t *py, uint64_t n,
+                        const uint64_t *gap, uint64_t ng, uint64_t consumed, uint32_t n_lines, uint64_t *counts,
+                        uint64_t *state, void *scratch, cudaStream_t s);
+}  // namespace scl
+
 // context facts the serving loop needs (scl_serve.cu); defined in scl_host.cu
 struct scl_ctx;
 uint32_t scl_ctx_max_traces(const scl_ctx *c);

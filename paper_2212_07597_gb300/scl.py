@@ -31,7 +31,7 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_replay_batch_host", "scl_sync", "scl_samples", "scl_line_stats", "scl_leak_scores",
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
-           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve")
+           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve", "scl_rate_samples")
 
 
 class SclError(RuntimeError):
@@ -143,6 +143,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scl_batch_stats": ([P, P], I),
             "scl_graph_enable": ([P, I], I),
             "scl_serve": ([P, P, U32, P, P, P], I),
+            "scl_rate_samples": ([P, P, P, P, U64, P, U64, U64, P, P, P], I),
             "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -355,6 +356,19 @@ def scl_serve(ctx: Context, reqs, hbm_budget: int = 0, max_batch: int = 0, realt
     _check(ctx, load().scl_serve(ctx.handle, arr, len(reqs), ctypes.byref(opts), out.ctypes.data,
                                  ctypes.byref(sm)))
     return out[:len(reqs)], {k: getattr(sm, k) for k, _ in scl_serve_summary._fields_}
+
+
+def scl_rate_samples(ctx: Context, delta, line, is_python, gap, consumed: int = 0, stream=None):
+    """Rate-based sampling over device arrays (torch CUDA tensors); returns
+    (counts [n_lines, 2], state [4]) as numpy arrays after synchronising the stream."""
+    import torch
+    dev = gap.device
+    counts = torch.empty(2 * ctx.cfg.n_lines, dtype=torch.int64, device=dev)
+    state = torch.empty(4, dtype=torch.int64, device=dev)
+    _check(ctx, load().scl_rate_samples(ctx.handle, _ptr(delta), _ptr(line), _ptr(is_python), len(delta), _ptr(gap),
+                                        len(gap), int(consumed), _ptr(counts), _ptr(state), _stream(stream)))
+    torch.cuda.synchronize(dev)
+    return counts.cpu().numpy().view(np.uint64).reshape(-1, 2), state.cpu().numpy().view(np.uint64)
 
 
 def scl_profile_enable(ctx: Context, on: bool = True) -> None:
