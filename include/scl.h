@@ -142,6 +142,23 @@ typedef struct {
     int64_t num, den;   /* likelihood = num / den under the configured leak_rule; den >= 2 */
 } scl_leak_score;
 
+/* Leak report row (Section 3.4, "Leak Report Filtering and Prioritization").  A line is
+ * reported when its leak likelihood exceeds 95% (20 num > 19 den, exactly) and the trace's
+ * memory grew by at least 1% (100 (footprint - F0) >= high-water mark > 0).  Its leak rate
+ * -- bytes allocated in the windows attributed to the line per elapsed time, with the event
+ * count as time -- is the exact fraction rate_num / rate_den; sort reported rows by it. */
+typedef struct {
+    uint32_t line;
+    uint8_t reported;   /* likely && growth */
+    uint8_t likely;     /* likelihood > 95% */
+    uint8_t growth;     /* the trace's footprint grew by >= 1% (the same for every line) */
+    uint8_t reserved;
+    uint64_t mallocs, frees;
+    int64_t num, den;   /* likelihood, as scl_leak_score */
+    int64_t rate_num;   /* bytes allocated in the line's sample windows */
+    uint64_t rate_den;  /* events elapsed */
+} scl_leak_report_row;
+
 /* Resident sampler state of one trace. */
 typedef struct {
     uint64_t n_events, n_copies, n_samples;
@@ -188,6 +205,7 @@ int scl_samples(scl_ctx *ctx, uint32_t trace, scl_sample *out, uint64_t cap, uin
 int scl_line_stats(scl_ctx *ctx, uint32_t trace, scl_line_stat *out, uint32_t cap, uint32_t *n_out);
 int scl_leak_scores(scl_ctx *ctx, uint32_t trace, scl_leak_score *out, uint32_t cap, uint32_t *n_out);
 int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_info *out);
+int scl_leak_report(scl_ctx *ctx, uint32_t trace, scl_leak_report_row *out, uint32_t cap, uint32_t *n_out);
 
 /* Checkpoint / resume of one trace's resident state (counter, window totals,
  * footprint, mark, tracked block, per-line tables, copy counter; not the sample

@@ -124,6 +124,7 @@ class Oracle:
         if rc:
             raise ValueError(f"orc_init failed ({rc})")
         self.n_lines = n_lines
+        self.initial_footprint = initial_footprint
 
     def __del__(self):
         lib = getattr(self, "_lib", None)
@@ -171,6 +172,24 @@ class Oracle:
             self._lib.orc_leak_score(ctypes.byref(self._st), l, ctypes.byref(a), ctypes.byref(b))
             num[l], den[l] = a.value, b.value
         return num, den
+
+    def leak_report(self) -> list[dict]:
+        """Section 3.4's report filter, per line: reported when the leak likelihood exceeds
+        95% and the trace's memory grew by at least 1%; leak rate = bytes allocated in the
+        line's sample windows per elapsed event (readings: growth = footprint - F0 against
+        the high-water mark; time = events)."""
+        lines = self.lines()
+        num, den = self.leak_scores()
+        st = self.state()
+        hwm, fp, n_ev = int(st["hwm"]), int(st["footprint"]), int(st["n_events"])
+        growth = hwm > 0 and 100 * (fp - self.initial_footprint) >= hwm
+        rows = []
+        for l in range(self.n_lines):
+            likely = 20 * int(num[l]) > 19 * int(den[l])        # likelihood = num / den > 0.95
+            rows.append(dict(line=l, likely=likely, growth=growth, reported=likely and growth,
+                             mallocs=int(lines["mallocs"][l]), frees=int(lines["frees"][l]), num=int(num[l]),
+                             den=int(den[l]), rate_num=int(lines["A"][l]), rate_den=n_ev))
+        return rows
 
     def state(self) -> dict:
         s = self._st

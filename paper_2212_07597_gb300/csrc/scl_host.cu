@@ -50,6 +50,7 @@ struct scl_ctx {
     // batch scratch
     DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
     DevBuf rate;   // scratch of scl_rate_samples
+    DevBuf report; // rows of scl_leak_report
     void *h_plan = nullptr;
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
@@ -398,7 +399,7 @@ void scl_replay_free(scl_ctx *c) {
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->lists, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
-                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate})
+                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
@@ -835,6 +836,24 @@ int scl_leak_scores(scl_ctx *c, uint32_t trace, scl_leak_score *out, uint32_t ca
     CK(launch_scores(c->lines, trace, L, c->cfg.leak_rule, c->scores, c->last_stream), "launch scores");
     CK(cudaMemcpyAsync(out, c->scores, sizeof(scl_leak_score) * L, cudaMemcpyDeviceToHost, c->last_stream),
        "read scores");
+    CK(cudaStreamSynchronize(c->last_stream), "sync");
+    return SCL_OK;
+}
+
+int scl_leak_report(scl_ctx *c, uint32_t trace, scl_leak_report_row *out, uint32_t cap, uint32_t *n_out) {
+    if (!c || !n_out) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    int r = sync_and_check(c);
+    if (r) return r;
+    const uint32_t L = c->cfg.n_lines;
+    *n_out = L;
+    if (cap < L) return fail(c, SCL_ERANGE, "output holds %u rows, %u needed", cap, L);
+    if ((r = ensure(c, c->report, sizeof(scl_leak_report_row) * L, c->last_stream, "leak report"))) return r;
+    CK(launch_report(c->lines, c->traces, trace, L, c->cfg.leak_rule, c->cfg.initial_footprint, c->report.p,
+                     c->last_stream),
+       "launch report");
+    CK(cudaMemcpyAsync(out, c->report.p, sizeof(scl_leak_report_row) * L, cudaMemcpyDeviceToHost, c->last_stream),
+       "read report");
     CK(cudaStreamSynchronize(c->last_stream), "sync");
     return SCL_OK;
 }

@@ -582,7 +582,46 @@ __global__ void k_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines,
     out[l] = s;
 }
 
+struct ReportRow {   // layout of scl_leak_report_row
+    uint32_t line;
+    uint8_t reported, likely, growth, pad;
+    uint64_t mallocs, frees;
+    int64_t num, den, rate_num;
+    uint64_t rate_den;
+};
+
+// Section 3.4's report filter: likelihood above 95% and overall growth of at least 1%;
+// leak rate = bytes allocated in the line's sample windows per event elapsed.
+__global__ void k_report(const LineRow *lines, const DevTrace *traces, uint32_t trace, uint32_t n_lines,
+                         uint32_t rule, int64_t F0, ReportRow *out) {
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_lines) return;
+    const LineRow &r = lines[(uint64_t)trace * n_lines + l];
+    const DevTrace &t = traces[trace];
+    const int64_t m = (int64_t)r.mallocs, f = (int64_t)r.frees;
+    ReportRow o;
+    o.line = l;
+    o.pad = 0;
+    o.mallocs = r.mallocs;
+    o.frees = r.frees;
+    o.den = rule == 0 ? m - f + 2 : m + 2;
+    o.num = o.den - (f + 1);
+    o.likely = (__int128)20 * o.num > (__int128)19 * o.den ? 1 : 0;
+    o.growth = t.hwm > 0 && (__int128)100 * ((__int128)t.footprint - F0) >= (__int128)t.hwm ? 1 : 0;
+    o.reported = o.likely && o.growth;
+    o.rate_num = r.A;
+    o.rate_den = t.n_events;
+    out[l] = o;
+}
+
 // ---------------------------------------------------------------- launchers
+cudaError_t launch_report(const LineRow *lines, const DevTrace *traces, uint32_t trace, uint32_t n_lines,
+                          uint32_t rule, int64_t F0, void *out, cudaStream_t s) {
+    k_report<<<(n_lines + 255) / 256, 256, 0, s>>>(lines, traces, trace, n_lines, rule, F0,
+                                                    static_cast<ReportRow *>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan(const LaunchPost &a, cudaStream_t s) {
     if (!a.nbt) return cudaSuccess;
     k_scan<<<a.nbt, NT, 0, s>>>(a);

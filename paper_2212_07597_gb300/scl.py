@@ -31,7 +31,8 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_replay_batch_host", "scl_sync", "scl_samples", "scl_line_stats", "scl_leak_scores",
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
-           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve", "scl_rate_samples")
+           "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve", "scl_rate_samples",
+           "scl_leak_report")
 
 
 class SclError(RuntimeError):
@@ -94,6 +95,9 @@ LINE_STAT_DTYPE = np.dtype([
     ("net", "<i8"), ("copy_samples", "<u8", (2,)), ("copy_bytes", "<u8", (2,))])
 LEAK_DTYPE = np.dtype([("line", "<u4"), ("reserved", "<u4"), ("mallocs", "<u8"), ("frees", "<u8"),
                        ("num", "<i8"), ("den", "<i8")])
+LEAK_REPORT_DTYPE = np.dtype([("line", "<u4"), ("reported", "u1"), ("likely", "u1"), ("growth", "u1"),
+                              ("reserved", "u1"), ("mallocs", "<u8"), ("frees", "<u8"), ("num", "<i8"),
+                              ("den", "<i8"), ("rate_num", "<i8"), ("rate_den", "<u8")])
 TRACE_INFO_DTYPE = np.dtype([
     ("n_events", "<u8"), ("n_copies", "<u8"), ("n_samples", "<u8"), ("c", "<i8"), ("A", "<i8"), ("F", "<i8"),
     ("A_py", "<i8"), ("F_py", "<i8"), ("footprint", "<i8"), ("hwm", "<i8"), ("tracked_addr", "<u8"),
@@ -144,6 +148,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scl_graph_enable": ([P, I], I),
             "scl_serve": ([P, P, U32, P, P, P], I),
             "scl_rate_samples": ([P, P, P, P, U64, P, U64, U64, P, P, P], I),
+            "scl_leak_report": ([P, U32, P, U32, P], I),
             "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -284,6 +289,13 @@ def scl_leak_scores(ctx: Context, trace: int) -> np.ndarray:
     out = np.zeros(ctx.cfg.n_lines, LEAK_DTYPE)
     n = ctypes.c_uint32()
     _check(ctx, load().scl_leak_scores(ctx.handle, trace, out.ctypes.data, len(out), ctypes.byref(n)))
+    return out
+
+
+def scl_leak_report(ctx: Context, trace: int) -> np.ndarray:
+    out = np.zeros(ctx.cfg.n_lines, LEAK_REPORT_DTYPE)
+    n = ctypes.c_uint32()
+    _check(ctx, load().scl_leak_report(ctx.handle, trace, out.ctypes.data, len(out), ctypes.byref(n)))
     return out
 
 

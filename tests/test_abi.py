@@ -51,7 +51,8 @@ def test_struct_layouts_match_c_compiler(tmp_path):
              "scl_request_result": scl.REQUEST_RESULT_DTYPE.itemsize,
              "scl_sample": scl.SAMPLE_DTYPE.itemsize, "scl_line_stat": scl.LINE_STAT_DTYPE.itemsize,
              "scl_leak_score": scl.LEAK_DTYPE.itemsize, "scl_trace_info": scl.TRACE_INFO_DTYPE.itemsize,
-             "scl_batch_info": scl.BATCH_INFO_DTYPE.itemsize}
+             "scl_batch_info": scl.BATCH_INFO_DTYPE.itemsize,
+             "scl_leak_report_row": scl.LEAK_REPORT_DTYPE.itemsize}
     inc = os.path.join(ROOT, "include")
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include "scl.h"\nint main(void){\n' +

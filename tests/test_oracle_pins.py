@@ -329,6 +329,40 @@ def test_segmentation_invariance():
     assert o.state() == whole.state()
 
 
+# ------------------------------------------------------------------ leak report (Section 3.4 filter)
+
+def test_leak_report_thresholds():
+    # m malloc-only 4 KiB objects... built directly: one line's crossings, no frees.  The
+    # printed likelihood (m + 1) / (m + 2) first exceeds 95% at m = 19.
+    T = 4096
+    for m, want in ((18, False), (19, True)):
+        d = np.full(m, 4096, np.int64)              # every event a new mark on line 0
+        o = oracle.Oracle(T, n_lines=2)
+        o.replay_events(d, np.arange(1, m + 1, dtype=np.uint64) * 4096, np.zeros(m, np.uint32),
+                        np.ones(m, np.uint8))
+        r = o.leak_report()
+        assert r[0]["mallocs"] == m and r[0]["frees"] == 0 and r[0]["likely"] == want
+        assert r[0]["growth"] and r[0]["reported"] == want         # footprint = mark: 100% growth
+        assert r[0]["rate_num"] == m * 4096 and r[0]["rate_den"] == m
+        assert not r[1]["likely"]                                   # no objects: 1/2
+
+
+def test_leak_report_growth_rule():
+    # growth: 100 (footprint - F0) >= mark.  Climb to a mark of 100 * 4096 bytes, then free
+    # back down to exactly 1% of it (reported) or one block less (not)
+    T = 4096
+    for keep, want in ((1, True), (0, False)):
+        up = np.full(100, 4096, np.int64)
+        down = np.full(100 - keep, -4096, np.int64)
+        d = np.concatenate([up, down])
+        addr = np.concatenate([np.arange(1, 101, dtype=np.uint64), np.arange(100, keep, -1, dtype=np.uint64)]) * 4096
+        o = oracle.Oracle(T, n_lines=1)
+        o.replay_events(d, addr, np.zeros(len(d), np.uint32), np.zeros(len(d), np.uint8))
+        st = o.state()
+        assert st["hwm"] == 100 * 4096 and st["footprint"] == keep * 4096
+        assert o.leak_report()[0]["growth"] == want
+
+
 # ------------------------------------------------------------------ rate-based sampling (Section 3.2)
 
 def _rate_brute(delta, line, py, gaps, consumed, n_lines):
