@@ -203,6 +203,13 @@ int scl_sync(scl_ctx *ctx);
  * returns SCL_EOVERFLOW.  scl_line_stats / scl_leak_scores return n_lines rows. */
 int scl_samples(scl_ctx *ctx, uint32_t trace, scl_sample *out, uint64_t cap, uint64_t *n_out);
 int scl_line_stats(scl_ctx *ctx, uint32_t trace, scl_line_stat *out, uint32_t cap, uint32_t *n_out);
+/* Footprint timeline of one line (Section 3.3's memory-trend feed): the event index and
+ * footprint of every retained sample attributed to `line`, in trace order, into host arrays
+ * idx_out / fp_out of cap entries; *n_out = the number of such samples (SCL_ERANGE when cap
+ * is smaller; SCL_EOVERFLOW when the log did not retain every sample).  The paper's
+ * downsampling of the plotted trend is not applied. */
+int scl_line_timeline(scl_ctx *ctx, uint32_t trace, uint32_t line, uint64_t *idx_out, int64_t *fp_out, uint64_t cap,
+                      uint64_t *n_out);
 int scl_leak_scores(scl_ctx *ctx, uint32_t trace, scl_leak_score *out, uint32_t cap, uint32_t *n_out);
 int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_info *out);
 int scl_leak_report(scl_ctx *ctx, uint32_t trace, scl_leak_report_row *out, uint32_t cap, uint32_t *n_out);

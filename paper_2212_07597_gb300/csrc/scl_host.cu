@@ -51,6 +51,7 @@ struct scl_ctx {
     DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
     DevBuf rate;   // scratch of scl_rate_samples
     DevBuf report; // rows of scl_leak_report
+    DevBuf tline;  // scratch and output of scl_line_timeline
     void *h_plan = nullptr;
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
@@ -399,7 +400,7 @@ void scl_replay_free(scl_ctx *c) {
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->lists, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
-                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report})
+                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report, &c->tline})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
@@ -798,6 +799,41 @@ int scl_samples(scl_ctx *c, uint32_t trace, scl_sample *out, uint64_t cap, uint6
     if (t.n_samples > have)
         return fail(c, SCL_EOVERFLOW, "%llu samples taken, only the first %llu retained (sample_log_capacity)",
                     (unsigned long long)t.n_samples, (unsigned long long)have);
+    return SCL_OK;
+}
+
+int scl_line_timeline(scl_ctx *c, uint32_t trace, uint32_t line, uint64_t *idx_out, int64_t *fp_out, uint64_t cap,
+                      uint64_t *n_out) {
+    if (!c || !n_out || (cap && (!idx_out || !fp_out))) return SCL_EINVAL;
+    if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
+    if (line >= c->cfg.n_lines) return fail(c, SCL_EINVAL, "line %u out of range", line);
+    int r = sync_and_check(c);
+    if (r) return r;
+    DevTrace t;
+    CK(cudaMemcpy(&t, c->traces + trace, sizeof t, cudaMemcpyDeviceToHost), "read trace state");
+    const uint64_t have = std::min<uint64_t>(t.n_samples, c->cfg.sample_log_capacity);
+    const uint64_t nb = (have + 4095) / 4096;
+    const uint64_t kcap = std::max<uint64_t>(cap, 1);
+    if ((r = ensure(c, c->tline, sizeof(uint64_t) * (nb + 1 + 2 * kcap), c->last_stream, "timeline"))) return r;
+    uint64_t *scratch = static_cast<uint64_t *>(c->tline.p);
+    uint64_t *d_idx = scratch + nb + 1;
+    int64_t *d_fp = reinterpret_cast<int64_t *>(d_idx + kcap);
+    CK(launch_timeline(c->log + (uint64_t)trace * c->cfg.sample_log_capacity, have, line, scratch, cap, d_idx, d_fp,
+                       c->last_stream),
+       "launch timeline");
+    uint64_t total = 0;
+    CK(cudaMemcpyAsync(&total, scratch + nb, sizeof total, cudaMemcpyDeviceToHost, c->last_stream), "read count");
+    CK(cudaStreamSynchronize(c->last_stream), "sync");
+    *n_out = total;
+    if (total > cap) return fail(c, SCL_ERANGE, "output holds %llu points, %llu needed", (unsigned long long)cap,
+                                 (unsigned long long)total);
+    if (total) {
+        CK(cudaMemcpy(idx_out, d_idx, sizeof(uint64_t) * total, cudaMemcpyDeviceToHost), "read timeline");
+        CK(cudaMemcpy(fp_out, d_fp, sizeof(int64_t) * total, cudaMemcpyDeviceToHost), "read timeline");
+    }
+    if (t.n_samples > have)
+        return fail(c, SCL_EOVERFLOW, "only the first %llu samples are retained (sample_log_capacity)",
+                    (unsigned long long)have);
     return SCL_OK;
 }
 

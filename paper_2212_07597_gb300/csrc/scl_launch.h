@@ -103,6 +103,8 @@ cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint
                          int64_t F0, uint64_t phase, cudaStream_t s);
 cudaError_t launch_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines, uint32_t rule, void *out,
                           cudaStream_t s);
+cudaError_t launch_timeline(const Sample *log, uint64_t n, uint32_t line, void *scratch, uint64_t cap,
+                            uint64_t *idx_out, int64_t *fp_out, cudaStream_t s);
 cudaError_t launch_report(const LineRow *lines, const DevTrace *traces, uint32_t trace, uint32_t n_lines,
                           uint32_t rule, int64_t F0, void *out, cudaStream_t s);
 

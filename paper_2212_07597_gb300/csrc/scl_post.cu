@@ -614,6 +614,67 @@ __global__ void k_report(const LineRow *lines, const DevTrace *traces, uint32_t 
     out[l] = o;
 }
 
+// ---------------------------------------------------------------- line timeline
+// Section 3.3's memory-trend feed for one line: (event index, footprint) of every retained
+// sample whose line is `line`, in trace order.  A stream compaction of the sample log:
+// per-block counts, one scan, then each block writes its matches at its offset.
+constexpr int TLB = 4096;   // log entries per block
+
+__global__ void __launch_bounds__(NT) k_tl_count(const Sample *log, uint64_t n, uint32_t line, uint64_t *cnt) {
+    __shared__ int64_t sh[NT / 32 + 1];
+    const uint64_t b0 = (uint64_t)blockIdx.x * TLB;
+    int64_t c = 0;
+    for (uint64_t i = b0 + threadIdx.x; i < n && i < b0 + TLB; i += NT) c += log[i].line == line;
+    int64_t tot;
+    (void)block_excl_sum(c, sh, &tot);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (uint64_t)tot;
+}
+
+__global__ void __launch_bounds__(NT) k_tl_scan(uint64_t *cnt, uint64_t nb, uint64_t *total) {
+    __shared__ int64_t sh[NT / 32 + 1];
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < nb; base += NT) {
+        const uint64_t i = base + threadIdx.x;
+        const int64_t x = i < nb ? (int64_t)cnt[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_excl_sum(x, sh, &tot);
+        if (i < nb) cnt[i] = carry + (uint64_t)ex;
+        carry += (uint64_t)tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// each thread takes TLB/NT consecutive entries, so matches keep their order
+__global__ void __launch_bounds__(NT) k_tl_write(const Sample *log, uint64_t n, uint32_t line, const uint64_t *off,
+                                                uint64_t cap, uint64_t *idx_out, int64_t *fp_out) {
+    __shared__ int64_t sh[NT / 32 + 1];
+    constexpr int PT = TLB / NT;
+    const uint64_t i0 = (uint64_t)blockIdx.x * TLB + (uint64_t)threadIdx.x * PT;
+    int64_t c = 0;
+    for (int q = 0; q < PT; ++q) c += i0 + q < n && log[i0 + q].line == line;
+    int64_t tot;
+    uint64_t o = off[blockIdx.x] + (uint64_t)block_excl_sum(c, sh, &tot);
+    for (int q = 0; q < PT; ++q) {
+        if (i0 + q < n && log[i0 + q].line == line) {
+            if (o < cap) { idx_out[o] = log[i0 + q].idx; fp_out[o] = log[i0 + q].footprint; }
+            ++o;
+        }
+    }
+}
+
+cudaError_t launch_timeline(const Sample *log, uint64_t n, uint32_t line, void *scratch, uint64_t cap,
+                            uint64_t *idx_out, int64_t *fp_out, cudaStream_t s) {
+    const uint64_t nb = (n + TLB - 1) / TLB;
+    uint64_t *cnt = static_cast<uint64_t *>(scratch);
+    uint64_t *total = cnt + nb;
+    cudaError_t e = cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+    if (e != cudaSuccess || !nb) return e;
+    k_tl_count<<<(unsigned)nb, NT, 0, s>>>(log, n, line, cnt);
+    k_tl_scan<<<1, NT, 0, s>>>(cnt, nb, total);
+    k_tl_write<<<(unsigned)nb, NT, 0, s>>>(log, n, line, cnt, cap, idx_out, fp_out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_report(const LineRow *lines, const DevTrace *traces, uint32_t trace, uint32_t n_lines,
                           uint32_t rule, int64_t F0, void *out, cudaStream_t s) {

@@ -32,7 +32,7 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
            "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve", "scl_rate_samples",
-           "scl_leak_report")
+           "scl_leak_report", "scl_line_timeline")
 
 
 class SclError(RuntimeError):
@@ -149,6 +149,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scl_serve": ([P, P, U32, P, P, P], I),
             "scl_rate_samples": ([P, P, P, P, U64, P, U64, U64, P, P, P], I),
             "scl_leak_report": ([P, U32, P, U32, P], I),
+            "scl_line_timeline": ([P, U32, U32, P, P, U64, P], I),
             "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -290,6 +291,20 @@ def scl_leak_scores(ctx: Context, trace: int) -> np.ndarray:
     n = ctypes.c_uint32()
     _check(ctx, load().scl_leak_scores(ctx.handle, trace, out.ctypes.data, len(out), ctypes.byref(n)))
     return out
+
+
+def scl_line_timeline(ctx: Context, trace: int, line: int) -> tuple[np.ndarray, np.ndarray]:
+    """(event indices, footprints) of the retained samples of one line, in trace order."""
+    lib = load()
+    n = ctypes.c_uint64()
+    rc = lib.scl_line_timeline(ctx.handle, trace, line, None, None, 0, ctypes.byref(n))
+    if rc not in (SCL_OK, SCL_ERANGE):
+        _check(ctx, rc)
+    idx = np.zeros(max(1, n.value), np.uint64)
+    fp = np.zeros(max(1, n.value), np.int64)
+    _check(ctx, lib.scl_line_timeline(ctx.handle, trace, line, idx.ctypes.data, fp.ctypes.data, n.value,
+                                      ctypes.byref(n)))
+    return idx[:n.value], fp[:n.value]
 
 
 def scl_leak_report(ctx: Context, trace: int) -> np.ndarray:

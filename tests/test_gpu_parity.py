@@ -325,3 +325,15 @@ def test_leak_report_matches_oracle():
         assert [int(x) for x in g[k]] == [int(r[k]) for r in w], k
     assert all(int(g["growth"][l]) == 1 for l in range(256))          # the trace grows
     assert int(g["reported"].sum()) > 0
+
+
+def test_line_timeline_matches_oracle_samples():
+    tr = tg.plain_trace(600_000, seed=41, n_lines=64, leak_lines=(0, 2))
+    ctx = gpu_ctx(1_048_573, n_lines=64, log_cap=1 << 18)
+    keep = replay(ctx, [(0, tr)])
+    w = oracle_of(tr, 1_048_573, n_lines=64).samples()
+    for l in (0, 1, 2, 63):
+        idx, fp = scl.scl_line_timeline(ctx, 0, l)
+        sel = w[w["line"] == l]
+        assert np.array_equal(idx, sel["idx"]) and np.array_equal(fp, sel["footprint"]), l
+        assert len(idx) == len(sel)
