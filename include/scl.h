@@ -330,6 +330,17 @@ int scl_rate_samples(scl_ctx *ctx, const int64_t *delta, const uint32_t *line, c
                      const uint64_t *gap, uint64_t n_gaps, uint64_t consumed, uint64_t *counts_out,
                      uint64_t *state_out, void *cuda_stream);
 
+/* Python vs native time (Section 2.2): n CPU-timer interrupts, vtime[k] the virtual time
+ * (ns, non-decreasing) at interrupt k and line[k] the interrupted line (device arrays).  The
+ * elapsed time T since the previous interrupt (t_prev before the first) goes to the line's
+ * Python counter up to the quantum q and to its native counter beyond it: python += min(T, q),
+ * native += T - min(T, q).  python_out / native_out (device, n_lines each) and flags_out
+ * (device, 1: 1 time went backwards, 2 a line id >= n_lines; such interrupts are skipped)
+ * are cleared by the call.  Pass vtime[n-1] as the next call's t_prev. */
+int scl_cpu_attribution(scl_ctx *ctx, const int64_t *vtime, const uint32_t *line, uint64_t n, int64_t quantum,
+                        int64_t t_prev, int64_t *python_out, int64_t *native_out, uint64_t *flags_out,
+                        void *cuda_stream);
+
 /* Failure-detection self test (no counterpart in the paper): launches one warp that
  * waits, with the same bounded wait the walker uses, on a barrier nothing arrives at.
  * The wait gives up after `limit` polls and the call returns SCL_ETIMEOUT; the

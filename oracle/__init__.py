@@ -216,6 +216,27 @@ def rate_samples(delta, line, is_python, gaps, consumed=0, n_lines=256, lib_path
     return counts.reshape(n_lines, 2), state
 
 
+def cpu_attribution(vtime, line, quantum, t_prev=0, n_lines=256):
+    """Section 2.2: each CPU-timer interrupt adds the quantum q of the elapsed virtual time
+    T to the interrupted line's Python time and the delay T - q to its native time
+    (reading: python += min(T, q), native += T - min(T, q)).  Returns (python, native,
+    flags) as in the library (1: time went backwards, 2: line id >= n_lines)."""
+    vtime = np.asarray(vtime, dtype=np.int64)
+    line = np.asarray(line, dtype=np.uint32)
+    prev = np.concatenate([[t_prev], vtime[:-1]]).astype(np.int64) if len(vtime) else np.zeros(0, np.int64)
+    T = vtime - prev
+    bad_t = T < 0
+    bad_l = line >= n_lines
+    ok = ~bad_t & ~bad_l
+    p = np.minimum(T, quantum)
+    py = np.zeros(n_lines, np.int64)
+    nat = np.zeros(n_lines, np.int64)
+    np.add.at(py, line[ok], p[ok])
+    np.add.at(nat, line[ok], (T - p)[ok])
+    flags = (1 if bad_t.any() else 0) | (2 if bad_l.any() else 0)
+    return py, nat, flags
+
+
 def replay(delta, addr, line, is_python, threshold, n_lines=256, copies=None, **kw) -> Oracle:
     """One-shot helper: replay a whole trace (and optionally its memcpy stream)."""
     o = Oracle(threshold, n_lines=n_lines, **kw)

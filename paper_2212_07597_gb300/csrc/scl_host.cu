@@ -1039,6 +1039,21 @@ int scl_rate_samples(scl_ctx *c, const int64_t *delta, const uint32_t *line, con
     return SCL_OK;
 }
 
+int scl_cpu_attribution(scl_ctx *c, const int64_t *vtime, const uint32_t *line, uint64_t n, int64_t quantum,
+                        int64_t t_prev, int64_t *python_out, int64_t *native_out, uint64_t *flags_out,
+                        void *stream) {
+    if (!c) return SCL_EINVAL;
+    if ((n && (!vtime || !line)) || !python_out || !native_out || !flags_out || quantum < 0)
+        return fail(c, SCL_EINVAL, "cpu attribution: NULL array or negative quantum");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_cpu_attr(vtime, line, n, quantum, t_prev, c->cfg.n_lines, python_out, native_out, flags_out,
+                       c->num_sms, s),
+       "launch cpu attribution");
+    c->last_stream = s;
+    return SCL_OK;
+}
+
 int scl_selftest_wait(scl_ctx *c, uint64_t limit, void *stream) {
     if (!c) return SCL_EINVAL;
     CK(cudaSetDevice(c->device), "cudaSetDevice");

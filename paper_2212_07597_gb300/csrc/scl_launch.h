@@ -116,6 +116,8 @@ size_t rate_scratch_bytes(uint64_t n, uint64_t ng);
 cudaError_t launch_rate(const int64_t *delta, const uint32_t *line, const uint8_t *py, uint64_t n,
                         const uint64_t *gap, uint64_t ng, uint64_t consumed, uint32_t n_lines, uint64_t *counts,
                         uint64_t *state, void *scratch, cudaStream_t s);
+cudaError_t launch_cpu_attr(const int64_t *vt, const uint32_t *line, uint64_t n, int64_t q, int64_t t_prev,
+                            uint32_t n_lines, int64_t *py, int64_t *nat, uint64_t *flags, int sms, cudaStream_t s);
 }  // namespace scl
 
 // context facts the serving loop needs (scl_serve.cu); defined in scl_host.cu

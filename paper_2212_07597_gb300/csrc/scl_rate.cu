@@ -8,6 +8,9 @@
 // sample per B_k in (S_{i-1}, S_i].  Tiles of 4,096 events get their byte range from a scan
 // of tile sums; each tile finds its B_k by binary search and places each one at its event
 // by a binary search in the tile's prefix, staged in shared memory.
+//
+// Also here: the Python / native split of CPU-timer interrupts (Section 2.2), the other
+// per-line attribution the profiler makes from an event stream.
 #include "scl_launch.h"
 
 namespace scl {
@@ -190,6 +193,38 @@ __global__ void k_rate_state(const uint64_t *pos, uint64_t ng, uint64_t consumed
 }
 
 }  // namespace
+
+// Section 2.2 (Python vs native time): at each CPU-timer interrupt the elapsed virtual time
+// T since the previous one is split between the interrupted line's Python counter (the
+// quantum q) and its native counter (the delay T - q).  Reading: T < q (a timer that fired
+// early) gives Python T and native 0, so every interval is attributed exactly once.
+__global__ void k_cpu_attr(const int64_t *vt, const uint32_t *line, uint64_t n, int64_t q, int64_t t_prev,
+                           uint32_t n_lines, int64_t *py, int64_t *nat, uint64_t *flags) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t T = vt[k] - (k ? vt[k - 1] : t_prev);
+        const uint32_t l = line[k];
+        if (T < 0 || l >= n_lines) {
+            atomicOr(reinterpret_cast<unsigned long long *>(flags), T < 0 ? 1ull : 2ull);
+            continue;
+        }
+        const int64_t p = T < q ? T : q;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&py[l]), (unsigned long long)p);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&nat[l]), (unsigned long long)(T - p));
+    }
+}
+
+cudaError_t launch_cpu_attr(const int64_t *vt, const uint32_t *line, uint64_t n, int64_t q, int64_t t_prev,
+                            uint32_t n_lines, int64_t *py, int64_t *nat, uint64_t *flags, int sms, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(py, 0, sizeof(int64_t) * n_lines, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(nat, 0, sizeof(int64_t) * n_lines, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(flags, 0, sizeof(uint64_t), s)) != cudaSuccess) return e;
+    if (!n) return cudaSuccess;
+    const uint64_t want = (n + RT - 1) / RT;
+    const unsigned grid = (unsigned)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
+    k_cpu_attr<<<grid, RT, 0, s>>>(vt, line, n, q, t_prev, n_lines, py, nat, flags);
+    return cudaGetLastError();
+}
 
 size_t rate_scratch_bytes(uint64_t n, uint64_t ng) {
     const uint64_t nt = (n + RTILE - 1) / RTILE, nb = (ng + GTILE - 1) / GTILE;

@@ -32,7 +32,7 @@ EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
            "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve", "scl_rate_samples",
-           "scl_leak_report", "scl_line_timeline")
+           "scl_leak_report", "scl_line_timeline", "scl_cpu_attribution")
 
 
 class SclError(RuntimeError):
@@ -150,6 +150,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scl_rate_samples": ([P, P, P, P, U64, P, U64, U64, P, P, P], I),
             "scl_leak_report": ([P, U32, P, U32, P], I),
             "scl_line_timeline": ([P, U32, U32, P, P, U64, P], I),
+            "scl_cpu_attribution": ([P, P, P, U64, ctypes.c_int64, ctypes.c_int64, P, P, P, P], I),
             "scl_copy_volume_noalloc": ([P, P, P, U64, U64, U64, U32, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
@@ -396,6 +397,20 @@ def scl_rate_samples(ctx: Context, delta, line, is_python, gap, consumed: int = 
                                         len(gap), int(consumed), _ptr(counts), _ptr(state), _stream(stream)))
     torch.cuda.synchronize(dev)
     return counts.cpu().numpy().view(np.uint64).reshape(-1, 2), state.cpu().numpy().view(np.uint64)
+
+
+def scl_cpu_attribution(ctx: Context, vtime, line, quantum: int, t_prev: int = 0, stream=None):
+    """Python / native time per line from CPU-timer interrupts (torch CUDA tensors);
+    returns (python [n_lines], native [n_lines], flags) as numpy after synchronising."""
+    import torch
+    dev = vtime.device
+    py = torch.empty(ctx.cfg.n_lines, dtype=torch.int64, device=dev)
+    nat = torch.empty(ctx.cfg.n_lines, dtype=torch.int64, device=dev)
+    fl = torch.empty(1, dtype=torch.int64, device=dev)
+    _check(ctx, load().scl_cpu_attribution(ctx.handle, _ptr(vtime), _ptr(line), len(vtime), int(quantum), int(t_prev),
+                                           _ptr(py), _ptr(nat), _ptr(fl), _stream(stream)))
+    torch.cuda.synchronize(dev)
+    return py.cpu().numpy(), nat.cpu().numpy(), int(fl.cpu().item())
 
 
 def scl_profile_enable(ctx: Context, on: bool = True) -> None:

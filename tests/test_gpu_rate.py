@@ -85,3 +85,16 @@ def test_long_trace_rate_vs_threshold_counts():
     o = oracle.Oracle(T0, n_lines=256)
     o.replay_events(tr.delta, tr.addr, tr.line, tr.is_python)
     assert int(st[0]) > 3 * len(o.samples())
+
+
+@pytest.mark.parametrize("n", [1, 777, 1_000_003])
+def test_cpu_attribution_matches_oracle(n):
+    q = 10_000_000
+    rng = np.random.default_rng(n)
+    vt = (np.cumsum(rng.integers(q // 2, 4 * q, n)) + 123).astype(np.int64)
+    ln = rng.integers(0, 256, n).astype(np.uint32)
+    ctx = gpu_ctx(T0)
+    py, nat, fl = scl.scl_cpu_attribution(ctx, torch.from_numpy(vt).cuda(), torch.from_numpy(ln.view(np.int32)).cuda(),
+                                          q, 123)
+    wpy, wnat, wfl = oracle.cpu_attribution(vt, ln, q, 123, n_lines=256)
+    assert np.array_equal(py, wpy) and np.array_equal(nat, wnat) and fl == wfl == 0

@@ -363,6 +363,38 @@ def test_leak_report_growth_rule():
         assert o.leak_report()[0]["growth"] == want
 
 
+# ------------------------------------------------------------------ Python / native time (Section 2.2)
+
+def test_cpu_attribution_rules():
+    q = 10_000_000   # 10 ms quantum
+    # interrupts exactly on time: all Python
+    vt = np.arange(1, 101, dtype=np.int64) * q
+    line = np.arange(100, dtype=np.uint32) % 4
+    py, nat, fl = oracle.cpu_attribution(vt, line, q, 0, n_lines=4)
+    assert py.tolist() == [25 * q] * 4 and nat.tolist() == [0] * 4 and fl == 0
+    # a delayed interrupt: the delay is native time of the interrupted line
+    vt2 = np.array([q, 2 * q, 5 * q], np.int64)
+    py, nat, fl = oracle.cpu_attribution(vt2, np.array([0, 1, 1], np.uint32), q, 0, n_lines=2)
+    assert py.tolist() == [q, 2 * q] and nat.tolist() == [0, 2 * q]
+    # every interval attributed exactly once (with an early interrupt, T < q)
+    rng = np.random.default_rng(1)
+    vt3 = np.cumsum(rng.integers(0, 3 * q, 5000)).astype(np.int64) + 7
+    ln = rng.integers(0, 16, 5000).astype(np.uint32)
+    py, nat, fl = oracle.cpu_attribution(vt3, ln, q, 7, n_lines=16)
+    assert int(py.sum() + nat.sum()) == int(vt3[-1] - 7) and fl == 0 and (nat >= 0).all()
+    # brute force per interrupt
+    bp, bn, prev = [0] * 16, [0] * 16, 7
+    for t, l in zip(vt3.tolist(), ln.tolist()):
+        T = t - prev
+        bp[l] += min(T, q)
+        bn[l] += T - min(T, q)
+        prev = t
+    assert py.tolist() == bp and nat.tolist() == bn
+    # time going backwards is flagged and skipped
+    _, _, fl = oracle.cpu_attribution(np.array([5, 3], np.int64), np.array([0, 0], np.uint32), q, 0, n_lines=1)
+    assert fl & 1
+
+
 # ------------------------------------------------------------------ rate-based sampling (Section 3.2)
 
 def _rate_brute(delta, line, py, gaps, consumed, n_lines):
