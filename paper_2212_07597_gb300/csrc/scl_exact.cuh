@@ -12,7 +12,7 @@
 // the unit's resets are known in advance (a reset list from k_sketch) no crossing
 // search runs; otherwise each step's prefix sums locate the crossings.
 //
-// Used by k_final for every unit whose entry k_chain resolved, and by k_sketch for the
+// Used by k_final for every unit whose entry k_chain resolved, and by k_first for the
 // first unit of each trace in a batch, whose entry is the trace's resident state; that
 // caller also wants the facts k_sketch records for a candidate run (FIRST = true).
 #pragma once
@@ -32,7 +32,7 @@ struct ExactIn {                 // the state entering the unit
     int64_t exit_c;              // counter after the unit (with a list)
 };
 
-struct ExactRun {                // FIRST only: the run's facts, as k_sketch records them
+struct ExactRun {                // FIRST only: the run's facts, as k_sketch records them for a candidate
     Cand *C0;                    // lane 0 writes the first RM reset positions and growth
                                  // prefixes here (the unit's candidate 0)
     int64_t gmax, tmax;          // largest prefix at a growth reset (all / index >= RM)

@@ -46,6 +46,7 @@ struct scl_ctx {
     unsigned *queue = nullptr;
     unsigned long long *stats = nullptr;   // device: chain counters of the last batch
     uint64_t last_units = 0;
+    uint64_t last_first_events = 0, last_sketch_events = 0;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
     DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
@@ -59,7 +60,7 @@ struct scl_ctx {
     // the copy-volume pass (Section 3.5) shares nothing with the event path: it runs on a
     // side stream between a fork after the sketch and a join before the state fold
     cudaStream_t side = nullptr, hi = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr, ev_first = nullptr;
     // host-to-device staging of scl_replay_batch_host: pieces spread over several copy
     // streams (several copy engines at once), joined back before the replay
     static constexpr int NCS = 4;
@@ -285,11 +286,20 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         int bps = 0;
         if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
         k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
+        // the first unit of each trace (whose entry is known) is replayed exactly on the side
+        // stream, beside the sketch of the other units
+        CK(cudaStreamWaitEvent(c->side, c->ev_in, 0), "fork the first units");
+        {
+            Prof p(c, c->side, "first");
+            CK(launch_first(k, c->side), "launch first");
+        }
+        CK(cudaEventRecord(c->ev_first, c->side), "first-unit event");
         {
             Prof p(c, s, "sketch");
             CK(launch_sketch(k, s), "launch sketch");
         }
         CK(cudaEventRecord(c->ev_fork, s), "fork event");
+        CK(cudaStreamWaitEvent(s, c->ev_first, 0), "join the first units");
         {
             Prof p(c, s, "match");
             CK(launch_match(k, s), "launch match");
@@ -413,6 +423,7 @@ void scl_replay_free(scl_ctx *c) {
     if (c->plan_done) cudaEventDestroy(c->plan_done);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_first) cudaEventDestroy(c->ev_first);
     if (c->side) cudaStreamDestroy(c->side);
     if (c->hi) cudaStreamDestroy(c->hi);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -469,6 +480,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming);
     for (int i = 0; i < scl_ctx::NCS && e == cudaSuccess; ++i)
         e = cudaStreamCreateWithFlags(&c->cstream[i], cudaStreamNonBlocking);
     for (int i = 0; i <= scl_ctx::NCS && e == cudaSuccess; ++i)
@@ -671,6 +683,20 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
 
     char *dp = static_cast<char *>(c->plan.p);
     c->last_units = units.size();
+    {
+        // events through k_first (first units) and k_sketch (other units, each with the
+        // warm-up over the tail of the unit before it, from a tile boundary)
+        const uint64_t W = c->tune.ext_events ? c->tune.ext_events : 32768;
+        uint64_t fe = 0, se = 0;
+        for (size_t u = 0; u < units.size(); ++u) {
+            if (units[u].first) { fe += units[u].len; continue; }
+            const uint64_t pl = units[u - 1].len;
+            const uint64_t from = pl > W ? (pl - W) / SKETCH_TILE * SKETCH_TILE : 0;
+            se += units[u].len + (pl - from);
+        }
+        c->last_first_events = fe;
+        c->last_sketch_events = se;
+    }
     c->last_stream = s;
     EnqArgs q{dp, hp, blob, o_units, o_bts, o_grp, o_ct, nbt, nunits, (int)cgroups.size(), (int)ctiles.size()};
     if (c->graph_on && !c->prof && s != nullptr) {
@@ -1019,6 +1045,8 @@ int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
     out->transparent = v[3];
     out->unit_events = c->tune.unit_events;
     out->walked_events = v[4];
+    out->first_events = c->last_first_events;
+    out->sketch_events = c->last_sketch_events;
     return SCL_OK;
 }
 

@@ -272,14 +272,23 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Staged 8-byte columns hold each lane's 8 events (64 bytes, one "row") with their four
-// 16-byte chunks permuted: chunk c of row r sits at chunk c ^ ((r >> 1) & 3).  A quarter
-// warp loading one chunk per lane then touches eight distinct bank groups.
-__device__ __forceinline__ int swz_chunk(int r, int c) { return c ^ ((r >> 1) & 3); }
-__device__ __forceinline__ int swz8(int i) {   // element i of a tile -> its staged position
-    const int r = i >> 3, k = i & 7;
-    return (r << 3) | (swz_chunk(r, k >> 1) << 1) | (k & 1);
+// Staged 8-byte columns hold each lane's EL events (one "row" of EL * 8 bytes) with the
+// row's 16-byte chunks permuted, so that a quarter warp loading one chunk per lane (eight
+// consecutive rows) touches eight distinct bank groups:
+//   EL = 8  (64-byte rows, 4 chunks):  chunk c of row r sits at chunk c ^ ((r >> 1) & 3)
+//   EL = 16 (128-byte rows, 8 chunks): chunk c of row r sits at chunk c ^ (r & 7)
+template <int EL>
+__device__ __forceinline__ int swz_chunk_el(int r, int c) {
+    static_assert(EL == 8 || EL == 16, "staged rows hold 8 or 16 events");
+    return EL == 8 ? c ^ ((r >> 1) & 3) : c ^ (r & 7);
 }
+template <int EL>
+__device__ __forceinline__ int swz_el(int i) {   // element i of a tile -> its staged position
+    const int r = i / EL, k = i % EL;
+    return r * EL + (swz_chunk_el<EL>(r, k >> 1) << 1) + (k & 1);
+}
+__device__ __forceinline__ int swz_chunk(int r, int c) { return swz_chunk_el<8>(r, c); }
+__device__ __forceinline__ int swz8(int i) { return swz_el<8>(i); }
 
 // Bounded wait for phase `parity` of the barrier, called by all 32 lanes of a warp.
 // Every lane polls (so each observes the phase completion); the answer is agreed by

@@ -7,6 +7,9 @@
 namespace scl {
 
 constexpr int SKETCH_MAX_WARPS = 16;   // k_sketch warps per block (its launch bound)
+constexpr int SKETCH_MIN_BLOCKS = 1;   // k_sketch blocks of SKETCH_MAX_WARPS resident per SM
+constexpr int FIRST_WARPS = 4;         // k_first warps per block
+constexpr int SKETCH_TILE = 256;       // k_sketch events per staged tile (warm-ups start on one)
 
 struct LaunchSketch {
     const Unit *units;
@@ -16,7 +19,7 @@ struct LaunchSketch {
     UnitSum *usum;
     Cand *cand;
     SRes *lists;
-    FRec *recs;          // first units: their records and outputs (k_sketch replays them exactly)
+    FRec *recs;          // first units: their records and outputs (k_first replays them exactly)
     UnitOut *uout;
     uint8_t *match;
     Walk *uwalk;
@@ -26,7 +29,7 @@ struct LaunchSketch {
     const DevTrace *traces;
     int64_t T;
     uint32_t warmup;
-    unsigned *queue;     // [0] sketch, [2] final
+    unsigned *queue;     // [0] sketch, [1] first units, [2] final
     ErrWord *err;
     unsigned long long spin;
     unsigned long long *stats;   // [walked, walked and merged, explicit entries, transparent, events walked]
@@ -83,6 +86,7 @@ struct LaunchPost {
 int sketch_occupancy(int warps_per_block, int *blocks_per_sm);
 int final_occupancy(int warps_per_block, int *blocks_per_sm);
 cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_first(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s);

@@ -13,14 +13,18 @@
 //           surely joined.  Equal counters are merged (followers copy their leader),
 //           and the distinct ones are run through the unit, recording the counter
 //           at the start and end, the resets, the last reset and the first largest
-//           prefix at a growth reset.  A trace's first unit runs the exact resident
-//           counter instead.  All lanes advance together, 128 events per step.
+//           prefix at a growth reset.  All lanes advance together, 256 events per step.
+// k_first   one warp per trace of the batch, beside k_sketch on another stream: the
+//           trace's first unit, whose entry is the trace's resident state, replayed
+//           exactly once (k_final skips it) and recorded as every candidate of the unit.
+//           (Inside k_sketch its exact replay set that kernel's register count.)
 // k_match   for each unit and each candidate k of the previous unit: the candidate of
 //           this unit whose start counter equals k's end counter, if any.
 // k_chain   one block per trace: follows the true candidate from unit to unit through
 //           the match table in shared memory; where no candidate carries the true
 //           counter the block walks the unit itself (helper warps summarise the steps
 //           ahead of the warp that runs the counter).
+#include <algorithm>
 #include <cstddef>
 
 #include "scl_exact.cuh"
@@ -63,11 +67,14 @@ __device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, i
 }
 
 // ---------------------------------------------------------------- k_sketch
-using SketchRing = Ring<false, 2, 512, 8>;   // two steps per tile: half the ring waits
-using FirstRing = Ring<true, 2, 256, 8>;       // the first unit of a trace: its exact replay
-constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing) > sizeof(FirstRing) ? sizeof(SketchRing) : sizeof(FirstRing);
+constexpr int SE = 8;                         // events per lane per sketch step (256 per step)
+using SketchRing = Ring<false, 2, 256, SE>;   // one step per tile: the other tile is in flight
+constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing);
+static_assert(SketchRing::kTL == SKETCH_TILE, "the host counts warm-up events in these tiles");
+static_assert(SKETCH_WARP_SMEM * SKETCH_MAX_WARPS * SKETCH_MIN_BLOCKS <= 227 * 1024,
+              "the resident sketch blocks' rings fit in one SM's shared memory");
 
-__global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
+__global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
                                                     Cand *cand, SRes *lists, FRec *recs, UnitOut *uout,
                                                     const DevTrace *traces, int64_t T, uint32_t warmup,
                                                     unsigned *queue, ErrWord *err, unsigned long long spin) {
@@ -84,55 +91,7 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS) k_sketch(const Unit *__
         const Unit U = units[u];
         bool ok = true;
         int64_t c;
-        if (U.first) {
-            // The trace's resident state is this unit's exact entry: replay it exactly now
-            // (k_final skips it) and record the run as every lane's candidate.
-            ring_release(sm, lane);
-            FirstRing &fr = *reinterpret_cast<FirstRing *>(&sm);
-            ring_init(fr, lane);
-            uint32_t fphase = 0;
-            const DevTrace st = traces[U.trace];
-            ExactIn in0;
-            in0.c = st.c;
-            in0.wA = lane == 0 ? st.A : 0;
-            in0.wApy = lane == 0 ? st.A_py : 0;
-            in0.wSpy = lane == 0 ? st.A_py - st.F_py : 0;
-            in0.mark = st.hwm;
-            in0.fpb = st.footprint;
-            in0.tk = st.tracked_valid ? 2u : 0u;   // as k_scan plans a trace's first unit
-            in0.taddr = st.tracked_addr;
-            in0.list = nullptr;
-            in0.nres = 0;
-            in0.exit_c = 0;
-            ExactRun R;
-            R.C0 = cand + (size_t)u * K;
-            UnitOut O;
-            uint32_t n = 0;
-            ok = exact_unit<true>(fr, fphase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R);
-            if (!ok) break;   // a wait timed out: leave (the ring may not be reusable)
-            ring_release(fr, lane);
-            ring_init(sm, lane);
-            phase = 0;
-            Cand *C = cand + (size_t)u * K + lane;
-            if (lane == 0)
-                for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
-            __syncwarp();
-            if (lane != 0) {
-                const Cand *C0 = R.C0;
-                for (int r = 0; r < RM; ++r) { C->pos[r] = C0->pos[r]; C->gp[r] = C0->gp[r]; }
-            }
-            C->c0 = st.c; C->c = O.c; C->last = R.last; C->n = n;
-            C->gmax = R.gmax; C->garg = R.garg; C->tmax = R.tmax; C->targ = R.targ;
-            C->list = NO_LIST; C->pad = 0;
-            if (lane == 0) {
-                UnitSum S;   // window totals are filled by k_totals, for the units that need them
-                S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = R.umin; S.maxQ = R.umax;
-                usum[u] = S;
-                uout[u] = O;
-                if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);
-            }
-            continue;
-        }
+        if (U.first) continue;   // replayed exactly by k_first
         {
             // warm-up over the tail of the previous unit of the trace; candidates whose
             // counters become equal run on as one (the lowest lane leads)
@@ -140,8 +99,8 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS) k_sketch(const Unit *__
             int lead = lane;
             const Unit Up = units[u - 1];
             const uint64_t from = Up.len > warmup ? ((Up.len - warmup) / SketchRing::kTL) * SketchRing::kTL : 0;
-            auto wstep = [&](const StepIn<8> &in, uint32_t) -> bool {
-                StepPrefix<8> sp;
+            auto wstep = [&](const StepIn<SE> &in, uint32_t) -> bool {
+                StepPrefix<SE> sp;
                 step_prefix(in, lane, sp, sm.xq);
                 const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
                 const bool act = lead == lane;
@@ -170,8 +129,8 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS) k_sketch(const Unit *__
         int64_t gmax = INT64_MIN, tmax = INT64_MIN;
         uint32_t garg = 0, targ = 0;
         int64_t P = 0, umax = INT64_MIN, umin = INT64_MAX;
-        auto step = [&](const StepIn<8> &in, uint32_t rel0) -> bool {
-            StepPrefix<8> sp;
+        auto step = [&](const StepIn<SE> &in, uint32_t rel0) -> bool {
+            StepPrefix<SE> sp;
             step_prefix(in, lane, sp, sm.xq);
             const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
             advance(sp, sm.xq, qmax, qmin, lane, T, active, c, [&](int k, int r, bool growth, int64_t Qr) {
@@ -234,6 +193,68 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS) k_sketch(const Unit *__
             usum[u] = S;
         }
         if (!ok) break;
+    }
+}
+
+// ---------------------------------------------------------------- k_first
+using FirstRing = Ring<true, 2, 256, 8>;
+
+__global__ void __launch_bounds__(32 * FIRST_WARPS) k_first(const Unit *__restrict__ units, const BTrace *__restrict__ bts,
+                                                           int nbt, UnitSum *usum, Cand *cand, FRec *recs, UnitOut *uout,
+                                                           const DevTrace *traces, int64_t T, unsigned *queue,
+                                                           ErrWord *err, unsigned long long spin) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FirstRing &fr = reinterpret_cast<FirstRing *>(smem_raw)[warp];
+    ring_init(fr, lane);
+    uint32_t fphase = 0;
+    while (true) {
+        int b = 0;
+        if (lane == 0) b = (int)atomicAdd(queue, 1u);
+        b = __shfl_sync(FULL, b, 0);
+        if (b >= nbt) break;
+        if (bts[b].nu == 0) continue;
+        const int u = (int)bts[b].u0;
+        const Unit U = units[u];
+        // The trace's resident state is this unit's exact entry: replay it exactly (k_final
+        // skips it) and record the run as every lane's candidate.
+        const DevTrace st = traces[U.trace];
+        ExactIn in0;
+        in0.c = st.c;
+        in0.wA = lane == 0 ? st.A : 0;
+        in0.wApy = lane == 0 ? st.A_py : 0;
+        in0.wSpy = lane == 0 ? st.A_py - st.F_py : 0;
+        in0.mark = st.hwm;
+        in0.fpb = st.footprint;
+        in0.tk = st.tracked_valid ? 2u : 0u;   // as k_scan plans a trace's first unit
+        in0.taddr = st.tracked_addr;
+        in0.list = nullptr;
+        in0.nres = 0;
+        in0.exit_c = 0;
+        ExactRun R;
+        R.C0 = cand + (size_t)u * K;
+        UnitOut O;
+        uint32_t n = 0;
+        const bool ok = exact_unit<true>(fr, fphase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R);
+        if (!ok) break;   // a wait timed out: leave (the ring may not be reusable)
+        Cand *C = cand + (size_t)u * K + lane;
+        if (lane == 0)
+            for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
+        __syncwarp();
+        if (lane != 0) {
+            const Cand *C0 = R.C0;
+            for (int r = 0; r < RM; ++r) { C->pos[r] = C0->pos[r]; C->gp[r] = C0->gp[r]; }
+        }
+        C->c0 = st.c; C->c = O.c; C->last = R.last; C->n = n;
+        C->gmax = R.gmax; C->garg = R.garg; C->tmax = R.tmax; C->targ = R.targ;
+        C->list = NO_LIST; C->pad = 0;
+        if (lane == 0) {
+            UnitSum S;   // window totals are filled by k_totals, for the units that need them
+            S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = R.umin; S.maxQ = R.umax;
+            usum[u] = S;
+            uout[u] = O;
+            if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);
+        }
     }
 }
 
@@ -676,6 +697,18 @@ cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.lists, a.recs,
                                                             a.uout, a.traces, a.T, a.warmup, a.queue, a.err, a.spin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first(const LaunchSketch &a, cudaStream_t s) {
+    if (!a.nbt) return cudaSuccess;
+    const int w = std::min(FIRST_WARPS, a.nbt);   // a lone trace takes one warp of one SM
+    const size_t smem = sizeof(FirstRing) * w;
+    cudaError_t e = cudaFuncSetAttribute(k_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min((a.nbt + w - 1) / w, 4 * a.num_sms));
+    k_first<<<blocks, 32 * w, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.recs, a.uout, a.traces, a.T,
+                                                   a.queue + 1, a.err, a.spin);
     return cudaGetLastError();
 }
 

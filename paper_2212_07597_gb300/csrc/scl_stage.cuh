@@ -4,8 +4,8 @@
 // A unit's columns are read in tiles of TILE events; NST tiles are in flight per
 // warp.  Full tiles of 16-byte aligned columns arrive as 16-byte cp.async copies issued
 // by all lanes (each lane's copies then arrive on the stage's mbarrier); the 8-byte
-// columns are written in the chunk-permuted layout of swz8, so the lanes' 16-byte loads
-// of their own 8 events are free of bank conflicts.  Partial or unaligned tiles are
+// columns are written in the chunk-permuted layout of swz_el, so the lanes' 16-byte loads
+// of their own EL events are free of bank conflicts.  Partial or unaligned tiles are
 // copied by the lanes with plain loads into the same layout.  Every wait is bounded;
 // whatever happens, no copy is left in flight when the walk returns.
 #pragma once
@@ -46,7 +46,8 @@ template <class RingT>
 __device__ __forceinline__ void ring_init(RingT &sm, int lane) {
     static_assert(sizeof(RingT) % 128 == 0, "rings laid end to end must stay aligned");
     static_assert(RingT::kTL % 16 == 0 && (RingT::kTL * 8) % 16 == 0, "bulk copies move 16-byte multiples");
-    static_assert(RingT::kE == 8, "the staged layout holds 8 events per lane");
+    static_assert(RingT::kE == 8 || RingT::kE == 16, "the staged layout holds 8 or 16 events per lane");
+    static_assert(RingT::kTL % (32 * RingT::kE) == 0, "a tile holds whole steps");
     if (lane == 0) {
         for (int s = 0; s < RingT::kNS; ++s) mbar_init(&sm.bar[s], 32);   // one arrival per lane
         fence_mbar_init();
@@ -77,16 +78,15 @@ __device__ __forceinline__ uint32_t py_of(const StepIn<EL> &in, int k) {
     return (uint32_t)(in.pw[k >> 3] >> (8 * (k & 7))) & 0xffu;
 }
 
-// The 8 consecutive 64-bit values of tile element e0 (a multiple of 8: one row of the
-// staged layout), as four 16-byte shared loads.
+// The EL consecutive 64-bit values of tile element e0 (a multiple of EL: one row of the
+// staged layout), as EL / 2 16-byte shared loads.
 template <int EL, class V>
 __device__ __forceinline__ void load_lane(const V *tile, uint32_t e0, V (&out)[EL]) {
-    static_assert(EL == 8, "one staged row per lane");
-    const int r = (int)(e0 >> 3);
-    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(tile + 8 * r);
+    const int r = (int)(e0 / EL);
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(tile + EL * r);
 #pragma unroll
     for (int q = 0; q < EL / 2; ++q) {
-        const ulonglong2 v = src[swz_chunk(r, q)];
+        const ulonglong2 v = src[swz_chunk_el<EL>(r, q)];
         out[2 * q] = (V)v.x;
         out[2 * q + 1] = (V)v.y;
     }
@@ -112,19 +112,17 @@ __device__ bool ring_walk(RingT &sm, const Unit &U, uint64_t from, uint64_t limi
         const uint64_t t0 = t * TILE;
         const uint64_t cnt = limit - t0 < (uint64_t)TILE ? limit - t0 : (uint64_t)TILE;
         if (bulk && cnt == (uint64_t)TILE) {
-            // 16-byte chunks j = lane + 32 i of the 8-byte columns land at their permuted
-            // places: row (lane >> 2) + 8 i, chunk swz_chunk(row, lane & 3), which does not
-            // depend on i -- one offset per lane, 64 elements further per i
-            const int off = 8 * (lane >> 2) + 2 * swz_chunk(lane >> 2, lane & 3);
+            // 16-byte chunk j = lane + 32 i of an 8-byte column (elements 2j, 2j + 1) lands
+            // at its permuted place swz_el(2j); eight consecutive lanes fill one 128-byte
+            // line of shared memory
             const int64_t *gd = U.delta + t0 + 2 * lane;
-            int64_t *sd = &sm.d[s][off];
 #pragma unroll
-            for (int i = 0; i < TILE / 64; ++i) cp_async16(sd + 64 * i, gd + 64 * i);
+            for (int i = 0; i < TILE / 64; ++i) cp_async16(&sm.d[s][swz_el<E>(2 * lane + 64 * i)], gd + 64 * i);
             if (ADDR) {
                 const uint64_t *ga = U.addr + t0 + 2 * lane;
-                uint64_t *sa = sm.a(s) + off;
+                uint64_t *sa = sm.a(s);
 #pragma unroll
-                for (int i = 0; i < TILE / 64; ++i) cp_async16(sa + 64 * i, ga + 64 * i);
+                for (int i = 0; i < TILE / 64; ++i) cp_async16(sa + swz_el<E>(2 * lane + 64 * i), ga + 64 * i);
             }
             if (ADDR)
                 for (int j = lane; j < TILE / 16; j += 32) cp_async16(sm.p(s) + 16 * j, U.py + t0 + 16 * j);
@@ -132,7 +130,7 @@ __device__ bool ring_walk(RingT &sm, const Unit &U, uint64_t from, uint64_t limi
             pending |= 1u << s;
         } else {
             for (uint32_t j = lane; j < (uint32_t)cnt; j += 32) {
-                const int js = swz8((int)j);
+                const int js = swz_el<E>((int)j);
                 sm.d[s][js] = U.delta[t0 + j];
                 if (ADDR) {
                     sm.p(s)[j] = U.py[t0 + j];
@@ -229,11 +227,11 @@ __device__ __forceinline__ void step_prefix(const StepIn<EL> &in, int lane, Step
     sp.tot = __shfl_sync(FULL, incl, 31);
     sp.lmax = mx + sp.ex;
     sp.lmin = mn + sp.ex;
-    if (xq) {   // EL == 8: the staged layout (lane = row); otherwise plain
+    if (xq) {   // the staged layout (lane = row)
         longlong2 *dst = reinterpret_cast<longlong2 *>(xq + lane * EL);
 #pragma unroll
         for (int q = 0; q < EL / 2; ++q)
-            dst[EL == 8 ? swz_chunk(lane, q) : q] = make_longlong2(sp.ex + sp.lp[2 * q], sp.ex + sp.lp[2 * q + 1]);
+            dst[swz_chunk_el<EL>(lane, q)] = make_longlong2(sp.ex + sp.lp[2 * q], sp.ex + sp.lp[2 * q + 1]);
         __syncwarp();
     }
 }
@@ -258,7 +256,7 @@ __device__ __forceinline__ int first_cross(const StepPrefix<EL> &sp, const int64
     while (m) {
         const int fl = __ffs(m) - 1;
         m &= m - 1;
-        const int64_t q = lane < EL ? xq[EL == 8 ? swz8(fl * EL + lane) : fl * EL + lane] : 0;
+        const int64_t q = lane < EL ? xq[swz_el<EL>(fl * EL + lane)] : 0;
         const unsigned h = __ballot_sync(FULL, lane < EL && fl * EL + lane > after && (q >= hi || q <= lo));
         if (h) {
             const int kf = __ffs(h) - 1;
