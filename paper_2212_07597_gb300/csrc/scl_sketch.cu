@@ -40,21 +40,22 @@ __device__ __forceinline__ int64_t candidate_entry(int k, int64_t T) {
 
 // Advance this lane's counter c (if `active`) over one step; at each reset of an
 // active lane call on_reset(lane_k, pos, growth, Qr) on all lanes (warp-uniform).
-template <int EL, class F>
-__device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, int64_t qmax, int64_t qmin, int lane,
-                                        int64_t T, bool active, int64_t &c, F &&on_reset) {
+// SP / I: the 64-bit step (StepPrefix, int64_t) or its 32-bit form (StepPrefix32, int32_t).
+template <class SP, class I, class F>
+__device__ __forceinline__ void advance(const SP &sp, const I *xq, I qmax, I qmin, int lane, I T, bool active, I &c,
+                                        F &&on_reset) {
     unsigned m = __ballot_sync(FULL, active && (c + qmax >= T || c + qmin <= -T));
-    int64_t cnew = c + sp.tot;
+    I cnew = c + sp.tot;
     while (m) {
         const int k = __ffs(m) - 1;
         m &= m - 1;
-        int64_t b = __shfl_sync(FULL, c, k);
+        I b = __shfl_sync(FULL, c, k);
         int after = -1;
         while (true) {
-            int64_t Qr;
+            I Qr;
             const int r = first_cross(sp, xq, lane, b, T, after, Qr);
             if (r < 0) break;
-            on_reset(k, r, b + Qr > 0, Qr);
+            on_reset(k, r, b + Qr > 0, (int64_t)Qr);
             b = -Qr;
             after = r;
             // from c = 0 after the reset, the rest of the step can only cross if its
@@ -64,6 +65,33 @@ __device__ __forceinline__ void advance(const StepPrefix<EL> &sp, int64_t *xq, i
         if (lane == k) cnew = b + sp.tot;
     }
     c = cnew;
+}
+
+// One step of every lane's counter: the 32-bit form when T and the step's deltas allow it
+// (t32: T <= 2^30), else the 64-bit one.  Returns the step total and prefix extremes.
+template <class F>
+__device__ __forceinline__ void sketch_step(const StepIn<8> &in, int64_t *xq, int lane, int64_t T, bool t32,
+                                            bool active, int64_t &c, int64_t &tot, int64_t &qmax, int64_t &qmin,
+                                            F &&on_reset) {
+    if (t32 && __all_sync(FULL, step_fits32(in))) {
+        StepPrefix32<8> sp;
+        int32_t *xq32 = reinterpret_cast<int32_t *>(xq);
+        step_prefix32(in, lane, sp, xq32);
+        const int32_t mx = __reduce_max_sync(FULL, sp.lmax), mn = __reduce_min_sync(FULL, sp.lmin);
+        int32_t c32 = (int32_t)c;
+        advance(sp, (const int32_t *)xq32, mx, mn, lane, (int32_t)T, active, c32, on_reset);
+        c = c32;
+        tot = sp.tot;
+        qmax = mx;
+        qmin = mn;
+    } else {
+        StepPrefix<8> sp;
+        step_prefix(in, lane, sp, xq);
+        qmax = warp_max(sp.lmax);
+        qmin = warp_min(sp.lmin);
+        advance(sp, (const int64_t *)xq, qmax, qmin, lane, T, active, c, on_reset);
+        tot = sp.tot;
+    }
 }
 
 // ---------------------------------------------------------------- k_sketch
@@ -82,6 +110,7 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sk
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     SketchRing &sm = *reinterpret_cast<SketchRing *>(smem_raw + (size_t)warp * SKETCH_WARP_SMEM);
     ring_init(sm, lane);
+    const bool t32 = T <= FIT32_T;
     uint32_t phase = 0;
     while (true) {
         int u = 0;
@@ -100,11 +129,9 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sk
             const Unit Up = units[u - 1];
             const uint64_t from = Up.len > warmup ? ((Up.len - warmup) / SketchRing::kTL) * SketchRing::kTL : 0;
             auto wstep = [&](const StepIn<SE> &in, uint32_t) -> bool {
-                StepPrefix<SE> sp;
-                step_prefix(in, lane, sp, sm.xq);
-                const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
                 const bool act = lead == lane;
-                advance(sp, sm.xq, qmax, qmin, lane, T, act, c, [](int, int, bool, int64_t) {});
+                int64_t tot, qmax, qmin;
+                sketch_step(in, sm.xq, lane, T, t32, act, c, tot, qmax, qmin, [](int, int, bool, int64_t) {});
                 const unsigned same = __match_any_sync(FULL, (unsigned long long)c) & __ballot_sync(FULL, act);
                 if (act) lead = __ffs(same) - 1;
                 return false;
@@ -130,10 +157,8 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sk
         uint32_t garg = 0, targ = 0;
         int64_t P = 0, umax = INT64_MIN, umin = INT64_MAX;
         auto step = [&](const StepIn<SE> &in, uint32_t rel0) -> bool {
-            StepPrefix<SE> sp;
-            step_prefix(in, lane, sp, sm.xq);
-            const int64_t qmax = warp_max(sp.lmax), qmin = warp_min(sp.lmin);
-            advance(sp, sm.xq, qmax, qmin, lane, T, active, c, [&](int k, int r, bool growth, int64_t Qr) {
+            int64_t tot, qmax, qmin;
+            sketch_step(in, sm.xq, lane, T, t32, active, c, tot, qmax, qmin, [&](int k, int r, bool growth, int64_t Qr) {
                 if (lane == k) {
                     const uint32_t pos = rel0 + (uint32_t)r;
                     const int64_t Pl = P + Qr;
@@ -159,7 +184,7 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sk
             // the unit's prefix extremes (for the transparency test of k_chain)
             umax = P + qmax > umax ? P + qmax : umax;
             umin = P + qmin < umin ? P + qmin : umin;
-            P += sp.tot;
+            P += tot;
             return false;
         };
         if (ok) ok = ring_walk<false>(sm, U, 0, U.len, phase, spin, err, lane, step);

@@ -267,4 +267,91 @@ __device__ __forceinline__ int first_cross(const StepPrefix<EL> &sp, const int64
     return -1;
 }
 
+// ---- the 32-bit form of a step, for the candidate counters of k_sketch.
+// When every delta of the step lies in [-2^22, 2^22) the step's prefixes lie in
+// (-2^30, 2^30); with T <= 2^30 a counter lies in (-2^30, 2^30) as well, so a counter plus
+// a prefix, T minus a counter and every other quantity of the crossing search fit in
+// int32.  The result is the same as the 64-bit form's: it is the same arithmetic without
+// overflow, in fewer integer instructions.
+constexpr int64_t FIT32_T = 1ll << 30;   // largest T for the 32-bit form
+constexpr int FIT32_SHIFT = 22;          // deltas in [-2^22, 2^22)
+
+template <int EL>
+__device__ __forceinline__ bool step_fits32(const StepIn<EL> &in) {
+    // d fits iff its high word is the sign extension of its low word (d is an int32)
+    // and the low word lies in [-2^22, 2^22), i.e. low + 2^22 < 2^23 as unsigned
+    uint32_t hx = 0, lv = 0;
+#pragma unroll
+    for (int k = 0; k < EL; ++k) {
+        const uint32_t lo = (uint32_t)(uint64_t)in.d[k];
+        const uint32_t hi = (uint32_t)((uint64_t)in.d[k] >> 32);
+        hx |= hi ^ (uint32_t)((int32_t)lo >> 31);
+        lv |= lo + (1u << FIT32_SHIFT);
+    }
+    return hx == 0 && (lv >> (FIT32_SHIFT + 1)) == 0;
+}
+
+template <int EL>
+struct StepPrefix32 {
+    int32_t lp[EL];
+    int32_t ex, tot, lmax, lmin;
+};
+
+// 32-bit rows of EL = 8 prefixes (32 bytes, two 16-byte chunks); chunk c of row r sits at
+// chunk c ^ ((r >> 2) & 1), so a quarter warp's 16-byte stores touch eight bank groups.
+__device__ __forceinline__ int swz32(int i) {
+    const int r = i >> 3, k = i & 7;
+    return (r << 3) | ((((k >> 2) ^ (r >> 2)) & 1) << 2) | (k & 3);
+}
+
+template <int EL>
+__device__ __forceinline__ void step_prefix32(const StepIn<EL> &in, int lane, StepPrefix32<EL> &sp, int32_t *xq) {
+    static_assert(EL == 8, "32-bit rows hold 8 prefixes");
+    sp.lp[0] = (int32_t)in.d[0];
+#pragma unroll
+    for (int k = 1; k < EL; ++k) sp.lp[k] = sp.lp[k - 1] + (int32_t)in.d[k];
+    int32_t mx = sp.lp[0], mn = sp.lp[0];
+#pragma unroll
+    for (int k = 1; k < EL; ++k) {
+        mx = max(mx, sp.lp[k]);
+        mn = min(mn, sp.lp[k]);
+    }
+    const int32_t lt = sp.lp[EL - 1];
+    int32_t incl = lt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    sp.ex = incl - lt;
+    sp.tot = __shfl_sync(FULL, incl, 31);
+    sp.lmax = mx + sp.ex;
+    sp.lmin = mn + sp.ex;
+    int4 *dst = reinterpret_cast<int4 *>(xq + lane * EL);
+    const int s = (lane >> 2) & 1;
+    dst[s] = make_int4(sp.ex + sp.lp[0], sp.ex + sp.lp[1], sp.ex + sp.lp[2], sp.ex + sp.lp[3]);
+    dst[s ^ 1] = make_int4(sp.ex + sp.lp[4], sp.ex + sp.lp[5], sp.ex + sp.lp[6], sp.ex + sp.lp[7]);
+    __syncwarp();
+}
+
+// first_cross on the 32-bit form (same contract)
+template <int EL>
+__device__ __forceinline__ int first_cross(const StepPrefix32<EL> &sp, const int32_t *xq, int lane, int32_t b,
+                                           int32_t T, int after, int32_t &Qr) {
+    const int32_t hi = T - b, lo = -T - b;
+    unsigned m = __ballot_sync(FULL, lane * EL + EL - 1 > after && (sp.lmax >= hi || sp.lmin <= lo));
+    while (m) {
+        const int fl = __ffs(m) - 1;
+        m &= m - 1;
+        const int32_t q = lane < EL ? xq[swz32(fl * EL + lane)] : 0;
+        const unsigned h = __ballot_sync(FULL, lane < EL && fl * EL + lane > after && (q >= hi || q <= lo));
+        if (h) {
+            const int kf = __ffs(h) - 1;
+            Qr = __shfl_sync(FULL, q, kf);
+            return fl * EL + kf;
+        }
+    }
+    return -1;
+}
+
 }  // namespace scl

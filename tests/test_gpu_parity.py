@@ -57,6 +57,38 @@ def test_adversarial_never_merges(T):
     assert_same(ctx, 0, oracle_of(tr, T))
 
 
+@pytest.mark.parametrize("T", [1 << 30, (1 << 30) + 1, 1_048_573])
+def test_candidate_counter_32bit_step_boundaries(T):
+    # the candidate counters take a 32-bit form of a step when T <= 2^30 and every delta of
+    # the step lies in [-2^22, 2^22): runs of the extreme deltas -2^22 and 2^22 - 1 (prefixes
+    # reaching -2^30 within one step), counters near +-T, and steps holding one delta just
+    # outside the range (2^22, -2^22 - 1, 2^40) mixed in
+    rng = np.random.default_rng(31)
+    parts = []
+    while sum(len(x) for x in parts) < 250_000:
+        n = int(rng.integers(1, 700))
+        mode = int(rng.integers(0, 5))
+        if mode == 0:
+            parts.append(np.full(n, (1 << 22) - 1, np.int64))
+        elif mode == 1:
+            parts.append(np.full(n, -(1 << 22), np.int64))
+        elif mode == 2:
+            parts.append(rng.choice(np.array([-(1 << 22), (1 << 22) - 1], np.int64), n))
+        elif mode == 3:
+            parts.append(rng.integers(-4096, 4097, n).astype(np.int64))
+        else:
+            x = rng.integers(-(1 << 22), 1 << 22, n).astype(np.int64)
+            x[int(rng.integers(0, n))] = int(rng.choice([1 << 22, -(1 << 22) - 1, 1 << 40, -(1 << 40)]))
+            parts.append(x)
+    d = np.concatenate(parts)
+    n = len(d)
+    tr = tg.Trace(d, np.arange(n, dtype=np.uint64) * 64, rng.integers(0, 64, n).astype(np.uint32),
+                  rng.integers(0, 2, n).astype(np.uint8))
+    ctx = gpu_ctx(T, n_lines=64, unit=8192, shift=0)   # up to one sample per event
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T, n_lines=64))
+
+
 def test_constant_closed_form():
     T = 1_048_573
     d, a, l, y = tg.constant(65536 + 100, 4096, 256)
