@@ -270,6 +270,7 @@ typedef struct {
     uint64_t transparent;       /* ... of which held no sample (skipped in O(1)) */
     uint64_t unit_events;       /* tuned events per unit (0: sized per batch) */
     uint64_t walked_events;     /* events the chain's walks covered before merging (or to the unit end) */
+    uint64_t searched;          /* units replayed exactly without a reset list (crossings searched) */
     uint64_t first_events;      /* events of the traces' first units (replayed exactly from the resident state) */
     uint64_t sketch_events;     /* events the candidate counters streamed: the other units and their warm-ups */
 } scl_batch_info;

@@ -92,8 +92,36 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         }
         return __any_sync(FULL, h);
     };
-    // every event of the step joins the open window (no sample in it)
+    // every event of the step joins the open window (no sample in it).  When the step's
+    // deltas lie in [-2^27, 2^27) a lane's sums over its 8 events fit in int32: they are
+    // formed in 32 bits and added to the 64-bit totals once, and the frees are screened on
+    // the low address word (a match is confirmed on the full address).
     auto whole_step = [&](const StepIn<E> &in) {
+        if (__all_sync(FULL, deltas_within<27>(in))) {
+            int32_t sA = 0, sApy = 0, sSpy = 0;
+            const uint32_t tlo = (uint32_t)taddr;
+            bool hl = false;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int32_t x = (int32_t)in.d[k];
+                const int32_t ps = max(x, 0);
+                const int32_t p = (int32_t)min(py_of(in, k), 1u);
+                sA += ps;
+                sApy += ps * p;
+                sSpy += x * p;
+                hl |= x < 0 && (uint32_t)in.a[k] == tlo;
+            }
+            accA += sA;
+            accApy += sApy;
+            accSpy += sSpy;
+            if (tk && __any_sync(FULL, hl)) {
+                bool h = false;
+#pragma unroll
+                for (int k = 0; k < E; ++k) h |= in.d[k] < 0 && in.a[k] == taddr;
+                if (__any_sync(FULL, h)) hit_tracked();
+            }
+            return;
+        }
         bool h = false;
 #pragma unroll
         for (int k = 0; k < E; ++k) {

@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ unit
                                                   const UnitTrue *__restrict__ utrue,
                                                   const UnitPlan *__restrict__ uplan, const SRes *__restrict__ lists,
                                                   FRec *recs, UnitOut *uout, int64_t T, unsigned *queue, ErrWord *err,
-                                                  unsigned long long spin) {
+                                                  unsigned long long spin, unsigned long long *stats) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FinalRing &sm = reinterpret_cast<FinalRing *>(smem_raw)[warp];
@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ unit
         in0.list = Tu.list != NO_LIST ? lists + U.lst0 + (uint64_t)Tu.list * U.lst_cap : nullptr;
         in0.nres = Tu.n;
         in0.exit_c = Tu.exit_c;
+        if (!in0.list && lane == 0) atomicAdd(&stats[5], 1ull);
         UnitOut O;
         uint32_t n = 0;
         const bool ok = exact_unit<false>(sm, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O,
@@ -89,7 +90,7 @@ cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_final<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.utrue, a.uplan, a.lists, a.recs,
-                                                           a.uout, a.T, a.queue, a.err, a.spin);
+                                                           a.uout, a.T, a.queue, a.err, a.spin, a.stats);
     return cudaGetLastError();
 }
 

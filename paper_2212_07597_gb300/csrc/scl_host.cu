@@ -218,7 +218,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     }
     CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * q.nbt, s), "memset");
     CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
-    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * 5, s), "memset");
+    CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * NSTATS, s), "memset");
     // the kernels of the event path run on a high-priority stream forked from the caller's,
     // so the copy-volume pass on the side stream takes only what they leave of the SMs
     cudaStream_t s_user = s;
@@ -346,6 +346,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         f.queue = c->queue + 2;
         f.err = c->errw;
         f.spin = cfg.spin_limit;
+        f.stats = c->stats;
         f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (nunits + c->num_sms - 1) / c->num_sms));
         int bps = 0;
         if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
@@ -466,8 +467,8 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMalloc(&c->errw, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaMalloc(&c->scores, sizeof(scl_leak_score) * L);
     if (e == cudaSuccess) e = cudaMalloc(&c->queue, sizeof(unsigned) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(unsigned long long) * 5);
-    if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * 5);
+    if (e == cudaSuccess) e = cudaMalloc(&c->stats, sizeof(unsigned long long) * NSTATS);
+    if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * NSTATS);
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
@@ -1035,7 +1036,7 @@ int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
     if (!c || !out) return SCL_EINVAL;
     int r = sync_and_check(c);
     if (r) return r;
-    unsigned long long v[5];
+    unsigned long long v[NSTATS];
     CK(cudaMemcpy(v, c->stats, sizeof v, cudaMemcpyDeviceToHost), "read batch stats");
     memset(out, 0, sizeof *out);
     out->units = c->last_units;
@@ -1045,6 +1046,7 @@ int scl_batch_stats(scl_ctx *c, scl_batch_info *out) {
     out->transparent = v[3];
     out->unit_events = c->tune.unit_events;
     out->walked_events = v[4];
+    out->searched = v[5];
     out->first_events = c->last_first_events;
     out->sketch_events = c->last_sketch_events;
     return SCL_OK;

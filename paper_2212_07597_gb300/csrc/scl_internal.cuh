@@ -96,7 +96,7 @@ constexpr int RM = 32;    // leading resets kept per candidate, to let a walk me
 
 // ---- reset lists: every reset of up to NL distinct candidate runs per unit, so the
 // exact replay of a unit whose true run has a complete list needs no crossing search
-constexpr int NL = 4;
+constexpr int NL = 8;
 constexpr uint32_t NO_LIST = 0xffffffffu;
 struct SRes {
     uint32_t pos;         // unit offset of the reset

@@ -6,6 +6,9 @@
 
 namespace scl {
 
+// device counters of a batch: units walked, walked and merged, explicit entries,
+// transparent, events walked (k_chain); units replayed with the crossing search (k_final)
+constexpr int NSTATS = 6;
 constexpr int SKETCH_MAX_WARPS = 16;   // k_sketch warps per block (its launch bound)
 constexpr int SKETCH_MIN_BLOCKS = 1;   // k_sketch blocks of SKETCH_MAX_WARPS resident per SM
 constexpr int FIRST_WARPS = 4;         // k_first warps per block
@@ -32,11 +35,12 @@ struct LaunchSketch {
     unsigned *queue;     // [0] sketch, [1] first units, [2] final
     ErrWord *err;
     unsigned long long spin;
-    unsigned long long *stats;   // [walked, walked and merged, explicit entries, transparent, events walked]
+    unsigned long long *stats;   // NSTATS counters of the batch, see NSTATS
     int blocks, warps_per_block, num_sms;
 };
 
 struct LaunchFinal {
+    unsigned long long *stats;   // [5]: units replayed with the crossing search
     const Unit *units;
     int nunits;
     const UnitTrue *utrue;

@@ -335,6 +335,7 @@ static_assert(offsetof(ChainSmem, slot) % 16 == 0 && sizeof(WalkSlot) % 16 == 0 
                   offsetof(WalkSlot, xq) % 16 == 0,
               "walk slots take 16-byte stores");
 static_assert(offsetof(ChainSmem, m) % 16 == 0, "match rows take 16-byte copies");
+static_assert(sizeof(ChainSmem) <= 227 * 1024, "the chain block's shared memory fits one SM");
 
 // Walk unit U from counter c until one of its resets is also a reset of a candidate of the
 // unit -- from there the run is that candidate's -- or to the unit's end.  The whole block

@@ -276,19 +276,26 @@ __device__ __forceinline__ int first_cross(const StepPrefix<EL> &sp, const int64
 constexpr int64_t FIT32_T = 1ll << 30;   // largest T for the 32-bit form
 constexpr int FIT32_SHIFT = 22;          // deltas in [-2^22, 2^22)
 
-template <int EL>
-__device__ __forceinline__ bool step_fits32(const StepIn<EL> &in) {
-    // d fits iff its high word is the sign extension of its low word (d is an int32)
-    // and the low word lies in [-2^22, 2^22), i.e. low + 2^22 < 2^23 as unsigned
+// This lane's deltas all lie in [-2^SHIFT, 2^SHIFT) (SHIFT < 31): each high word is the
+// sign extension of its low word (the delta is an int32) and low + 2^SHIFT < 2^(SHIFT+1)
+// as unsigned.
+template <int SHIFT, int EL>
+__device__ __forceinline__ bool deltas_within(const StepIn<EL> &in) {
+    static_assert(SHIFT > 0 && SHIFT < 31, "a 32-bit range");
     uint32_t hx = 0, lv = 0;
 #pragma unroll
     for (int k = 0; k < EL; ++k) {
         const uint32_t lo = (uint32_t)(uint64_t)in.d[k];
         const uint32_t hi = (uint32_t)((uint64_t)in.d[k] >> 32);
         hx |= hi ^ (uint32_t)((int32_t)lo >> 31);
-        lv |= lo + (1u << FIT32_SHIFT);
+        lv |= lo + (1u << SHIFT);
     }
-    return hx == 0 && (lv >> (FIT32_SHIFT + 1)) == 0;
+    return hx == 0 && (lv >> (SHIFT + 1)) == 0;
+}
+
+template <int EL>
+__device__ __forceinline__ bool step_fits32(const StepIn<EL> &in) {
+    return deltas_within<FIT32_SHIFT>(in);
 }
 
 template <int EL>

@@ -435,7 +435,8 @@ def scl_kernel_times(ctx: Context) -> dict:
 
 BATCH_INFO_DTYPE = np.dtype([("units", "<u8"), ("walked", "<u8"), ("walked_merged", "<u8"),
                              ("explicit_entries", "<u8"), ("transparent", "<u8"), ("unit_events", "<u8"),
-                             ("walked_events", "<u8"), ("first_events", "<u8"), ("sketch_events", "<u8")])
+                             ("walked_events", "<u8"), ("searched", "<u8"), ("first_events", "<u8"),
+                             ("sketch_events", "<u8")])
 
 
 def scl_batch_stats(ctx: Context) -> dict:
