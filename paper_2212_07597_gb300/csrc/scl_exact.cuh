@@ -231,8 +231,41 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, kstep);
         c = in0.exit_c;
     } else {
-        // ---- search for the crossings from the entry counter
+        // ---- search for the crossings from the entry counter (in the 32-bit form of a
+        // step when T and the step's deltas allow it: the same arithmetic without overflow)
+        const bool t32 = T <= FIT32_T;
         auto step = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+            if (t32 && __all_sync(FULL, step_fits32(in))) {
+                StepPrefix32<E> sp;
+                int32_t *xq32 = reinterpret_cast<int32_t *>(sm.xq);
+                step_prefix32(in, lane, sp, xq32);
+                if (FIRST) {
+                    umax = P + sp.lmax > umax ? P + sp.lmax : umax;
+                    umin = P + sp.lmin < umin ? P + sp.lmin : umin;
+                }
+                const int32_t T32 = (int32_t)T;
+                int32_t b = (int32_t)c;
+                if (__ballot_sync(FULL, b + sp.lmax >= T32 || b + sp.lmin <= -T32) == 0) {
+                    whole_step(in);
+                    c += sp.tot;
+                    P += sp.tot;
+                    return false;
+                }
+                int after = -1;
+                while (true) {
+                    int32_t Qr;
+                    const int r = first_cross(sp, (const int32_t *)xq32, lane, b, T32, after, Qr);
+                    if (tk && frees_hit(in, after, r < 0 ? STEP : r)) hit_tracked();
+                    if (r < 0) break;
+                    close(in, after, r, rel0, (int64_t)(b + Qr), P + Qr);
+                    b = -Qr;
+                    after = r;
+                }
+                add_events(in, after, STEP, accA, accApy, accSpy);
+                c = b + sp.tot;
+                P += sp.tot;
+                return false;
+            }
             StepPrefix<E> sp;
             step_prefix(in, lane, sp, sm.xq);
             if (FIRST) {

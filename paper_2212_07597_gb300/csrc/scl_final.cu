@@ -11,6 +11,8 @@ namespace scl {
 
 using FinalRing = Ring<true, 3, 256, 8>;
 
+// 14 warps per block at most (128 registers, a few spilled on cold paths: a cap of 136
+// registers left blocks of only 12 warps on an SM, and the replay ran 40% longer)
 __global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ units, int nunits,
                                                   const UnitTrue *__restrict__ utrue,
                                                   const UnitPlan *__restrict__ uplan, const SRes *__restrict__ lists,

@@ -349,6 +349,8 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         f.stats = c->stats;
         f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (nunits + c->num_sms - 1) / c->num_sms));
         int bps = 0;
+        // fewer warps per block if the requested block does not fit an SM
+        while (f.warps_per_block > 1 && (final_occupancy(f.warps_per_block, &bps) || bps < 1)) --f.warps_per_block;
         if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
         f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
         Prof p(c, s, "final");
@@ -594,12 +596,22 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         B.u0 = (uint32_t)units.size();
         B.c0 = (uint32_t)ctiles.size();
         uint64_t gidx = c->h_events[B.trace];
+        // The trace's first unit is replayed exactly by one warp (k_first) beside the sketch
+        // of the others.  With fewer traces than SMs those warps run nearly alone, so when
+        // more units follow the first one is kept to one warm-up's length and its warp is
+        // done well before the sketch; with many traces the first units keep full length
+        // (one exact pass instead of a sketch pass and an exact one).
+        const uint64_t W = c->tune.ext_events ? c->tune.ext_events : 32768;
+        const uint64_t first_len = nbt < (uint32_t)c->num_sms && tev[b] > UE
+                                       ? std::min<uint64_t>(UE, std::max<uint64_t>(32768, (W + UNIT_ALIGN - 1) / UNIT_ALIGN * UNIT_ALIGN))
+                                       : UE;
         for (uint32_t i : groups[b]) {
             const scl_segment &g = segs[i];
-            for (uint64_t off = 0; off < g.ev.n; off += UE) {
+            for (uint64_t off = 0, len; off < g.ev.n; off += len) {
+                len = std::min<uint64_t>(units.size() == B.u0 ? first_len : UE, g.ev.n - off);
                 Unit U;
                 memset(&U, 0, sizeof U);
-                U.len = std::min<uint64_t>(UE, g.ev.n - off);
+                U.len = len;
                 U.delta = g.ev.delta + off;
                 U.py = g.ev.is_python + off;
                 U.addr = g.ev.addr + off;

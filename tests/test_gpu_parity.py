@@ -23,7 +23,7 @@ def test_plain_1m_default_tuning():
     assert_same(ctx, 0, oracle_of(tr, T0))
 
 
-@pytest.mark.parametrize("unit", [1024, 4096, 32768])
+@pytest.mark.parametrize("unit", [1024, 4096, 32768, 131072])
 def test_small_units_speculation_and_merge(unit):
     tr = tg.plain_trace(300_001, seed=1, leak_lines=(0, 3))
     ctx = gpu_ctx(T0, unit=unit)
