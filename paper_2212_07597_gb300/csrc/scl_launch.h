@@ -12,7 +12,7 @@ constexpr int NSTATS = 6;
 constexpr int SKETCH_MAX_WARPS = 16;   // k_sketch warps per block (its launch bound)
 constexpr int SKETCH_MIN_BLOCKS = 1;   // k_sketch blocks of SKETCH_MAX_WARPS resident per SM
 constexpr int FIRST_WARPS = 4;         // k_first warps per block
-constexpr int SKETCH_TILE = 256;       // k_sketch events per staged tile (warm-ups start on one)
+constexpr int SKETCH_TILE = 512;       // k_sketch events per staged tile (warm-ups start on one)
 
 struct LaunchSketch {
     const Unit *units;

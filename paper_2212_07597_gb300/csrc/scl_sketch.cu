@@ -94,9 +94,15 @@ __device__ __forceinline__ void sketch_step(const StepIn<8> &in, int64_t *xq, in
     }
 }
 
+// Lanes holding the same counter.  With T <= 2^30 every counter lies in (-2^30, 2^30), so
+// its low word identifies it and the 32-bit match serves.
+__device__ __forceinline__ unsigned match_counter(int64_t c, bool t32) {
+    return t32 ? __match_any_sync(FULL, (unsigned)c) : __match_any_sync(FULL, (unsigned long long)c);
+}
+
 // ---------------------------------------------------------------- k_sketch
 constexpr int SE = 8;                         // events per lane per sketch step (256 per step)
-using SketchRing = Ring<false, 2, 256, SE>;   // one step per tile: the other tile is in flight
+using SketchRing = Ring<false, 2, 512, SE>;   // two steps per tile: the other tile is in flight
 constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing);
 static_assert(SketchRing::kTL == SKETCH_TILE, "the host counts warm-up events in these tiles");
 static_assert(SKETCH_WARP_SMEM * SKETCH_MAX_WARPS * SKETCH_MIN_BLOCKS <= 227 * 1024,
@@ -132,7 +138,7 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sk
                 const bool act = lead == lane;
                 int64_t tot, qmax, qmin;
                 sketch_step(in, sm.xq, lane, T, t32, act, c, tot, qmax, qmin, [](int, int, bool, int64_t) {});
-                const unsigned same = __match_any_sync(FULL, (unsigned long long)c) & __ballot_sync(FULL, act);
+                const unsigned same = match_counter(c, t32) & __ballot_sync(FULL, act);
                 if (act) lead = __ffs(same) - 1;
                 return false;
             };
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sk
             c = __shfl_sync(FULL, c, lead);
         }
         const int64_t c0 = c;
-        const unsigned same = __match_any_sync(FULL, (unsigned long long)c);
+        const unsigned same = match_counter(c, t32);
         const int leader = __ffs(same) - 1;
         const bool active = leader == lane;
         // the first NL distinct runs record every reset (for the exact replay)
