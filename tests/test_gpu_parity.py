@@ -331,19 +331,24 @@ def test_edge_cases_tiny_traces_one_line_huge_threshold():
 
 @pytest.mark.parametrize("pinned", [False, True])
 def test_host_entry_point_many_pieces_over_copy_streams(pinned):
-    # host arrays larger than one staging piece go over several copy streams; a pinned event
-    # line column is read in place by the kernels instead of copied
-    tr = tg.plain_trace(9_000_000, seed=33)
-    ctx = gpu_ctx(T0, log_cap=1 << 18)
-    cols = [tr.delta, tr.addr, tr.line, tr.is_python, tr.csize, tr.cline, tr.cpy]
-    if pinned:
-        import torch
-        cols = [torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else
-                                 x.view(np.int32) if x.dtype == np.uint32 else x).pin_memory().numpy() for x in cols]
-    seg = scl.segment(0, *cols)
-    scl.scl_replay_batch_host(ctx, [seg])
+    # host arrays larger than one 64 MiB staging piece go over several copy streams, for
+    # two traces in one call; a pinned event line column is read in place
+    trs = [tg.plain_trace(777_777, seed=34), tg.plain_trace(16_000_000, seed=33)]
+    ctx = gpu_ctx(T0, log_cap=1 << 18, max_traces=2)
+    segs, keep = [], []   # the host arrays must outlive the call's stream work
+    for tid, tr in enumerate(trs):
+        cols = [tr.delta, tr.addr, tr.line, tr.is_python, tr.csize, tr.cline, tr.cpy]
+        if pinned:
+            import torch
+            cols = [torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else
+                                     x.view(np.int32) if x.dtype == np.uint32 else x).pin_memory().numpy()
+                    for x in cols]
+        keep.append(cols)
+        segs.append(scl.segment(tid, *cols))
+    scl.scl_replay_batch_host(ctx, segs)
     scl.scl_sync(ctx)
-    assert_same(ctx, 0, oracle_of(tr, T0))
+    for tid, tr in enumerate(trs):
+        assert_same(ctx, tid, oracle_of(tr, T0))
 
 
 def test_leak_report_matches_oracle():
