@@ -274,13 +274,14 @@ def measured_peak():
 
 def roofline_of(ktimes, n, m, traffic=True, sketch_n=None):
     """Dominant kernel of the path and its algorithmic GB/s over its CUDA-event time per launch.
-    The sketch streams the events of every unit but the traces' first ones (sketch_n).  The
+    The sketch and the exact replay take the events of every unit but the traces' first ones
+    (sketch_n; those are replayed by k_first).  The
     dominant kernel is taken on the event path's stream: the copy-volume kernels run on a
     lower-priority side stream beside it, so their event-timed spans include waits for SMs."""
     dom = max((k for k in ktimes if k in EVENT_KERNELS), key=lambda k: ktimes[k][0])
     d_ms, d_cnt = ktimes[dom]
     units = n if dom in EVENT_KERNELS else m
-    if dom == "sketch" and sketch_n is not None:
+    if dom in EVENT_KERNELS and sketch_n is not None:
         units = sketch_n
     achieved = ALG_BYTES[dom] * units / (d_ms / d_cnt / 1e3) / 1e9
     peak, src = measured_peak()
@@ -743,7 +744,7 @@ def main():
     dom = max((k for k in ktimes if k in EVENT_KERNELS), key=lambda k: ktimes[k][0])   # see roofline_of
     d_ms, d_cnt = ktimes[dom]
     per_launch_units = n if dom in EVENT_KERNELS else m
-    if dom == "sketch":   # the trace's first unit is replayed exactly by k_first instead
+    if dom in EVENT_KERNELS:   # the trace's first unit is replayed exactly by k_first instead
         per_launch_units = n - bstats["first_events"]
     alg = ALG_BYTES[dom] * per_launch_units
     achieved = alg / (d_ms / d_cnt / 1e3) / 1e9
@@ -843,7 +844,9 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
                 "data": "synthetic",
                 "config": {"workload": meta["workload"], "threshold": meta["threshold"], "n_lines": meta["n_lines"],
-                           "memcpys": m, "l2": "inputs larger than L2 (5.9 GB per step), no flush",
+                           "memcpys": m,
+                           "l2": f"inputs larger than L2 ({(PATH_BYTES_PER_EVENT * n + PATH_BYTES_PER_COPY * m) / 1e9:.1f} GB "
+                                 "per step), no flush",
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
                 "hbm_gbs_path": path_gbs,
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
