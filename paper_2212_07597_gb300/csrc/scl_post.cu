@@ -104,43 +104,102 @@ __device__ __forceinline__ MaxPos mp_shfl(const MaxPos &x, int l) {
     return y;
 }
 
-// block-wide exclusive (max, first position) scan; *total = block result
-__device__ MaxPos block_excl_maxpos(MaxPos v, MaxPos *sh, MaxPos *total) {
+// N sums (and N (max, first position) scans) over a block of BT threads at once: one set of
+// barriers for all of them instead of one per scan.  ex = exclusive result, tot = block total.
+template <int BT, int N>
+__device__ __forceinline__ void block_excl_sums(const int64_t (&v)[N], int64_t (&ex)[N], int64_t (&tot)[N],
+                                                int64_t (*sh)[N]) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const MaxPos id = {INT64_MIN, 0, -1};
-    MaxPos x = v;
+    int64_t x[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = v[k];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        MaxPos t = mp_shfl_up(x, o);
-        if (lane >= o) x = mp_better(t, x);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int64_t t = __shfl_up_sync(FULL, x[k], o);
+            if (lane >= o) x[k] += t;
+        }
     }
-    MaxPos ex = mp_shfl_up(x, 1);
-    if (lane == 0) ex = id;
-    if (lane == 31) sh[w] = x;
+    if (lane == 31)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[w][k] = x[k];
     __syncthreads();
     if (w == 0) {
-        MaxPos y = lane < NT / 32 ? sh[lane] : id;
-        MaxPos yi = y;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            MaxPos t = mp_shfl_up(yi, o);
-            if (lane >= o) yi = mp_better(t, yi);
+        for (int k = 0; k < N; ++k) {
+            const int64_t y = lane < BT / 32 ? sh[lane][k] : 0;
+            int64_t yi = y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t t = __shfl_up_sync(FULL, yi, o);
+                if (lane >= o) yi += t;
+            }
+            if (lane < BT / 32) sh[lane][k] = yi - y;
+            if (lane == BT / 32 - 1) sh[BT / 32][k] = yi;
         }
-        MaxPos ye = mp_shfl_up(yi, 1);
-        if (lane == 0) ye = id;
-        if (lane < NT / 32) sh[lane] = ye;
-        if (lane == NT / 32 - 1) sh[NT / 32] = yi;
     }
     __syncthreads();
-    const MaxPos r = mp_better(sh[w], ex);
-    *total = sh[NT / 32];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        ex[k] = x[k] - v[k] + sh[w][k];
+        tot[k] = sh[BT / 32][k];
+    }
     __syncthreads();
-    return r;
 }
 
-__global__ void __launch_bounds__(NT) k_scan(LaunchPost a) {
-    __shared__ int64_t sh[NT / 32 + 1];
-    __shared__ MaxPos shm[NT / 32 + 1];
+template <int BT, int N>
+__device__ __forceinline__ void block_excl_maxpos_n(const MaxPos (&v)[N], MaxPos (&ex)[N], MaxPos (&tot)[N],
+                                                    MaxPos (*sh)[N]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const MaxPos id = {INT64_MIN, 0, -1};
+    MaxPos x[N], e[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) x[k] = v[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const MaxPos t = mp_shfl_up(x[k], o);
+            if (lane >= o) x[k] = mp_better(t, x[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        e[k] = mp_shfl_up(x[k], 1);
+        if (lane == 0) e[k] = id;
+        if (lane == 31) sh[w][k] = x[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const MaxPos y = lane < BT / 32 ? sh[lane][k] : id;
+            MaxPos yi = y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const MaxPos t = mp_shfl_up(yi, o);
+                if (lane >= o) yi = mp_better(t, yi);
+            }
+            MaxPos ye = mp_shfl_up(yi, 1);
+            if (lane == 0) ye = id;
+            if (lane < BT / 32) sh[lane][k] = ye;
+            if (lane == BT / 32 - 1) sh[BT / 32][k] = yi;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        ex[k] = mp_better(sh[w][k], e[k]);
+        tot[k] = sh[BT / 32][k];
+    }
+    __syncthreads();
+}
+
+template <int BT>
+__global__ void __launch_bounds__(BT) k_scan(LaunchPost a) {
+    __shared__ int64_t sh[BT / 32 + 1][5];
+    __shared__ MaxPos shm[BT / 32 + 1][2];
     const int b = blockIdx.x;
     const BTrace B = a.bts[b];
     const DevTrace st = a.traces[B.trace];
@@ -148,33 +207,31 @@ __global__ void __launch_bounds__(NT) k_scan(LaunchPost a) {
     int64_t ccnt = 0, cfp = st.footprint, cA = 0, cApy = 0, cSpy = 0;
     MaxPos cg = none;     // best growth footprint of the batch so far
     MaxPos clast = none;  // latest reset so far (v = trace index)
-    for (uint32_t base = 0; base < B.nu; base += NT) {
+    for (uint32_t base = 0; base < B.nu; base += BT) {
         const uint32_t i = base + threadIdx.x;
         const bool valid = i < B.nu;
         const uint32_t u = B.u0 + (valid ? i : 0);
         const Unit &U = a.units[u];
         const UnitTrue Tu = a.utrue[u];
         const UnitSum S = a.usum[u];
-        int64_t t;
-        const int64_t ec = block_excl_sum(valid ? (int64_t)Tu.n : 0, sh, &t);
-        const int64_t ncnt = ccnt + t;
-        const int64_t et = block_excl_sum(valid ? S.total : 0, sh, &t);
-        const int64_t fpb = cfp + et;
-        const int64_t nfp = cfp + t;
-        const int64_t eA = block_excl_sum(valid ? S.totA : 0, sh, &t);
-        const int64_t nA = cA + t;
-        const int64_t eApy = block_excl_sum(valid ? S.totApy : 0, sh, &t);
-        const int64_t nApy = cApy + t;
-        const int64_t eSpy = block_excl_sum(valid ? S.totSpy : 0, sh, &t);
-        const int64_t nSpy = cSpy + t;
-        MaxPos g = none;
-        if (valid && Tu.gmax != INT64_MIN) { g.v = fpb + Tu.gmax; g.pos = U.gidx0 + Tu.garg; g.unit = u; }
-        MaxPos gt;
-        const MaxPos eg = mp_better(cg, block_excl_maxpos(g, shm, &gt));
-        MaxPos lr = none;
-        if (valid && Tu.exit_last >= 0) { lr.v = Tu.exit_last; lr.pos = (uint64_t)Tu.exit_last; lr.unit = u; }
-        MaxPos lt;
-        const MaxPos el = mp_better(clast, block_excl_maxpos(lr, shm, &lt));
+        // sample counts, footprint changes and window totals of the units, scanned at once
+        int64_t sv[5] = {valid ? (int64_t)Tu.n : 0, valid ? S.total : 0, valid ? S.totA : 0,
+                         valid ? S.totApy : 0, valid ? S.totSpy : 0};
+        int64_t se[5], st5[5];
+        block_excl_sums<BT, 5>(sv, se, st5, sh);
+        const int64_t ec = se[0], ncnt = ccnt + st5[0];
+        const int64_t fpb = cfp + se[1], nfp = cfp + st5[1];
+        const int64_t eA = se[2], nA = cA + st5[2];
+        const int64_t eApy = se[3], nApy = cApy + st5[3];
+        const int64_t eSpy = se[4], nSpy = cSpy + st5[4];
+        // the best growth footprint and the latest reset before each unit
+        MaxPos mv[2] = {none, none};
+        if (valid && Tu.gmax != INT64_MIN) { mv[0].v = fpb + Tu.gmax; mv[0].pos = U.gidx0 + Tu.garg; mv[0].unit = u; }
+        if (valid && Tu.exit_last >= 0) { mv[1].v = Tu.exit_last; mv[1].pos = (uint64_t)Tu.exit_last; mv[1].unit = u; }
+        MaxPos me[2], mt[2];
+        block_excl_maxpos_n<BT, 2>(mv, me, mt, shm);
+        const MaxPos eg = mp_better(cg, me[0]), gt = mt[0];
+        const MaxPos el = mp_better(clast, me[1]), lt = mt[1];
         if (valid) {
             UnitPlan Pn;
             Pn.fp_base = fpb;
@@ -223,23 +280,23 @@ __global__ void __launch_bounds__(NT) k_scan(LaunchPost a) {
 
 // window totals of the units strictly between a reset's unit and the unit it opens
 // into: a second pass over the units, once every unit's read-back unit is known
-__global__ void __launch_bounds__(NT) k_scan_window(LaunchPost a) {
-    __shared__ int64_t sh[NT / 32 + 1];
+template <int BT>
+__global__ void __launch_bounds__(BT) k_scan_window(LaunchPost a) {
+    __shared__ int64_t sh[BT / 32 + 1][3];
     const BTrace B = a.bts[blockIdx.x];
     // prefix sums of the unit totals, then differences
     int64_t cA = 0, cApy = 0, cSpy = 0;
-    for (uint32_t base = 0; base < B.nu; base += NT) {
+    for (uint32_t base = 0; base < B.nu; base += BT) {
         const uint32_t i = base + threadIdx.x;
         const bool valid = i < B.nu;
         const uint32_t u = B.u0 + (valid ? i : 0);
         const UnitSum S = a.usum[u];
-        int64_t t;
-        const int64_t eA = block_excl_sum(valid ? S.totA : 0, sh, &t);
-        const int64_t nA = cA + t;
-        const int64_t eApy = block_excl_sum(valid ? S.totApy : 0, sh, &t);
-        const int64_t nApy = cApy + t;
-        const int64_t eSpy = block_excl_sum(valid ? S.totSpy : 0, sh, &t);
-        const int64_t nSpy = cSpy + t;
+        int64_t sv[3] = {valid ? S.totA : 0, valid ? S.totApy : 0, valid ? S.totSpy : 0};
+        int64_t se[3], stt[3];
+        block_excl_sums<BT, 3>(sv, se, stt, sh);
+        const int64_t eA = se[0], nA = cA + stt[0];
+        const int64_t eApy = se[1], nApy = cApy + stt[1];
+        const int64_t eSpy = se[2], nSpy = cSpy + stt[2];
         if (valid) {
             a.pref[3 * (size_t)u + 0] = cA + eA;
             a.pref[3 * (size_t)u + 1] = cApy + eApy;
@@ -248,7 +305,7 @@ __global__ void __launch_bounds__(NT) k_scan_window(LaunchPost a) {
         cA = nA; cApy = nApy; cSpy = nSpy;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < B.nu; i += NT) {
+    for (uint32_t i = threadIdx.x; i < B.nu; i += BT) {
         const uint32_t u = B.u0 + i;
         UnitPlan &Pn = a.uplan[u];
         if (Pn.rb_unit < 0) continue;
@@ -685,10 +742,14 @@ cudaError_t launch_report(const LineRow *lines, const DevTrace *traces, uint32_t
 
 cudaError_t launch_scan(const LaunchPost &a, cudaStream_t s) {
     if (!a.nbt) return cudaSuccess;
-    k_scan<<<a.nbt, NT, 0, s>>>(a);
+    // one block per trace: 1,024 threads when traces average hundreds of units
+    const bool wide = a.nunits / a.nbt > NT;
+    if (wide) k_scan<1024><<<a.nbt, 1024, 0, s>>>(a);
+    else k_scan<NT><<<a.nbt, NT, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_scan_window<<<a.nbt, NT, 0, s>>>(a);
+    if (wide) k_scan_window<1024><<<a.nbt, 1024, 0, s>>>(a);
+    else k_scan_window<NT><<<a.nbt, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
