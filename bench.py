@@ -757,6 +757,14 @@ def main():
     peak_src = "of measured" if peak else "of fallback"
     peak = peak or 6800.0
     path_gbs = (PATH_BYTES_PER_EVENT * n + PATH_BYTES_PER_COPY * m) * args.steps / (ms / 1e3) / 1e9
+    # both event-path kernels (the dominant one above, and the other), same arithmetic
+    ev_roof = {}
+    for k in EVENT_KERNELS:
+        if k in ktimes and ktimes[k][1]:
+            u = n - bstats["first_events"]
+            a_k = ALG_BYTES[k] * u / (ktimes[k][0] / ktimes[k][1] / 1e3) / 1e9
+            ev_roof[k] = {"ms": ktimes[k][0] / ktimes[k][1], "achieved": a_k, "frac": a_k / peak,
+                          "traffic": traffic_for(k, u, bstats["sketch_events"])}
 
     # end to end through the host entry point
     e2e = None
@@ -853,6 +861,7 @@ def main():
                              "frac": achieved / peak, "peak_source": peak_src,
                              "traffic": traffic_for(dom, per_launch_units, bstats["sketch_events"]),
                              "alg_bytes_per_unit": ALG_BYTES[dom]},
+                "roofline_event_kernels": ev_roof,
                 "kernels_ms_per_step": {k: v[0] / max(1, v[1]) * (v[1] / args.steps) for k, v in ktimes.items()},
                 "tuning": tuned,
                 "gpu_launches": launches,
