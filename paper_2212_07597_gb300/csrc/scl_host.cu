@@ -58,9 +58,10 @@ struct scl_ctx {
     cudaEvent_t plan_done = nullptr;
     bool plan_pending = false;
     // the copy-volume pass (Section 3.5) shares nothing with the event path: it runs on a
-    // side stream between a fork after the sketch and a join before the state fold
+    // side stream (after the first units' exact replay) between a fork at the start of the
+    // call and a join before the state fold
     cudaStream_t side = nullptr, hi = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr, ev_first = nullptr;
+    cudaEvent_t ev_join = nullptr, ev_in = nullptr, ev_out = nullptr, ev_first = nullptr;
     // host-to-device staging of scl_replay_batch_host: pieces spread over several copy
     // streams (several copy engines at once), joined back before the replay
     static constexpr int NCS = 4;
@@ -225,6 +226,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     CK(cudaEventRecord(c->ev_in, s_user), "fork event");
     s = c->hi;
     CK(cudaStreamWaitEvent(s, c->ev_in, 0), "fork the event path");
+    CK(cudaStreamWaitEvent(c->side, c->ev_in, 0), "fork the side stream");
 
     const Unit *d_units = reinterpret_cast<const Unit *>(dp + q.o_units);
     const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + q.o_bts);
@@ -288,7 +290,6 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
         // the first unit of each trace (whose entry is known) is replayed exactly on the side
         // stream, beside the sketch of the other units
-        CK(cudaStreamWaitEvent(c->side, c->ev_in, 0), "fork the first units");
         {
             Prof p(c, c->side, "first");
             CK(launch_first(k, c->side), "launch first");
@@ -298,7 +299,6 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
             Prof p(c, s, "sketch");
             CK(launch_sketch(k, s), "launch sketch");
         }
-        CK(cudaEventRecord(c->ev_fork, s), "fork event");
         CK(cudaStreamWaitEvent(s, c->ev_first, 0), "join the first units");
         {
             Prof p(c, s, "match");
@@ -313,9 +313,9 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
             CK(launch_totals(k, s), "launch totals");
         }
     }
-    // ---- the copy-volume pass, on the side stream (after the sketch when there is one)
-    if (!nunits) CK(cudaEventRecord(c->ev_fork, s), "fork event");
-    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork the copy pass");
+    // ---- the copy-volume pass, on the side stream after the first units: it shares nothing
+    // with the event path, and its blocks (which cannot sit beside a sketch block) take the
+    // SMs that the sketch's last units leave idle
     {
         Prof p(c, c->side, "copy_sum");
         CK(launch_copy_sum(a, c->side), "launch copy sum");
@@ -424,7 +424,6 @@ void scl_replay_free(scl_ctx *c) {
     cudaFree(c->stats);
     if (c->h_plan) cudaFreeHost(c->h_plan);
     if (c->plan_done) cudaEventDestroy(c->plan_done);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_first) cudaEventDestroy(c->ev_first);
     if (c->side) cudaStreamDestroy(c->side);
@@ -481,7 +480,6 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming);
     for (int i = 0; i < scl_ctx::NCS && e == cudaSuccess; ++i)
