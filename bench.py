@@ -652,7 +652,9 @@ def run_serving(args):
                                "served_events_per_s": N / (sum(rt_walls) / len(rt_walls)),
                                "batches_per_pass": float(np.mean(rt_batches))},
                 "saturated_batches_per_pass": float(np.mean(batches)),
-                "roofline": dict(roof, measured="per-kernel CUDA events over one profiled saturated pass"),
+                "roofline": dict(roof, measured="per-kernel CUDA events over one profiled saturated pass",
+                                 note="units = a batch's events on average; the traces' first units of each "
+                                      "batch go to k_first instead, so this is an upper bound"),
                 "kernels_ms_per_pass": {k: v[0] for k, v in ktimes.items()},
                 "gpu_launches": int(sum(c for _, c in ktimes.values())) * args.steps,
                 "generation_s": t_gen, "clocks": clk,
