@@ -72,7 +72,15 @@ struct scl_ctx {
     // graph replay of repeated identical batches
     bool graph_on = false;
     cudaGraphExec_t gexec = nullptr;
-    uint64_t gsig = 0;
+    // the captured batch: its plan (the graph uploads it from this pinned copy, which only a
+    // recapture rewrites, so the host never waits for a running graph to reuse h_plan) and
+    // the buffers and tuning it was captured with
+    void *g_plan = nullptr;
+    size_t g_plan_cap = 0, g_blob = 0;
+    std::vector<const void *> g_ptrs;
+    scl_tuning g_tune{};
+    cudaEvent_t g_done = nullptr;   // recorded after each graph launch (before a recapture)
+    bool g_pending = false;
     // profiling
     bool prof = false;
     std::vector<ProfEntry> prof_pending;
@@ -378,6 +386,39 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     return SCL_OK;
 }
 
+namespace {
+
+// Stream capture records kernels without the priority of the stream they were launched on,
+// so a replayed graph would let the copy-volume pass and the first units' replay compete
+// with the event path on equal terms.  Give every kernel node the priority of its stream:
+// the side stream's kernels the lowest, the others the highest.
+int graph_priorities(scl_ctx *c, cudaGraph_t g) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priority range");
+    const void *side[8];
+    int ns = copy_kernels(side, 7);
+    side[ns++] = first_kernel();
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn), "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn), "graph nodes");
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nd, &t), "graph node type");
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        CK(cudaGraphKernelNodeGetParams(nd, &kp), "kernel node parameters");
+        bool low = false;
+        for (int i = 0; i < ns; ++i) low |= kp.func == side[i];
+        cudaKernelNodeAttrValue v{};
+        v.priority = low ? least : greatest;
+        CK(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v), "kernel node priority");
+    }
+    return SCL_OK;
+}
+
+}  // namespace
+
 // ============================================================================ C ABI
 
 uint32_t scl_ctx_max_traces(const scl_ctx *c) { return c->cfg.max_traces; }
@@ -435,6 +476,8 @@ void scl_replay_free(scl_ctx *c) {
     for (int i = 0; i <= scl_ctx::NCS; ++i)
         if (c->cev[i]) cudaEventDestroy(c->cev[i]);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->g_plan) cudaFreeHost(c->g_plan);
+    if (c->g_done) cudaEventDestroy(c->g_done);
     delete c;
 }
 
@@ -472,6 +515,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(unsigned long long) * NSTATS);
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->g_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         int least = 0, greatest = 0;
@@ -711,35 +755,46 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     c->last_stream = s;
     EnqArgs q{dp, hp, blob, o_units, o_bts, o_grp, o_ct, nbt, nunits, (int)cgroups.size(), (int)ctiles.size()};
     if (c->graph_on && !c->prof && s != nullptr) {
-        // identical plan bytes and buffers -> the captured graph is exactly this batch's work
-        uint64_t sig = 1469598103934665603ull;
-        auto mix = [&](const void *p, size_t n) {
-            const unsigned char *b = static_cast<const unsigned char *>(p);
-            for (size_t i = 0; i < n; ++i) sig = (sig ^ b[i]) * 1099511628211ull;
-        };
-        mix(hp, blob);
-        const void *ptrs[] = {c->plan.p, c->usum.p, c->cand.p, c->lists.p, c->match.p, c->uwalk.p, c->utrue.p, c->umode.p,
-                              c->uexp.p, c->uplan.p, c->uout.p, c->pref.p, c->recs.p, c->btres.p, c->ctsum.p};
-        mix(ptrs, sizeof ptrs);
-        mix(&c->tune, sizeof c->tune);
-        mix(&blob, sizeof blob);
-        if (!c->gexec || sig != c->gsig) {
+        // relaunch when the plan bytes, the buffers and the tuning equal the captured batch's:
+        // the graph is then exactly this batch's work
+        const std::vector<const void *> ptrs = {c->plan.p, c->usum.p, c->cand.p, c->lists.p, c->match.p,
+                                                c->uwalk.p, c->utrue.p, c->umode.p, c->uexp.p, c->uplan.p,
+                                                c->uout.p, c->pref.p, c->recs.p, c->btres.p, c->ctsum.p};
+        const bool same = c->gexec && c->g_blob == blob && c->g_ptrs == ptrs &&
+                          memcmp(&c->g_tune, &c->tune, sizeof c->tune) == 0 && memcmp(c->g_plan, hp, blob) == 0;
+        if (!same) {
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->g_pending) {   // an earlier launch may still be reading g_plan
+                CK(cudaEventSynchronize(c->g_done), "wait for the previous graph");
+                c->g_pending = false;
+            }
+            if (blob > c->g_plan_cap) {
+                if (c->g_plan) cudaFreeHost(c->g_plan);
+                c->g_plan = nullptr;
+                c->g_plan_cap = 0;
+                CK(cudaMallocHost(&c->g_plan, blob), "pinned graph plan");
+                c->g_plan_cap = blob;
+            }
+            memcpy(c->g_plan, hp, blob);
+            EnqArgs qg = q;
+            qg.hp = static_cast<const char *>(c->g_plan);
             CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
-            const int rq = enqueue_batch(c, s, q, false);
+            const int rq = enqueue_batch(c, s, qg, false);
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(s, &g);
             if (rq) { if (g) cudaGraphDestroy(g); return rq; }
             CK(ec, "end capture");
+            if (const int rp = graph_priorities(c, g)) { cudaGraphDestroy(g); return rp; }
             const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
             cudaGraphDestroy(g);
             CK(ei, "instantiate graph");
-            c->gsig = sig;
+            c->g_blob = blob;
+            c->g_ptrs = ptrs;
+            c->g_tune = c->tune;
         }
         CK(cudaGraphLaunch(c->gexec, s), "graph launch");
-        // the graph reads the plan buffer in its first node: it may be rewritten once the graph is done
-        CK(cudaEventRecord(c->plan_done, s), "plan event");
-        c->plan_pending = true;
+        CK(cudaEventRecord(c->g_done, s), "graph event");
+        c->g_pending = true;
     } else {
         const int rq = enqueue_batch(c, s, q, true);
         if (rq) return rq;

@@ -107,6 +107,12 @@ cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_state(const LaunchPost &a, cudaStream_t s);
 
+// kernels that run on the lower-priority side stream (the first units' exact replay and
+// the copy-volume pass): a captured graph gives its kernel nodes the priorities of the
+// streams they were captured from by matching these
+const void *first_kernel();
+int copy_kernels(const void **out, int cap);
+
 cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
                          int64_t F0, uint64_t phase, cudaStream_t s);
 cudaError_t launch_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines, uint32_t rule, void *out,

@@ -795,6 +795,14 @@ cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+int copy_kernels(const void **out, int cap) {
+    const void *k[] = {reinterpret_cast<const void *>(k_copy_sum), reinterpret_cast<const void *>(k_copy_scan),
+                       reinterpret_cast<const void *>(k_copy_apply)};
+    const int n = (int)(sizeof k / sizeof k[0]);
+    for (int i = 0; i < n && i < cap; ++i) out[i] = k[i];
+    return n;
+}
+
 cudaError_t launch_state(const LaunchPost &a, cudaStream_t s) {
     if (!a.nbt) return cudaSuccess;
     k_state<<<(a.nbt + 127) / 128, 128, 0, s>>>(a);

@@ -744,6 +744,8 @@ cudaError_t launch_first(const LaunchSketch &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+const void *first_kernel() { return reinterpret_cast<const void *>(k_first); }
+
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s) {
     const int threads = a.nunits * K;
     k_match<<<(threads + 255) / 256, 256, 0, s>>>(a.units, a.nunits, a.cand, a.match);
