@@ -238,6 +238,9 @@ typedef struct {
     uint32_t warps_per_block;/* sketch warps per thread block (1..16) */
     uint32_t ext_events;     /* warm-up events each unit's candidates run before the unit (multiple of 256; 0 = 32768) */
     uint32_t final_warps;    /* exact-replay warps per thread block (1..14) */
+    uint32_t first_events;   /* length of each trace's first unit, replayed exactly in one pass from the
+                                trace's resident state (multiple of 1024; 0 = unit_events); with fewer
+                                traces than SMs a first unit is one warm-up long instead */
 } scl_tuning;
 int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);

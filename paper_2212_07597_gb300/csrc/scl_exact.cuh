@@ -9,12 +9,12 @@
 // 256 events per step.  delta, the python flag and the address are staged through the
 // copy ring; the line id of a sample is left to k_compact (which reads it for every
 // record in parallel, instead of this warp waiting on one load per sample).  When
-// the unit's resets are known in advance (a reset list from k_sketch) no crossing
+// the unit's resets are known in advance (a reset list from the sketch) no crossing
 // search runs; otherwise each step's prefix sums locate the crossings.
 //
-// Used by k_final for every unit whose entry k_chain resolved, and by k_first for the
+// Used by k_final for every unit whose entry k_chain resolved, and by k_phase1 for the
 // first unit of each trace in a batch, whose entry is the trace's resident state; that
-// caller also wants the facts k_sketch records for a candidate run (FIRST = true).
+// caller also wants the facts the sketch records for a candidate run (FIRST = true).
 #pragma once
 #include "scl_stage.cuh"
 
@@ -32,7 +32,7 @@ struct ExactIn {                 // the state entering the unit
     int64_t exit_c;              // counter after the unit (with a list)
 };
 
-struct ExactRun {                // FIRST only: the run's facts, as k_sketch records them for a candidate
+struct ExactRun {                // FIRST only: the run's facts, as the sketch records them for a candidate
     Cand *C0;                    // lane 0 writes the first RM reset positions and growth
                                  // prefixes here (the unit's candidate 0)
     int64_t gmax, tmax;          // largest prefix at a growth reset (all / index >= RM)
@@ -44,12 +44,20 @@ struct ExactRun {                // FIRST only: the run's facts, as k_sketch rec
 
 // Replays unit U; writes its records to out[0 .. cap) and returns false if a wait timed
 // out.  n (records taken), enter_hit and the state after the unit are returned.
+//
+// The open window's totals are kept warp-uniform.  A step whose deltas all lie in
+// [-2^22, 2^22) has lane sums and a warp sum below 2^30 in magnitude, so its share of a
+// window is formed in 32 bits and summed over the warp with one redux.sync per total; any
+// other step uses 64-bit lane sums and a shuffle reduction.  The frees of the step that
+// hit the tracked block are found once per step (a bit per event), and re-found only when
+// a sample starts tracking another block.
 template <bool FIRST, class RingT>
 __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const ExactIn &in0, FRec *out, uint32_t cap,
                            int64_t T, unsigned long long spin, ErrWord *err, int lane, uint32_t &n_out,
                            UnitOut &O, ExactRun *R) {
     constexpr int E = RingT::kE, STEP = 32 * E;
-    int64_t accA = in0.wA, accApy = in0.wApy, accSpy = in0.wSpy;
+    static_assert(E == 8, "a lane's events fit one byte of bits");
+    int64_t accA = warp_sum(in0.wA), accApy = warp_sum(in0.wApy), accSpy = warp_sum(in0.wSpy);
     int64_t c = in0.c;
     int64_t P = 0;
     int64_t mark = in0.mark;
@@ -71,74 +79,59 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
             enter_hit = 1;
         }
     };
-    auto add_events = [&](const StepIn<E> &in, int after, int upto, int64_t &sA, int64_t &sApy, int64_t &sSpy) {
+    // this lane's events at step positions (after, upto], as a bit mask over its E events
+    auto range = [&](int after, int upto) -> uint32_t {
+        const int lo = after + 1 - lane * E, hi = upto - lane * E;   // event offsets k in [lo, hi]
+        if (hi < 0 || lo > E - 1) return 0u;
+        const uint32_t up = hi >= E - 1 ? 0xffu : (2u << hi) - 1u;
+        const uint32_t dn = lo <= 0 ? 0u : (1u << lo) - 1u;
+        return up & ~dn;
+    };
+    // bit k: event k of this lane is a free of the tracked block
+    auto free_bits = [&](const StepIn<E> &in) -> uint32_t {
+        uint32_t b = 0;
+        if (tk) {
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int pos = lane * E + k;
-            if (pos > after && pos <= upto) {
-                const int64_t x = in.d[k];
+            for (int k = 0; k < E; ++k) b |= (in.d[k] < 0 && in.a[k] == taddr) ? 1u << k : 0u;
+        }
+        return b;
+    };
+    // add the warp's events at step positions (after, upto] to the window totals
+    auto fold = [&](const StepIn<E> &in, bool fits, uint32_t m) {
+        if (fits) {
+            int32_t sA = 0, sApy = 0, sSpy = 0;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int32_t x = (m >> k) & 1u ? (int32_t)in.d[k] : 0;
+                const int32_t ps = max(x, 0);
+                const int32_t py = (int32_t)min(py_of(in, k), 1u);
+                sA += ps;
+                sApy += ps * py;
+                sSpy += x * py;
+            }
+            accA += __reduce_add_sync(FULL, sA);
+            accApy += __reduce_add_sync(FULL, sApy);
+            accSpy += __reduce_add_sync(FULL, sSpy);
+        } else {
+            int64_t sA = 0, sApy = 0, sSpy = 0;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                const int64_t x = (m >> k) & 1u ? in.d[k] : 0;
                 const int64_t ps = x > 0 ? x : 0;
                 sA += ps;
                 if (py_of(in, k)) { sApy += ps; sSpy += x; }
             }
+            accA += warp_sum(sA);
+            accApy += warp_sum(sApy);
+            accSpy += warp_sum(sSpy);
         }
     };
-    auto frees_hit = [&](const StepIn<E> &in, int after, int upto) -> bool {
-        bool h = false;
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int pos = lane * E + k;
-            h |= pos > after && pos <= upto && in.d[k] < 0 && in.a[k] == taddr;
-        }
-        return __any_sync(FULL, h);
-    };
-    // every event of the step joins the open window (no sample in it).  When the step's
-    // deltas lie in [-2^27, 2^27) a lane's sums over its 8 events fit in int32: they are
-    // formed in 32 bits and added to the 64-bit totals once, and the frees are screened on
-    // the low address word (a match is confirmed on the full address).
-    auto whole_step = [&](const StepIn<E> &in) {
-        if (__all_sync(FULL, deltas_within<27>(in))) {
-            int32_t sA = 0, sApy = 0, sSpy = 0;
-            const uint32_t tlo = (uint32_t)taddr;
-            bool hl = false;
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const int32_t x = (int32_t)in.d[k];
-                const int32_t ps = max(x, 0);
-                const int32_t p = (int32_t)min(py_of(in, k), 1u);
-                sA += ps;
-                sApy += ps * p;
-                sSpy += x * p;
-                hl |= x < 0 && (uint32_t)in.a[k] == tlo;
-            }
-            accA += sA;
-            accApy += sApy;
-            accSpy += sSpy;
-            if (tk && __any_sync(FULL, hl)) {
-                bool h = false;
-#pragma unroll
-                for (int k = 0; k < E; ++k) h |= in.d[k] < 0 && in.a[k] == taddr;
-                if (__any_sync(FULL, h)) hit_tracked();
-            }
-            return;
-        }
-        bool h = false;
-#pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const int64_t x = in.d[k];
-            h |= x < 0 && in.a[k] == taddr;
-            const int64_t ps = x > 0 ? x : 0;
-            accA += ps;
-            if (py_of(in, k)) { accApy += ps; accSpy += x; }
-        }
-        if (tk && __any_sync(FULL, h)) hit_tracked();
-    };
-    // the sample at step position r (frees up to it already tested): counter cr there,
-    // unit-local prefix Pr there
-    auto close = [&](const StepIn<E> &in, int after, int r, uint32_t rel0, int64_t cr, int64_t Pr) {
-        int64_t sA = accA, sApy = accApy, sSpy = accSpy;
-        add_events(in, after, r, sA, sApy, sSpy);
-        const int64_t wA = warp_sum(sA), wApy = warp_sum(sApy), wSpy = warp_sum(sSpy);
+    // the sample at step position r, closing the window after the events at (after, r] join
+    // it (frees up to it already tested): counter cr there, unit-local prefix Pr there.
+    // Returns true if the sample started tracking its block.
+    auto close = [&](const StepIn<E> &in, bool fits, int after, int r, uint32_t rel0, int64_t cr,
+                     int64_t Pr) -> bool {
+        fold(in, fits, range(after, r));
         const int fl = r / E, kf = r % E;
         uint64_t av = in.a[0];
         uint32_t pyv = py_of(in, 0);
@@ -160,7 +153,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
             Rr.recl = 0;
             Rr.py = pyv ? 1 : 0;
             Rr.pad = 0;
-            Rr.A = wA; Rr.F = wA - cr; Rr.A_py = wApy; Rr.F_py = wApy - wSpy; Rr.P = Pr;
+            Rr.A = accA; Rr.F = accA - cr; Rr.A_py = accApy; Rr.F_py = accApy - accSpy; Rr.P = Pr;
             out[n] = Rr;
         }
         if (FIRST) {
@@ -172,6 +165,12 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         if (hwm) { mark = fp; tk = 3; taddr = av; tslot = n; }
         ++n;
         accA = accApy = accSpy = 0;
+        return hwm;
+    };
+    // every event of the step joins the open window (no sample in it)
+    auto whole_step = [&](const StepIn<E> &in, bool fits) {
+        fold(in, fits, 0xffu);
+        if (tk && __any_sync(FULL, free_bits(in) != 0)) hit_tracked();
     };
 
     bool ok;
@@ -195,10 +194,12 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         if (!nres) npos = 0xffffffffu;
         int64_t cst = c, Pprev = 0;   // counter at the open window's start, prefix there
         auto kstep = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+            const bool fits = __all_sync(FULL, step_fits32(in));
             if (npos >= rel0 + (uint32_t)STEP) {
-                whole_step(in);
+                whole_step(in, fits);
                 return false;
             }
+            uint32_t fb = free_bits(in);
             int after = -1;
             while (npos < rel0 + (uint32_t)STEP) {
                 if (npos < rel0 + (uint32_t)(after + 1)) {   // positions must increase
@@ -207,8 +208,8 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                     break;
                 }
                 const int r = (int)(npos - rel0);
-                if (tk && frees_hit(in, after, r)) hit_tracked();
-                close(in, after, r, rel0, cst + (nP - Pprev), nP);
+                if (tk && __any_sync(FULL, (fb & range(after, r)) != 0)) hit_tracked();
+                if (close(in, fits, after, r, rel0, cst + (nP - Pprev), nP)) fb = free_bits(in);
                 cst = 0;
                 Pprev = nP;
                 after = r;
@@ -224,8 +225,8 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                     npos = 0xffffffffu;
                 }
             }
-            if (tk && frees_hit(in, after, STEP)) hit_tracked();
-            add_events(in, after, STEP, accA, accApy, accSpy);
+            if (tk && __any_sync(FULL, (fb & range(after, STEP - 1)) != 0)) hit_tracked();
+            fold(in, fits, range(after, STEP - 1));
             return false;
         };
         ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, kstep);
@@ -235,7 +236,8 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         // step when T and the step's deltas allow it: the same arithmetic without overflow)
         const bool t32 = T <= FIT32_T;
         auto step = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
-            if (t32 && __all_sync(FULL, step_fits32(in))) {
+            const bool fits = __all_sync(FULL, step_fits32(in));
+            if (t32 && fits) {
                 StepPrefix32<E> sp;
                 int32_t *xq32 = reinterpret_cast<int32_t *>(sm.xq);
                 step_prefix32(in, lane, sp, xq32);
@@ -246,22 +248,23 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                 const int32_t T32 = (int32_t)T;
                 int32_t b = (int32_t)c;
                 if (__ballot_sync(FULL, b + sp.lmax >= T32 || b + sp.lmin <= -T32) == 0) {
-                    whole_step(in);
+                    whole_step(in, true);
                     c += sp.tot;
                     P += sp.tot;
                     return false;
                 }
+                uint32_t fb = free_bits(in);
                 int after = -1;
                 while (true) {
                     int32_t Qr;
                     const int r = first_cross(sp, (const int32_t *)xq32, lane, b, T32, after, Qr);
-                    if (tk && frees_hit(in, after, r < 0 ? STEP : r)) hit_tracked();
+                    if (tk && __any_sync(FULL, (fb & range(after, r < 0 ? STEP - 1 : r)) != 0)) hit_tracked();
                     if (r < 0) break;
-                    close(in, after, r, rel0, (int64_t)(b + Qr), P + Qr);
+                    if (close(in, true, after, r, rel0, (int64_t)(b + Qr), P + Qr)) fb = free_bits(in);
                     b = -Qr;
                     after = r;
                 }
-                add_events(in, after, STEP, accA, accApy, accSpy);
+                fold(in, true, range(after, STEP - 1));
                 c = b + sp.tot;
                 P += sp.tot;
                 return false;
@@ -273,34 +276,34 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                 umin = P + sp.lmin < umin ? P + sp.lmin : umin;
             }
             if (__ballot_sync(FULL, c + sp.lmax >= T || c + sp.lmin <= -T) == 0) {
-                whole_step(in);
+                whole_step(in, fits);
                 c += sp.tot;
                 P += sp.tot;
                 return false;
             }
+            uint32_t fb = free_bits(in);
             int64_t b = c;
             int after = -1;
             while (true) {
                 int64_t Qr;
                 const int r = first_cross(sp, sm.xq, lane, b, T, after, Qr);
                 // frees up to and including the sample's event see the block tracked so far
-                if (tk && frees_hit(in, after, r < 0 ? STEP : r)) hit_tracked();
+                if (tk && __any_sync(FULL, (fb & range(after, r < 0 ? STEP - 1 : r)) != 0)) hit_tracked();
                 if (r < 0) break;
-                close(in, after, r, rel0, b + Qr, P + Qr);
+                if (close(in, fits, after, r, rel0, b + Qr, P + Qr)) fb = free_bits(in);
                 b = -Qr;
                 after = r;
             }
-            add_events(in, after, STEP, accA, accApy, accSpy);
+            fold(in, fits, range(after, STEP - 1));
             c = b + sp.tot;
             P += sp.tot;
             return false;
         };
         ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, step);
     }
-    const int64_t a = warp_sum(accA), ap = warp_sum(accApy), spy = warp_sum(accSpy);
     O.count = n;
     O.enter_hit = enter_hit;
-    O.c = c; O.A = a; O.F = a - c; O.Apy = ap; O.Fpy = ap - spy;
+    O.c = c; O.A = accA; O.F = accA - c; O.Apy = accApy; O.Fpy = accApy - accSpy;
     n_out = n;
     if (FIRST) {
         R->gmax = gmax; R->garg = garg; R->tmax = tmax; R->targ = targ; R->last = last; R->P = P;

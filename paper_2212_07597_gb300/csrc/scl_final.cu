@@ -2,7 +2,7 @@
 //
 // One warp per unit (scl_exact.cuh).  The entering counter, window totals, footprint,
 // mark and tracked block come from k_chain / k_scan, so no speculation is left here.
-// The first unit of each trace in the batch was already replayed by k_first (its
+// The first unit of each trace in the batch was already replayed by k_phase1 (its
 // entering state is the trace's resident state) and is skipped.
 #include "scl_exact.cuh"
 #include "scl_launch.h"
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ unit
         u = __shfl_sync(FULL, u, 0);
         if (u >= nunits) break;
         const Unit U = units[u];
-        if (U.first) continue;   // replayed by k_first
+        if (U.first) continue;   // replayed by k_phase1
         const UnitTrue Tu = utrue[u];
         const UnitPlan Pl = uplan[u];
         ExactIn in0;

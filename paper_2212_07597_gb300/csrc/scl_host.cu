@@ -57,11 +57,9 @@ struct scl_ctx {
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
     bool plan_pending = false;
-    // the copy-volume pass (Section 3.5) shares nothing with the event path: it runs on a
-    // side stream (after the first units' exact replay) between a fork at the start of the
-    // call and a join before the state fold
-    cudaStream_t side = nullptr, hi = nullptr;
-    cudaEvent_t ev_join = nullptr, ev_in = nullptr, ev_out = nullptr, ev_first = nullptr;
+    // the replay's kernels run on a high-priority stream forked from the caller's
+    cudaStream_t hi = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // host-to-device staging of scl_replay_batch_host: pieces spread over several copy
     // streams (several copy engines at once), joined back before the replay
     static constexpr int NCS = 4;
@@ -208,7 +206,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 struct EnqArgs {
     char *dp;
     const char *hp;
-    size_t blob, o_units, o_bts, o_grp, o_ct;
+    size_t blob, o_units, o_bts, o_grp, o_ct, o_ord;
     uint32_t nbt;
     int nunits, ngroups, nctiles;
 };
@@ -228,13 +226,13 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     CK(cudaMemsetAsync(c->btres.p, 0, sizeof(BTraceRes) * q.nbt, s), "memset");
     CK(cudaMemsetAsync(c->queue, 0, sizeof(unsigned) * 4, s), "memset");
     CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * NSTATS, s), "memset");
-    // the kernels of the event path run on a high-priority stream forked from the caller's,
-    // so the copy-volume pass on the side stream takes only what they leave of the SMs
+    if (q.nctiles) CK(cudaMemsetAsync(c->ctsum.p, 0, copy_status_bytes(q.nctiles), s), "memset");
+    // the kernels run on a high-priority stream forked from the caller's (other work on the
+    // device yields SMs to the replay) and joined back at the end
     cudaStream_t s_user = s;
     CK(cudaEventRecord(c->ev_in, s_user), "fork event");
     s = c->hi;
-    CK(cudaStreamWaitEvent(s, c->ev_in, 0), "fork the event path");
-    CK(cudaStreamWaitEvent(c->side, c->ev_in, 0), "fork the side stream");
+    CK(cudaStreamWaitEvent(s, c->ev_in, 0), "fork the replay");
 
     const Unit *d_units = reinterpret_cast<const Unit *>(dp + q.o_units);
     const BTrace *d_bts = reinterpret_cast<const BTrace *>(dp + q.o_bts);
@@ -262,11 +260,8 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
     a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
     a.ngroups = q.ngroups;
-    a.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
-    a.nctiles = q.nctiles;
-    a.ctile_sum = static_cast<uint64_t *>(c->ctsum.p);
     a.err = c->errw;
-    if (nunits) {
+    if (nunits || q.nctiles) {
         LaunchSketch k;
         k.units = d_units;
         k.nunits = nunits;
@@ -290,53 +285,40 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         k.spin = cfg.spin_limit;
         k.stats = c->stats;
         k.num_sms = c->num_sms;
+        k.order = reinterpret_cast<const uint32_t *>(dp + q.o_ord);
+        k.nitems = nunits;
+        k.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
+        k.nctiles = q.nctiles;
+        k.cstatus = c->ctsum.p;
+        k.btres = static_cast<BTraceRes *>(c->btres.p);
+        k.lines = c->lines;
+        k.n_lines = cfg.n_lines;
+        k.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
         // spread the units over all SMs: fewer warps per block when units are few
-        k.warps_per_block = std::max(1, std::min(std::min((int)c->tune.warps_per_block, SKETCH_MAX_WARPS),
-                                                 (nunits + c->num_sms - 1) / c->num_sms));
+        const int items = nunits + q.nctiles;
+        k.warps_per_block = std::max(1, std::min(std::min((int)c->tune.warps_per_block, PHASE1_MAX_WARPS),
+                                                 (items + c->num_sms - 1) / c->num_sms));
         int bps = 0;
-        if (sketch_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
-        k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
-        // the first unit of each trace (whose entry is known) is replayed exactly on the side
-        // stream, beside the sketch of the other units
+        if (phase1_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
+        k.blocks = std::max(1, std::min(bps * c->num_sms, (items + k.warps_per_block - 1) / k.warps_per_block));
         {
-            Prof p(c, c->side, "first");
-            CK(launch_first(k, c->side), "launch first");
+            // the traces' first units replayed exactly and the other units sketched, from one queue
+            Prof p(c, s, "phase1");
+            CK(launch_phase1(k, s), "launch phase 1");
         }
-        CK(cudaEventRecord(c->ev_first, c->side), "first-unit event");
-        {
-            Prof p(c, s, "sketch");
-            CK(launch_sketch(k, s), "launch sketch");
-        }
-        CK(cudaStreamWaitEvent(s, c->ev_first, 0), "join the first units");
-        {
-            Prof p(c, s, "match");
-            CK(launch_match(k, s), "launch match");
-        }
-        {
-            Prof p(c, s, "chain");
-            CK(launch_chain(k, s), "launch chain");
-        }
-        {
+        if (nunits) {
+            {
+                Prof p(c, s, "match");
+                CK(launch_match(k, s), "launch match");
+            }
+            {
+                Prof p(c, s, "chain");
+                CK(launch_chain(k, s), "launch chain");
+            }
             Prof p(c, s, "totals");
             CK(launch_totals(k, s), "launch totals");
         }
     }
-    // ---- the copy-volume pass, on the side stream after the first units: it shares nothing
-    // with the event path, and its blocks (which cannot sit beside a sketch block) take the
-    // SMs that the sketch's last units leave idle
-    {
-        Prof p(c, c->side, "copy_sum");
-        CK(launch_copy_sum(a, c->side), "launch copy sum");
-    }
-    {
-        Prof p(c, c->side, "copy_scan");
-        CK(launch_copy_scan(a, c->side), "launch copy scan");
-    }
-    {
-        Prof p(c, c->side, "copy_apply");
-        CK(launch_copy_apply(a, c->side), "launch copy apply");
-    }
-    CK(cudaEventRecord(c->ev_join, c->side), "join event");
     {
         Prof p(c, s, "scan");
         CK(launch_scan(a, s), "launch scan");
@@ -376,28 +358,23 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         Prof p(c, s, "epi");
         CK(launch_epi(a, s), "launch epi");
     }
-    CK(cudaStreamWaitEvent(s, c->ev_join, 0), "join the copy pass");
     {
         Prof p(c, s, "state");
         CK(launch_state(a, s), "launch state");
     }
     CK(cudaEventRecord(c->ev_out, s), "join event");
-    CK(cudaStreamWaitEvent(s_user, c->ev_out, 0), "join the event path");
+    CK(cudaStreamWaitEvent(s_user, c->ev_out, 0), "join the replay");
     return SCL_OK;
 }
 
 namespace {
 
-// Stream capture records kernels without the priority of the stream they were launched on,
-// so a replayed graph would let the copy-volume pass and the first units' replay compete
-// with the event path on equal terms.  Give every kernel node the priority of its stream:
-// the side stream's kernels the lowest, the others the highest.
+// Stream capture records kernels without the priority of the stream they were launched on:
+// give every kernel node the high priority of the replay stream, as plain launches have.
 int graph_priorities(scl_ctx *c, cudaGraph_t g) {
     int least = 0, greatest = 0;
     CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priority range");
-    const void *side[8];
-    int ns = copy_kernels(side, 7);
-    side[ns++] = first_kernel();
+    (void)least;
     size_t nn = 0;
     CK(cudaGraphGetNodes(g, nullptr, &nn), "graph nodes");
     std::vector<cudaGraphNode_t> nodes(nn);
@@ -406,12 +383,8 @@ int graph_priorities(scl_ctx *c, cudaGraph_t g) {
         cudaGraphNodeType t;
         CK(cudaGraphNodeGetType(nd, &t), "graph node type");
         if (t != cudaGraphNodeTypeKernel) continue;
-        cudaKernelNodeParams kp{};
-        CK(cudaGraphKernelNodeGetParams(nd, &kp), "kernel node parameters");
-        bool low = false;
-        for (int i = 0; i < ns; ++i) low |= kp.func == side[i];
         cudaKernelNodeAttrValue v{};
-        v.priority = low ? least : greatest;
+        v.priority = greatest;
         CK(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v), "kernel node priority");
     }
     return SCL_OK;
@@ -465,9 +438,6 @@ void scl_replay_free(scl_ctx *c) {
     cudaFree(c->stats);
     if (c->h_plan) cudaFreeHost(c->h_plan);
     if (c->plan_done) cudaEventDestroy(c->plan_done);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->ev_first) cudaEventDestroy(c->ev_first);
-    if (c->side) cudaStreamDestroy(c->side);
     if (c->hi) cudaStreamDestroy(c->hi);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -516,7 +486,6 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     if (e == cudaSuccess) e = cudaMemset(c->errw, 0, sizeof(ErrWord));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->plan_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->g_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         int least = 0, greatest = 0;
         e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
@@ -524,8 +493,6 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming);
     for (int i = 0; i < scl_ctx::NCS && e == cudaSuccess; ++i)
         e = cudaStreamCreateWithFlags(&c->cstream[i], cudaStreamNonBlocking);
     for (int i = 0; i <= scl_ctx::NCS && e == cudaSuccess; ++i)
@@ -547,7 +514,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     }
     c->h_events.assign(NTr, 0);
     c->tune.unit_events = cfg.unit_events;   // 0: sized per batch
-    c->tune.warps_per_block = SKETCH_MAX_WARPS;
+    c->tune.warps_per_block = PHASE1_MAX_WARPS;
     c->tune.ext_events = 0;
     c->tune.final_warps = 14;
     *out = c;
@@ -562,10 +529,10 @@ int scl_tuning_get(const scl_ctx *c, scl_tuning *out) {
 
 int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
     if (!c || !t) return SCL_EINVAL;
-    if (t->unit_events % UNIT_ALIGN || t->warps_per_block < 1 || t->warps_per_block > 16 ||
-        t->final_warps < 1 || t->final_warps > 14 || (t->ext_events % 256))
-        return fail(c, SCL_EINVAL, "tuning: unit_events multiple of 1024 (0: per batch), warps_per_block 1..16, final_warps 1..14, "
-                                   "ext_events multiple of %d", 256);
+    if (t->unit_events % UNIT_ALIGN || t->first_events % UNIT_ALIGN || t->warps_per_block < 1 ||
+        t->warps_per_block > 16 || t->final_warps < 1 || t->final_warps > 14 || (t->ext_events % 256))
+        return fail(c, SCL_EINVAL, "tuning: unit_events and first_events multiples of 1024 (0: default), "
+                                   "warps_per_block 1..16, final_warps 1..14, ext_events multiple of %d", 256);
     c->tune = *t;
     return SCL_OK;
 }
@@ -638,7 +605,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         B.u0 = (uint32_t)units.size();
         B.c0 = (uint32_t)ctiles.size();
         uint64_t gidx = c->h_events[B.trace];
-        // The trace's first unit is replayed exactly by one warp (k_first) beside the sketch
+        // The trace's first unit is replayed exactly by one warp (k_phase1) beside the sketch
         // of the others.  With fewer traces than SMs those warps run nearly alone, so when
         // more units follow the first one is kept to one warm-up's length and its warp is
         // done well before the sketch; with many traces the first units keep full length
@@ -646,7 +613,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         const uint64_t W = c->tune.ext_events ? c->tune.ext_events : 32768;
         const uint64_t first_len = nbt < (uint32_t)c->num_sms && tev[b] > UE
                                        ? std::min<uint64_t>(UE, std::max<uint64_t>(32768, (W + UNIT_ALIGN - 1) / UNIT_ALIGN * UNIT_ALIGN))
-                                       : UE;
+                                       : (c->tune.first_events ? c->tune.first_events : UE);
         for (uint32_t i : groups[b]) {
             const scl_segment &g = segs[i];
             for (uint64_t off = 0, len; off < g.ev.n; off += len) {
@@ -672,9 +639,9 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 rec_total += U.rec_cap;
                 lst_total += (uint64_t)NL * U.lst_cap;
             }
-            for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
+            for (uint64_t off = 0; off < g.cp.n; off += COPY_WTILE) {
                 CopyTile T;
-                T.len = (uint32_t)std::min<uint64_t>(COPY_TILE, g.cp.n - off);
+                T.len = (uint32_t)std::min<uint64_t>(COPY_WTILE, g.cp.n - off);
                 T.size = g.cp.size + off;
                 T.line = g.cp.line + off;
                 T.py = g.cp.is_python + off;
@@ -695,12 +662,36 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     const int nunits = (int)units.size();
     const size_t nu1 = std::max<size_t>(1, units.size());
 
-    // ---- plan blob: units | bts | groups | copy tiles
+    // ---- phase-1 order: longest work first (a first unit's exact replay costs about twice
+    // a sketched unit's events; a sketched unit also streams its warm-up)
+    std::vector<uint32_t> p1order(units.size());
+    {
+        const uint64_t W = c->tune.ext_events ? c->tune.ext_events : 32768;
+        std::vector<uint64_t> cost(units.size());
+        for (size_t u = 0; u < units.size(); ++u)
+            cost[u] = units[u].first ? 2 * units[u].len : units[u].len + std::min<uint64_t>(W, units[u - 1].len);
+        for (size_t u = 0; u < units.size(); ++u) p1order[u] = (uint32_t)u;
+        std::stable_sort(p1order.begin(), p1order.end(), [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+    }
+    // ---- copy tiles in rounds over the traces (every trace's first tile, then every second
+    // tile, ...): a trace's tiles stay in order for the look-back, a predecessor was taken
+    // long before, and the warps at work spread their counter updates over many traces
+    std::vector<uint32_t> corder;
+    corder.reserve(ctiles.size());
+    {
+        uint32_t maxnc = 0;
+        for (const BTrace &B : bts) maxnc = std::max(maxnc, B.nc);
+        for (uint32_t r = 0; r < maxnc; ++r)
+            for (const BTrace &B : bts)
+                if (r < B.nc) corder.push_back(B.c0 + r);
+    }
+    // ---- plan blob: units | bts | groups | copy tiles | phase-1 order (units, then copy tiles)
     const size_t o_units = 0;
     const size_t o_bts = al256(o_units + sizeof(Unit) * units.size());
     const size_t o_grp = al256(o_bts + sizeof(BTrace) * bts.size());
     const size_t o_ct = al256(o_grp + sizeof(CompactGroup) * cgroups.size());
-    const size_t blob = al256(o_ct + sizeof(CopyTile) * ctiles.size());
+    const size_t o_ord = al256(o_ct + sizeof(CopyTile) * ctiles.size());
+    const size_t blob = al256(o_ord + sizeof(uint32_t) * (p1order.size() + corder.size()));
     if (c->plan_pending) {
         CK(cudaEventSynchronize(c->plan_done), "wait for previous plan upload");
         c->plan_pending = false;
@@ -717,6 +708,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     memcpy(hp + o_bts, bts.data(), sizeof(BTrace) * bts.size());
     memcpy(hp + o_grp, cgroups.data(), sizeof(CompactGroup) * cgroups.size());
     memcpy(hp + o_ct, ctiles.data(), sizeof(CopyTile) * ctiles.size());
+    memcpy(hp + o_ord, p1order.data(), sizeof(uint32_t) * p1order.size());
+    memcpy(hp + o_ord + sizeof(uint32_t) * p1order.size(), corder.data(), sizeof(uint32_t) * corder.size());
 
     int r;
     if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;
@@ -733,13 +726,13 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     if ((r = ensure(c, c->pref, sizeof(int64_t) * 3 * nu1, s, "window prefixes"))) return r;
     if ((r = ensure(c, c->recs, sizeof(FRec) * std::max<uint64_t>(1, rec_total), s, "sample records"))) return r;
     if ((r = ensure(c, c->btres, sizeof(BTraceRes) * nbt, s, "batch trace results"))) return r;
-    if ((r = ensure(c, c->ctsum, sizeof(uint64_t) * std::max<size_t>(1, ctiles.size()), s, "copy tile sums")))
+    if ((r = ensure(c, c->ctsum, copy_status_bytes(std::max<size_t>(1, ctiles.size())), s, "copy tile states")))
         return r;
 
     char *dp = static_cast<char *>(c->plan.p);
     c->last_units = units.size();
     {
-        // events through k_first (first units) and k_sketch (other units, each with the
+        // events through the exact replay of first units and the sketch (other units, each with the
         // warm-up over the tail of the unit before it, from a tile boundary)
         const uint64_t W = c->tune.ext_events ? c->tune.ext_events : 32768;
         uint64_t fe = 0, se = 0;
@@ -753,7 +746,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         c->last_sketch_events = se;
     }
     c->last_stream = s;
-    EnqArgs q{dp, hp, blob, o_units, o_bts, o_grp, o_ct, nbt, nunits, (int)cgroups.size(), (int)ctiles.size()};
+    EnqArgs q{dp, hp, blob, o_units, o_bts, o_grp, o_ct, o_ord, nbt, nunits, (int)cgroups.size(), (int)ctiles.size()};
     if (c->graph_on && !c->prof && s != nullptr) {
         // relaunch when the plan bytes, the buffers and the tuning equal the captured batch's:
         // the graph is then exactly this batch's work
@@ -1216,7 +1209,7 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     int rc = copy_state(true) == cudaSuccess ? SCL_OK : SCL_ECUDA;
     const uint32_t units[] = {0, 65536, 131072, 262144};
     const uint32_t fwarps[] = {10, 14};
-    const uint32_t swarps[] = {8, (uint32_t)SKETCH_MAX_WARPS};
+    const uint32_t swarps[] = {8, (uint32_t)PHASE1_MAX_WARPS};
     const uint32_t warm[] = {16384, 32768};
     for (uint32_t ue : units)
         for (uint32_t fw : fwarps)

@@ -19,7 +19,8 @@ constexpr int STEP = 32 * E;       // events per walker step
 constexpr int TILE = 256;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
 constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
-constexpr int COPY_TILE = 4096;    // memcpy events per copy-pass block
+constexpr int COPY_TILE = 4096;    // memcpy events per block of the allocation-free copy sampler
+constexpr int COPY_WTILE = 1024;   // memcpy events per warp tile of the replay's copy sampler
 constexpr int SMEM_LINES_MAX = 1024;  // per-line tables kept in shared memory up to this L
 
 // error codes mirrored from scl.h

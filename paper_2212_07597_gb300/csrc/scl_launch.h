@@ -9,10 +9,8 @@ namespace scl {
 // device counters of a batch: units walked, walked and merged, explicit entries,
 // transparent, events walked (k_chain); units replayed with the crossing search (k_final)
 constexpr int NSTATS = 6;
-constexpr int SKETCH_MAX_WARPS = 16;   // k_sketch warps per block (its launch bound)
-constexpr int SKETCH_MIN_BLOCKS = 1;   // k_sketch blocks of SKETCH_MAX_WARPS resident per SM
-constexpr int FIRST_WARPS = 4;         // k_first warps per block
-constexpr int SKETCH_TILE = 512;       // k_sketch events per staged tile (warm-ups start on one)
+constexpr int PHASE1_MAX_WARPS = 16;   // k_phase1 warps per block (its launch bound)
+constexpr int SKETCH_TILE = 512;       // sketch events per staged tile (warm-ups start on one)
 
 struct LaunchSketch {
     const Unit *units;
@@ -22,7 +20,7 @@ struct LaunchSketch {
     UnitSum *usum;
     Cand *cand;
     SRes *lists;
-    FRec *recs;          // first units: their records and outputs (k_first replays them exactly)
+    FRec *recs;          // first units: their records and outputs (k_phase1 replays them exactly)
     UnitOut *uout;
     uint8_t *match;
     Walk *uwalk;
@@ -32,7 +30,16 @@ struct LaunchSketch {
     const DevTrace *traces;
     int64_t T;
     uint32_t warmup;
-    unsigned *queue;     // [0] sketch, [1] first units, [2] final
+    const uint32_t *order;   // phase-1 work: unit indices, longest work first, then copy tile indices
+    int nitems;              // units (the copy tiles follow them in the queue)
+    const CopyTile *ctiles;  // the copy-volume sampler's warp tiles, trace by trace
+    int nctiles;
+    void *cstatus;           // CopyStatus per tile (look-back), cleared before the batch
+    BTraceRes *btres;
+    LineRow *lines;
+    uint32_t n_lines;
+    uint64_t Tc;
+    unsigned *queue;     // [0] phase 1, [2] final
     ErrWord *err;
     unsigned long long spin;
     unsigned long long *stats;   // NSTATS counters of the batch, see NSTATS
@@ -80,17 +87,14 @@ struct LaunchPost {
     uint64_t Tc;
     const CompactGroup *groups;
     int ngroups;
-    const CopyTile *ctiles;
-    int nctiles;
-    uint64_t *ctile_sum;   // per copy tile: sum, then (after the scan) base counter
     ErrWord *err;
 };
 
 
-int sketch_occupancy(int warps_per_block, int *blocks_per_sm);
+int phase1_occupancy(int warps_per_block, int *blocks_per_sm);
 int final_occupancy(int warps_per_block, int *blocks_per_sm);
-cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s);
-cudaError_t launch_first(const LaunchSketch &a, cudaStream_t s);
+cudaError_t launch_phase1(const LaunchSketch &a, cudaStream_t s);
+size_t copy_status_bytes(size_t ntiles);   // look-back state of the copy-volume tiles
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s);
@@ -102,16 +106,7 @@ cudaError_t launch_scan(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_compact(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_mark(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_epi(const LaunchPost &a, cudaStream_t s);
-cudaError_t launch_copy_sum(const LaunchPost &a, cudaStream_t s);
-cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s);
-cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_state(const LaunchPost &a, cudaStream_t s);
-
-// kernels that run on the lower-priority side stream (the first units' exact replay and
-// the copy-volume pass): a captured graph gives its kernel nodes the priorities of the
-// streams they were captured from by matching these
-const void *first_kernel();
-int copy_kernels(const void **out, int cap);
 
 cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
                          int64_t F0, uint64_t phase, cudaStream_t s);

@@ -9,8 +9,6 @@
 //   k_mark     a block tracked when a unit starts and freed inside it is marked
 //              reclaimed (Section 3.4's pointer comparison spans units).
 //   k_epi      closes each object's trial at the next crossing: frees += reclaimed.
-//   k_copy_*   the copy-volume sampler of Section 3.5: one sample per T_c bytes
-//              copied, counted from the running byte count.
 //   k_state    folds the batch into the trace's resident state.
 #include "scl_internal.cuh"
 #include <algorithm>
@@ -462,101 +460,6 @@ __global__ void k_epi(LaunchPost a) {
     }
 }
 
-// ---------------------------------------------------------------- copy volume (Section 3.5)
-__global__ void __launch_bounds__(NT) k_copy_sum(LaunchPost a) {
-    __shared__ int64_t sh[NT / 32 + 1];
-    const CopyTile C = a.ctiles[blockIdx.x];
-    uint64_t s = 0;
-    int ovf = 0;
-    for (uint32_t j = threadIdx.x; j < C.len; j += NT) {
-        const uint64_t x = C.size[j];
-        ovf |= (s + x < s);
-        s += x;
-    }
-    // sizes of one tile are summed in 64 bits; overflow is reported
-    if (__syncthreads_or(ovf) && threadIdx.x == 0) set_error(a.err, E_OVERFLOW, 7, blockIdx.x);
-    int64_t tot;
-    (void)block_excl_sum((int64_t)s, sh, &tot);
-    if (threadIdx.x == 0) a.ctile_sum[blockIdx.x] = (uint64_t)tot;
-}
-
-__global__ void __launch_bounds__(NT) k_copy_scan(LaunchPost a) {
-    __shared__ int64_t sh[NT / 32 + 1];
-    const BTrace B = a.bts[blockIdx.x];
-    const uint64_t start = a.traces[B.trace].copy_counter;
-    uint64_t carry = 0;
-    for (uint32_t base = 0; base < B.nc; base += NT) {
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < B.nc;
-        int64_t tot;
-        const uint64_t v = valid ? a.ctile_sum[B.c0 + i] : 0;
-        const int64_t ex = block_excl_sum((int64_t)v, sh, &tot);
-        if (valid) a.ctile_sum[B.c0 + i] = start + carry + (uint64_t)ex;
-        carry += (uint64_t)tot;
-    }
-    if (threadIdx.x == 0) a.btres[blockIdx.x].copy_total = carry;
-}
-
-constexpr int CPT = COPY_TILE / NT;   // memcpy events per thread
-
-constexpr uint32_t COPY_HOT_LINES = 1024;   // lines counted in shared memory per tile
-
-// Section 3.5 per tile: the copy counter before the tile (from k_copy_scan) plus the
-// running byte count; a memcpy takes one sample per multiple of T_c its bytes pass.
-// Only the sample counts are kept (copy bytes = samples * T_c, formed by the query).
-// Counts of lines below 1,024 -- with skewed line use, nearly all of them -- gather in
-// shared memory and reach the trace's rows once per tile; higher lines count in global
-// memory directly.  Each thread owns CPT consecutive memcpys (sizes staged through shared
-// memory, padded against bank conflicts) and carries the remainder mod T_c, so a division
-// is needed only once per thread and for a memcpy of at least 8 T_c.
-__global__ void __launch_bounds__(NT) k_copy_apply(LaunchPost a) {
-    extern __shared__ __align__(16) unsigned long long chist[];   // [hot lines][2]: samples, by flag
-    __shared__ unsigned long long ssz[COPY_TILE + COPY_TILE / CPT];
-    __shared__ int64_t sh[NT / 32 + 1];
-    const CopyTile C = a.ctiles[blockIdx.x];
-    const BTrace &B = a.bts[C.bt];
-    const uint32_t hot = a.n_lines < COPY_HOT_LINES ? a.n_lines : COPY_HOT_LINES;
-    for (uint32_t i = threadIdx.x; i < 2 * hot; i += NT) chist[i] = 0;
-    for (uint32_t j = threadIdx.x; j < COPY_TILE; j += NT) ssz[j + j / CPT] = j < C.len ? C.size[j] : 0ull;
-    __syncthreads();
-    const unsigned long long Tc = a.Tc;
-    const uint32_t j0 = threadIdx.x * CPT;
-    const unsigned long long *mine = &ssz[j0 + threadIdx.x];
-    unsigned long long loc = 0;
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) loc += mine[k];
-    int64_t tot;
-    const uint64_t ex = (uint64_t)block_excl_sum((int64_t)loc, sh, &tot);
-    const uint64_t start = a.ctile_sum[blockIdx.x] + ex;   // bytes counted before this thread's first memcpy
-    unsigned long long rem = start % Tc;
-    LineRow *grow = a.lines + (uint64_t)B.trace * a.n_lines;
-    for (int k = 0; k < CPT; ++k) {
-        const uint32_t j = j0 + k;
-        if (j >= C.len) break;
-        const unsigned long long sz = mine[k];
-        unsigned long long q;
-        if (sz / 8 >= Tc) {   // (8 * T_c could overflow for T_c above 2^61)
-            q = (rem + sz) / Tc;
-            rem = (rem + sz) % Tc;
-        } else {
-            rem += sz;
-            q = 0;
-            while (rem >= Tc) { rem -= Tc; ++q; }
-        }
-        if (!q) continue;
-        const uint32_t line = C.line[j];
-        if (line >= a.n_lines) { set_error(a.err, E_RANGE, line, j); continue; }
-        const int f = C.py[j] ? 1 : 0;
-        if (line < hot) atomicAdd(&chist[2 * line + f], q);
-        else atomicAdd(&grow[line].copy_samples[f], q);
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < 2 * hot; i += NT) {
-        const unsigned long long v = chist[i];
-        if (v) atomicAdd(&grow[i >> 1].copy_samples[i & 1], v);
-    }
-}
-
 // ---------------------------------------------------------------- k_state
 __global__ void k_state(LaunchPost a) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -772,35 +675,6 @@ cudaError_t launch_epi(const LaunchPost &a, cudaStream_t s) {
     if (!a.nunits) return cudaSuccess;
     k_epi<<<(a.nunits + 7) / 8, 256, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-cudaError_t launch_copy_sum(const LaunchPost &a, cudaStream_t s) {
-    if (!a.nctiles) return cudaSuccess;
-    k_copy_sum<<<a.nctiles, NT, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_copy_scan(const LaunchPost &a, cudaStream_t s) {
-    if (!a.nctiles) return cudaSuccess;
-    k_copy_scan<<<a.nbt, NT, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_copy_apply(const LaunchPost &a, cudaStream_t s) {
-    if (!a.nctiles) return cudaSuccess;
-    const size_t smem = (size_t)std::min(a.n_lines, COPY_HOT_LINES) * 2 * 8;
-    cudaError_t e = cudaFuncSetAttribute(k_copy_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem ? smem : 1));
-    if (e != cudaSuccess) return e;
-    k_copy_apply<<<a.nctiles, NT, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-int copy_kernels(const void **out, int cap) {
-    const void *k[] = {reinterpret_cast<const void *>(k_copy_sum), reinterpret_cast<const void *>(k_copy_scan),
-                       reinterpret_cast<const void *>(k_copy_apply)};
-    const int n = (int)(sizeof k / sizeof k[0]);
-    for (int i = 0; i < n && i < cap; ++i) out[i] = k[i];
-    return n;
 }
 
 cudaError_t launch_state(const LaunchPost &a, cudaStream_t s) {

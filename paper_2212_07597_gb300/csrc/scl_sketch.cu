@@ -6,18 +6,20 @@
 // each other when one event pushes both over the threshold, which happens quickly
 // for runs whose counters are close and slowly otherwise.
 //
-// k_sketch  one warp per unit.  The 32 lanes start 32 counters spread over (-T, T)
-//           a warm-up stretch before the unit (at the end of the previous unit of
-//           the trace) and run them to the unit's start, where they have collapsed
-//           into a few distinct values that any run through the warm-up has almost
-//           surely joined.  Equal counters are merged (followers copy their leader),
-//           and the distinct ones are run through the unit, recording the counter
-//           at the start and end, the resets, the last reset and the first largest
-//           prefix at a growth reset.  All lanes advance together, 256 events per step.
-// k_first   one warp per trace of the batch, beside k_sketch on another stream: the
-//           trace's first unit, whose entry is the trace's resident state, replayed
-//           exactly once (k_final skips it) and recorded as every candidate of the unit.
-//           (Inside k_sketch its exact replay set that kernel's register count.)
+// k_phase1  one persistent kernel; each warp takes units from one queue, longest work first:
+//           - the first unit of a trace in the batch, whose entry is the trace's resident
+//             state, is replayed exactly once (k_final skips it) and recorded as every
+//             candidate of the unit;
+//           - any other unit is sketched: the 32 lanes start 32 counters spread over
+//             (-T, T) a warm-up stretch before the unit (at the end of the previous unit of
+//             the trace) and run them to the unit's start, where they have collapsed into a
+//             few distinct values that any run through the warm-up has almost surely
+//             joined.  Equal counters are merged (followers copy their leader), and the
+//             distinct ones are run through the unit, recording the counter at the start
+//             and end, the resets, the last reset and the first largest prefix at a growth
+//             reset.  All lanes advance together, 256 events per step.
+//           Sharing one queue lets the latency-bound counters and the bandwidth-bound exact
+//           replays run side by side on every SM.
 // k_match   for each unit and each candidate k of the previous unit: the candidate of
 //           this unit whose start counter equals k's end counter, if any.
 // k_chain   one block per trace: follows the true candidate from unit to unit through
@@ -27,6 +29,7 @@
 #include <algorithm>
 #include <cstddef>
 
+#include "scl_copy.cuh"
 #include "scl_exact.cuh"
 #include "scl_launch.h"
 
@@ -100,192 +103,225 @@ __device__ __forceinline__ unsigned match_counter(int64_t c, bool t32) {
     return t32 ? __match_any_sync(FULL, (unsigned)c) : __match_any_sync(FULL, (unsigned long long)c);
 }
 
-// ---------------------------------------------------------------- k_sketch
+// ---------------------------------------------------------------- phase 1: sketch and first units
 constexpr int SE = 8;                         // events per lane per sketch step (256 per step)
 using SketchRing = Ring<false, 2, 512, SE>;   // two steps per tile: the other tile is in flight
-constexpr size_t SKETCH_WARP_SMEM = sizeof(SketchRing);
+using FirstRing = Ring<true, 2, 256, 8>;
 static_assert(SketchRing::kTL == SKETCH_TILE, "the host counts warm-up events in these tiles");
-static_assert(SKETCH_WARP_SMEM * SKETCH_MAX_WARPS * SKETCH_MIN_BLOCKS <= 227 * 1024,
-              "the resident sketch blocks' rings fit in one SM's shared memory");
 
-__global__ void __launch_bounds__(32 * SKETCH_MAX_WARPS, SKETCH_MIN_BLOCKS) k_sketch(const Unit *__restrict__ units, int nunits, UnitSum *usum,
-                                                    Cand *cand, SRes *lists, FRec *recs, UnitOut *uout,
-                                                    const DevTrace *traces, int64_t T, uint32_t warmup,
-                                                    unsigned *queue, ErrWord *err, unsigned long long spin) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SketchRing &sm = *reinterpret_cast<SketchRing *>(smem_raw + (size_t)warp * SKETCH_WARP_SMEM);
-    ring_init(sm, lane);
+// A warp's shared memory holds one ring at a time: the sketch's (deltas only) or the exact
+// replay's (deltas, addresses, flags).  Switching invalidates the old ring's barriers first.
+union alignas(128) Phase1Smem {
+    SketchRing s;
+    FirstRing f;
+    CopySmem c;
+};
+constexpr size_t PHASE1_WARP_SMEM = sizeof(Phase1Smem);
+static_assert(PHASE1_WARP_SMEM % 128 == 0, "per-warp slices laid end to end stay aligned");
+static_assert(PHASE1_WARP_SMEM * PHASE1_MAX_WARPS <= 227 * 1024, "a block's rings fit one SM's shared memory");
+
+// Candidate counters of unit u (not a trace's first unit): 32 counters spread over (-T, T)
+// run through a warm-up over the tail of the previous unit of the trace, collapse, and the
+// distinct ones run through the unit recording what k_match / k_chain / k_final need.
+// Returns false if a wait timed out.
+__device__ bool sketch_unit(SketchRing &sm, uint32_t &phase, int u, const Unit *__restrict__ units, UnitSum *usum,
+                            Cand *cand, SRes *lists, int64_t T, uint32_t warmup, ErrWord *err,
+                            unsigned long long spin, int lane) {
     const bool t32 = T <= FIT32_T;
-    uint32_t phase = 0;
-    while (true) {
-        int u = 0;
-        if (lane == 0) u = (int)atomicAdd(queue, 1u);
-        u = __shfl_sync(FULL, u, 0);
-        if (u >= nunits) break;
-        const Unit U = units[u];
-        bool ok = true;
-        int64_t c;
-        if (U.first) continue;   // replayed exactly by k_first
-        {
-            // warm-up over the tail of the previous unit of the trace; candidates whose
-            // counters become equal run on as one (the lowest lane leads)
-            c = candidate_entry(lane, T);
-            int lead = lane;
-            const Unit Up = units[u - 1];
-            const uint64_t from = Up.len > warmup ? ((Up.len - warmup) / SketchRing::kTL) * SketchRing::kTL : 0;
-            auto wstep = [&](const StepIn<SE> &in, uint32_t) -> bool {
-                const bool act = lead == lane;
-                int64_t tot, qmax, qmin;
-                sketch_step(in, sm.xq, lane, T, t32, act, c, tot, qmax, qmin, [](int, int, bool, int64_t) {});
-                const unsigned same = match_counter(c, t32) & __ballot_sync(FULL, act);
-                if (act) lead = __ffs(same) - 1;
-                return false;
-            };
-            ok = ring_walk<false>(sm, Up, from, Up.len, phase, spin, err, lane, wstep);
-            // followers take their leader's counter (leaders may have joined others later)
-#pragma unroll
-            for (int r = 0; r < 5; ++r) lead = __shfl_sync(FULL, lead, lead);
-            c = __shfl_sync(FULL, c, lead);
-        }
-        const int64_t c0 = c;
-        const unsigned same = match_counter(c, t32);
-        const int leader = __ffs(same) - 1;
-        const bool active = leader == lane;
-        // the first NL distinct runs record every reset (for the exact replay)
-        const uint32_t rank = (uint32_t)__popc(__ballot_sync(FULL, active) & ((1u << lane) - 1u));
-        const uint32_t myslot = active && rank < (uint32_t)NL ? rank : NO_LIST;
-        SRes *L = myslot != NO_LIST ? lists + U.lst0 + (uint64_t)myslot * U.lst_cap : nullptr;
-        Cand *C = cand + (size_t)u * K + lane;
-        uint32_t n = 0;
-        int32_t last = -1;
-        int64_t gmax = INT64_MIN, tmax = INT64_MIN;
-        uint32_t garg = 0, targ = 0;
-        int64_t P = 0, umax = INT64_MIN, umin = INT64_MAX;
-        auto step = [&](const StepIn<SE> &in, uint32_t rel0) -> bool {
+    const Unit U = units[u];
+    bool ok = true;
+    int64_t c;
+    {
+        // warm-up over the tail of the previous unit of the trace; candidates whose
+        // counters become equal run on as one (the lowest lane leads)
+        c = candidate_entry(lane, T);
+        int lead = lane;
+        const Unit Up = units[u - 1];
+        const uint64_t from = Up.len > warmup ? ((Up.len - warmup) / SketchRing::kTL) * SketchRing::kTL : 0;
+        auto wstep = [&](const StepIn<SE> &in, uint32_t) -> bool {
+            const bool act = lead == lane;
             int64_t tot, qmax, qmin;
-            sketch_step(in, sm.xq, lane, T, t32, active, c, tot, qmax, qmin, [&](int k, int r, bool growth, int64_t Qr) {
-                if (lane == k) {
-                    const uint32_t pos = rel0 + (uint32_t)r;
-                    const int64_t Pl = P + Qr;
-                    if (growth && Pl > gmax) { gmax = Pl; garg = pos; }
-                    if (n < (uint32_t)RM) {
-                        C->pos[n] = pos;
-                        C->gp[n] = growth ? Pl : INT64_MIN;
-                    } else if (growth && Pl > tmax) {
-                        tmax = Pl;
-                        targ = pos;
-                    }
-                    if (L && n < U.lst_cap) {
-                        SRes q;
-                        q.pos = pos;
-                        q.pad = 0;
-                        q.P = Pl;
-                        L[n] = q;
-                    }
-                    ++n;
-                    last = (int32_t)pos;
-                }
-            });
-            // the unit's prefix extremes (for the transparency test of k_chain)
-            umax = P + qmax > umax ? P + qmax : umax;
-            umin = P + qmin < umin ? P + qmin : umin;
-            P += tot;
+            sketch_step(in, sm.xq, lane, T, t32, act, c, tot, qmax, qmin, [](int, int, bool, int64_t) {});
+            const unsigned same = match_counter(c, t32) & __ballot_sync(FULL, act);
+            if (act) lead = __ffs(same) - 1;
             return false;
         };
-        if (ok) ok = ring_walk<false>(sm, U, 0, U.len, phase, spin, err, lane, step);
-        __syncwarp();
-        // followers take their leader's run
-        if (active) {
-            for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
-        }
-        __syncwarp();
-        if (!active) {
-            const Cand *Lc = cand + (size_t)u * K + leader;
-            for (int r = 0; r < RM; ++r) { C->pos[r] = Lc->pos[r]; C->gp[r] = Lc->gp[r]; }
-        }
-        C->c0 = c0;
-        C->c = __shfl_sync(FULL, c, leader);
-        C->last = __shfl_sync(FULL, last, leader);
-        C->n = __shfl_sync(FULL, n, leader);
-        C->gmax = __shfl_sync(FULL, gmax, leader);
-        C->garg = __shfl_sync(FULL, garg, leader);
-        C->tmax = __shfl_sync(FULL, tmax, leader);
-        C->targ = __shfl_sync(FULL, targ, leader);
-        {
-            const uint32_t ls = __shfl_sync(FULL, myslot, leader);
-            const uint32_t nl = __shfl_sync(FULL, n, leader);
-            C->list = ls != NO_LIST && nl <= U.lst_cap ? ls : NO_LIST;
-            C->pad = 0;
-        }
-        if (lane == 0) {
-            UnitSum S;   // window totals are filled by k_totals, for the units that need them
-            S.total = P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = umin; S.maxQ = umax;
-            usum[u] = S;
-        }
-        if (!ok) break;
+        ok = ring_walk<false>(sm, Up, from, Up.len, phase, spin, err, lane, wstep);
+        // followers take their leader's counter (leaders may have joined others later)
+#pragma unroll
+        for (int r = 0; r < 5; ++r) lead = __shfl_sync(FULL, lead, lead);
+        c = __shfl_sync(FULL, c, lead);
     }
+    const int64_t c0 = c;
+    const unsigned same = match_counter(c, t32);
+    const int leader = __ffs(same) - 1;
+    const bool active = leader == lane;
+    // the first NL distinct runs record every reset (for the exact replay)
+    const uint32_t rank = (uint32_t)__popc(__ballot_sync(FULL, active) & ((1u << lane) - 1u));
+    const uint32_t myslot = active && rank < (uint32_t)NL ? rank : NO_LIST;
+    SRes *L = myslot != NO_LIST ? lists + U.lst0 + (uint64_t)myslot * U.lst_cap : nullptr;
+    Cand *C = cand + (size_t)u * K + lane;
+    uint32_t n = 0;
+    int32_t last = -1;
+    int64_t gmax = INT64_MIN, tmax = INT64_MIN;
+    uint32_t garg = 0, targ = 0;
+    int64_t P = 0, umax = INT64_MIN, umin = INT64_MAX;
+    auto step = [&](const StepIn<SE> &in, uint32_t rel0) -> bool {
+        int64_t tot, qmax, qmin;
+        sketch_step(in, sm.xq, lane, T, t32, active, c, tot, qmax, qmin, [&](int k, int r, bool growth, int64_t Qr) {
+            if (lane == k) {
+                const uint32_t pos = rel0 + (uint32_t)r;
+                const int64_t Pl = P + Qr;
+                if (growth && Pl > gmax) { gmax = Pl; garg = pos; }
+                if (n < (uint32_t)RM) {
+                    C->pos[n] = pos;
+                    C->gp[n] = growth ? Pl : INT64_MIN;
+                } else if (growth && Pl > tmax) {
+                    tmax = Pl;
+                    targ = pos;
+                }
+                if (L && n < U.lst_cap) {
+                    SRes q;
+                    q.pos = pos;
+                    q.pad = 0;
+                    q.P = Pl;
+                    L[n] = q;
+                }
+                ++n;
+                last = (int32_t)pos;
+            }
+        });
+        // the unit's prefix extremes (for the transparency test of k_chain)
+        umax = P + qmax > umax ? P + qmax : umax;
+        umin = P + qmin < umin ? P + qmin : umin;
+        P += tot;
+        return false;
+    };
+    if (ok) ok = ring_walk<false>(sm, U, 0, U.len, phase, spin, err, lane, step);
+    __syncwarp();
+    // followers take their leader's run
+    if (active) {
+        for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
+    }
+    __syncwarp();
+    if (!active) {
+        const Cand *Lc = cand + (size_t)u * K + leader;
+        for (int r = 0; r < RM; ++r) { C->pos[r] = Lc->pos[r]; C->gp[r] = Lc->gp[r]; }
+    }
+    C->c0 = c0;
+    C->c = __shfl_sync(FULL, c, leader);
+    C->last = __shfl_sync(FULL, last, leader);
+    C->n = __shfl_sync(FULL, n, leader);
+    C->gmax = __shfl_sync(FULL, gmax, leader);
+    C->garg = __shfl_sync(FULL, garg, leader);
+    C->tmax = __shfl_sync(FULL, tmax, leader);
+    C->targ = __shfl_sync(FULL, targ, leader);
+    {
+        const uint32_t ls = __shfl_sync(FULL, myslot, leader);
+        const uint32_t nl = __shfl_sync(FULL, n, leader);
+        C->list = ls != NO_LIST && nl <= U.lst_cap ? ls : NO_LIST;
+        C->pad = 0;
+    }
+    if (lane == 0) {
+        UnitSum S;   // window totals are filled by k_totals, for the units that need them
+        S.total = P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = umin; S.maxQ = umax;
+        usum[u] = S;
+    }
+    return ok;
 }
 
-// ---------------------------------------------------------------- k_first
-using FirstRing = Ring<true, 2, 256, 8>;
+// The first unit u of a trace in the batch: its entry is the trace's resident state, so it
+// is replayed exactly once (k_final skips it) and the run is recorded as every candidate.
+// Returns false if a wait timed out.
+__device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__restrict__ units, UnitSum *usum,
+                           Cand *cand, FRec *recs, UnitOut *uout, const DevTrace *traces, int64_t T, ErrWord *err,
+                           unsigned long long spin, int lane) {
+    const Unit U = units[u];
+    const DevTrace st = traces[U.trace];
+    ExactIn in0;
+    in0.c = st.c;
+    in0.wA = lane == 0 ? st.A : 0;
+    in0.wApy = lane == 0 ? st.A_py : 0;
+    in0.wSpy = lane == 0 ? st.A_py - st.F_py : 0;
+    in0.mark = st.hwm;
+    in0.fpb = st.footprint;
+    in0.tk = st.tracked_valid ? 2u : 0u;   // as k_scan plans a trace's first unit
+    in0.taddr = st.tracked_addr;
+    in0.list = nullptr;
+    in0.nres = 0;
+    in0.exit_c = 0;
+    ExactRun R;
+    R.C0 = cand + (size_t)u * K;
+    UnitOut O;
+    uint32_t n = 0;
+    const bool ok = exact_unit<true>(fr, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R);
+    if (!ok) return false;   // a wait timed out (the ring may not be reusable)
+    Cand *C = cand + (size_t)u * K + lane;
+    if (lane == 0)
+        for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
+    __syncwarp();
+    if (lane != 0) {
+        const Cand *C0 = R.C0;
+        for (int r = 0; r < RM; ++r) { C->pos[r] = C0->pos[r]; C->gp[r] = C0->gp[r]; }
+    }
+    C->c0 = st.c; C->c = O.c; C->last = R.last; C->n = n;
+    C->gmax = R.gmax; C->garg = R.garg; C->tmax = R.tmax; C->targ = R.targ;
+    C->list = NO_LIST; C->pad = 0;
+    if (lane == 0) {
+        UnitSum S;   // window totals are filled by k_totals, for the units that need them
+        S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = R.umin; S.maxQ = R.umax;
+        usum[u] = S;
+        uout[u] = O;
+        if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);
+    }
+    return true;
+}
 
-__global__ void __launch_bounds__(32 * FIRST_WARPS) k_first(const Unit *__restrict__ units, const BTrace *__restrict__ bts,
-                                                           int nbt, UnitSum *usum, Cand *cand, FRec *recs, UnitOut *uout,
-                                                           const DevTrace *traces, int64_t T, unsigned *queue,
-                                                           ErrWord *err, unsigned long long spin) {
+// Phase 1, one persistent kernel: every warp takes work from one queue -- the units
+// (`order`, longest work first), then the copy-volume tiles in rounds over the traces (a
+// trace's tiles in order) -- replaying a
+// trace's first unit exactly, sketching every other unit, and sampling memcpy tiles, so the
+// latency-bound candidate counters and the bandwidth-bound passes share the SMs, a long
+// first unit starts early, and the short copy tiles fill the end.
+__global__ void __launch_bounds__(32 * PHASE1_MAX_WARPS, 1) k_phase1(const LaunchSketch a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    FirstRing &fr = reinterpret_cast<FirstRing *>(smem_raw)[warp];
-    ring_init(fr, lane);
-    uint32_t fphase = 0;
+    Phase1Smem &sm = *reinterpret_cast<Phase1Smem *>(smem_raw + (size_t)warp * PHASE1_WARP_SMEM);
+    int cur = -1;   // staging area in use: 0 sketch ring, 1 exact ring, 2 copy tile
+    uint32_t phase = 0;
+    CopyStatus *cstatus = static_cast<CopyStatus *>(a.cstatus);
     while (true) {
-        int b = 0;
-        if (lane == 0) b = (int)atomicAdd(queue, 1u);
-        b = __shfl_sync(FULL, b, 0);
-        if (b >= nbt) break;
-        if (bts[b].nu == 0) continue;
-        const int u = (int)bts[b].u0;
-        const Unit U = units[u];
-        // The trace's resident state is this unit's exact entry: replay it exactly (k_final
-        // skips it) and record the run as every lane's candidate.
-        const DevTrace st = traces[U.trace];
-        ExactIn in0;
-        in0.c = st.c;
-        in0.wA = lane == 0 ? st.A : 0;
-        in0.wApy = lane == 0 ? st.A_py : 0;
-        in0.wSpy = lane == 0 ? st.A_py - st.F_py : 0;
-        in0.mark = st.hwm;
-        in0.fpb = st.footprint;
-        in0.tk = st.tracked_valid ? 2u : 0u;   // as k_scan plans a trace's first unit
-        in0.taddr = st.tracked_addr;
-        in0.list = nullptr;
-        in0.nres = 0;
-        in0.exit_c = 0;
-        ExactRun R;
-        R.C0 = cand + (size_t)u * K;
-        UnitOut O;
-        uint32_t n = 0;
-        const bool ok = exact_unit<true>(fr, fphase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R);
-        if (!ok) break;   // a wait timed out: leave (the ring may not be reusable)
-        Cand *C = cand + (size_t)u * K + lane;
-        if (lane == 0)
-            for (uint32_t r = n; r < (uint32_t)RM; ++r) { C->pos[r] = 0xffffffffu; C->gp[r] = INT64_MIN; }
-        __syncwarp();
-        if (lane != 0) {
-            const Cand *C0 = R.C0;
-            for (int r = 0; r < RM; ++r) { C->pos[r] = C0->pos[r]; C->gp[r] = C0->gp[r]; }
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(a.queue, 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= a.nitems + a.nctiles) break;
+        const int u = it < a.nitems ? (int)a.order[it] : -1;
+        const int want = u < 0 ? 2 : a.units[u].first ? 1 : 0;
+        if (want != cur) {
+            if (cur == 0) ring_release(sm.s, lane);
+            if (cur == 1) ring_release(sm.f, lane);
+            if (cur == 2) copy_smem_release(sm.c, lane);
+            if (want == 0) ring_init(sm.s, lane);
+            if (want == 1) ring_init(sm.f, lane);
+            if (want == 2) copy_smem_init(sm.c, lane);
+            cur = want;
+            phase = 0;
         }
-        C->c0 = st.c; C->c = O.c; C->last = R.last; C->n = n;
-        C->gmax = R.gmax; C->garg = R.garg; C->tmax = R.tmax; C->targ = R.targ;
-        C->list = NO_LIST; C->pad = 0;
-        if (lane == 0) {
-            UnitSum S;   // window totals are filled by k_totals, for the units that need them
-            S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = R.umin; S.maxQ = R.umax;
-            usum[u] = S;
-            uout[u] = O;
-            if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);
+        bool ok;
+        if (want == 2) {
+            const uint32_t t = a.order[it];
+            const CopyTile ct = a.ctiles[t];
+            const BTrace B = a.bts[ct.bt];
+            ok = copy_tile(sm.c, phase, ct, t, B.c0, cstatus, a.traces[B.trace].copy_counter, a.Tc, a.n_lines,
+                           a.lines + (uint64_t)B.trace * a.n_lines, t + 1 == B.c0 + B.nc ? a.btres + ct.bt : nullptr,
+                           a.err, a.spin, lane);
+        } else if (want == 1) {
+            ok = first_unit(sm.f, phase, u, a.units, a.usum, a.cand, a.recs, a.uout, a.traces, a.T, a.err, a.spin,
+                            lane);
+        } else {
+            ok = sketch_unit(sm.s, phase, u, a.units, a.usum, a.cand, a.lists, a.T, a.warmup, a.err, a.spin, lane);
         }
+        if (!ok) break;   // a wait timed out: leave (the staging area may not be reusable)
     }
 }
 
@@ -723,28 +759,16 @@ cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_sketch(const LaunchSketch &a, cudaStream_t s) {
-    const size_t smem = SKETCH_WARP_SMEM * a.warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_phase1(const LaunchSketch &a, cudaStream_t s) {
+    if (!a.nitems && !a.nctiles) return cudaSuccess;
+    const size_t smem = PHASE1_WARP_SMEM * a.warps_per_block;
+    cudaError_t e = cudaFuncSetAttribute(k_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sketch<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.usum, a.cand, a.lists, a.recs,
-                                                            a.uout, a.traces, a.T, a.warmup, a.queue, a.err, a.spin);
+    k_phase1<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_first(const LaunchSketch &a, cudaStream_t s) {
-    if (!a.nbt) return cudaSuccess;
-    const int w = std::min(FIRST_WARPS, a.nbt);   // a lone trace takes one warp of one SM
-    const size_t smem = sizeof(FirstRing) * w;
-    cudaError_t e = cudaFuncSetAttribute(k_first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int blocks = std::max(1, std::min((a.nbt + w - 1) / w, 4 * a.num_sms));
-    k_first<<<blocks, 32 * w, smem, s>>>(a.units, a.bts, a.nbt, a.usum, a.cand, a.recs, a.uout, a.traces, a.T,
-                                                   a.queue + 1, a.err, a.spin);
-    return cudaGetLastError();
-}
-
-const void *first_kernel() { return reinterpret_cast<const void *>(k_first); }
+size_t copy_status_bytes(size_t ntiles) { return sizeof(CopyStatus) * ntiles; }
 
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s) {
     const int threads = a.nunits * K;
@@ -762,11 +786,11 @@ cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int sketch_occupancy(int warps_per_block, int *blocks_per_sm) {
-    const size_t smem = SKETCH_WARP_SMEM * warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(k_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int phase1_occupancy(int warps_per_block, int *blocks_per_sm) {
+    const size_t smem = PHASE1_WARP_SMEM * warps_per_block;
+    cudaError_t e = cudaFuncSetAttribute(k_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sketch, 32 * warps_per_block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_phase1, 32 * warps_per_block, smem);
     return e == cudaSuccess ? 0 : -1;
 }
 

@@ -267,7 +267,7 @@ __device__ __forceinline__ int first_cross(const StepPrefix<EL> &sp, const int64
     return -1;
 }
 
-// ---- the 32-bit form of a step, for the candidate counters of k_sketch.
+// ---- the 32-bit form of a step, for the candidate counters of the sketch.
 // When every delta of the step lies in [-2^22, 2^22) the step's prefixes lie in
 // (-2^30, 2^30); with T <= 2^30 a counter lies in (-2^30, 2^30) as well, so a counter plus
 // a prefix, T minus a counter and every other quantity of the crossing search fit in
