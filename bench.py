@@ -3,24 +3,38 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
 A step is one pass of the whole path -- threshold sampler, attribution, high-water
-crossings, leak membership test, leak scores, copy-volume sampler -- over one
-trace resident in HBM (the trace's state is reset before each step).  The default
-workload is the single 2^28-event trace (5 leaking lines, a +2 GiB ramp, 2^28/10
-memcpys, T = 10,485,767); its 5.9 GB of input is far larger than the 129 MB L2,
-so no flush is needed between steps.  Under torchrun each rank replays its own
-trace (seed + rank): per-GPU work is fixed (weak scaling).
+crossings, leak membership test, leak scores, copy-volume sampler -- over one batch of
+synthetic traces resident in HBM (the traces' state is reset before each step).
 
-One JSON line is printed by rank 0.  `value` is alloc/free events per second over
-all ranks, timed with CUDA events on the replay stream; `e2e` is the same metric
-through scl_replay_batch_host with pinned host buffers (host-to-device copies and
-the read-back of the per-line results inside the timed region); `roofline` is the
-dominant kernel's algorithmic bytes per launch over its CUDA-event duration;
-`cpu_baseline` times the sequential oracle on this host and also checks that the
-last GPU step agrees with it exactly.  --impl reference times the oracle instead.
+Workloads (`--workload`):
+  batched (default)  4,096 independent traces, log-uniform 10k-4M events (2.70 G events,
+                     270 M memcpys), 4,096 lines, leak injection in every 100th trace,
+                     T = 10,485,767: one scl_replay_batch per step, relaunched as a CUDA
+                     graph, tuned by scl_autotune first.  57 GB of input per step, far larger
+                     than the 129 MB L2, so no flush is needed between steps.
+  long_256m          one trace of 2^28 events (5 leaking lines, a +2 GiB ramp, 2^28/10
+                     memcpys).
+  sweep              1,024 traces x 1M events in four families (4 GiB mallocs, adversarial
+                     +-(T-1), malloc-only 4 KiB, 70% frees) at each T in {1; 1,048,573;
+                     10,485,767; 104,857,601}: a step replays the four batches.
+  plain_1m           one 1M-event trace.
+  serving            512 processes x 16 segments of 64k events through scl_serve.
+Under torchrun each rank replays its own batch (seed + rank): per-GPU work is fixed
+(weak scaling); rank 0 prints the line.
+
+One JSON line is printed by rank 0.  `value` is alloc/free events per second over all
+ranks, timed with CUDA events on the replay stream; `e2e` is the same metric through
+scl_replay_batch_host with pinned host buffers (host-to-device copies and the read-back
+of per-line results inside the timed region); `roofline` is the dominant kernel's
+algorithmic bytes per launch over its CUDA-event duration; `cpu_baseline` times the
+sequential oracle with one thread per host core on a sample of the workload's traces,
+which also checks the last GPU step against it exactly.  --impl reference times that
+oracle instead, on the same sample, configuration and metric.
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import hashlib
 import json
 import os
@@ -35,36 +49,35 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic bytes each kernel must read per unit it processes
-ALG_BYTES = {
-    "sketch": 8.0,        # delta per event: the candidate counters (warm-up re-reads are overhead, not counted)
-    "final": 17.0,        # delta (8) + addr (8) + is_python (1) per event: the exact replay
-    "copy_apply": 13.0,   # size (8) + line (4) + is_python (1) per memcpy event
-    "copy_sum": 8.0,      # size per memcpy event
-}
-EVENT_KERNELS = ("sketch", "final")
-PATH_BYTES_PER_EVENT = 17.0        # delta + addr + is_python: every event field the path reads
-PATH_BYTES_PER_COPY = 13.0
+METRIC = "alloc/free events replayed per second (bit-exact)"
+# algorithmic bytes each unit of work must read (a unit: an event or a memcpy)
+EVENT_BYTES = 21.0       # delta 8 + addr 8 + line 4 + flag 1: the workload's bytes per event
+COPY_BYTES = 13.0        # size 8 + line 4 + flag 1 per memcpy
+EXACT_BYTES = 17.0       # an exact replay reads delta, addr and flag (the line only at samples)
+SKETCH_BYTES = 8.0       # the candidate counters read delta (warm-up re-reads are overhead)
+ALG_BYTES = {"sketch": SKETCH_BYTES, "final": EXACT_BYTES, "first": EXACT_BYTES, "copy": COPY_BYTES}
+EVENT_KERNELS = ("phase1", "final")
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default="long_256m", choices=["long_256m", "plain_1m", "batched", "serving"])
-    p.add_argument("--events", type=int, default=0, help="override the trace length (testing)")
-    p.add_argument("--traces", type=int, default=0, help="batched: number of traces (default 4,096)")
+    p.add_argument("--workload", default="batched", choices=["batched", "long_256m", "plain_1m", "sweep", "serving"])
+    p.add_argument("--events", type=int, default=0, help="override a trace length (testing)")
+    p.add_argument("--traces", type=int, default=0, help="batched / sweep: number of traces")
     p.add_argument("--procs", type=int, default=0, help="serving: processes (default 512)")
     p.add_argument("--segs", type=int, default=0, help="serving: segments per process (default 16)")
-    p.add_argument("--no-tune", action="store_true", help="batched: skip the autotuner")
+    p.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     p.add_argument("--tune", action="store_true", help="long/plain: run the autotuner before timing")
     p.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     p.add_argument("--no-rate", action="store_true", help="long/plain: skip the rate-based sampling comparison")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    return p.parse_args()
+    p.add_argument("--no-loop", action="store_true", help="batched: skip the per-trace loop comparison")
+    return p.parse_args(argv)
 
 
 def dist_env():
@@ -94,15 +107,11 @@ def job_throughput(ms, events, device="cpu"):
     return aggregate([float(t.item())], [float(e.item())])
 
 
-def make_trace(workload: str, rank: int, n_override: int = 0):
-    from paper_2212_07597_gb300 import tracegen as tg
-    if workload == "long_256m":
-        n = n_override or (1 << 28)
-        return tg.long_trace(n, seed=1 + rank), dict(workload=f"single long trace, {n:,} events", events=n,
-                                                     memcpys=n // 10, threshold=tg.T_PLAIN, n_lines=256)
-    n = n_override or 1_000_000
-    return tg.plain_trace(n, seed=rank), dict(workload=f"plain trace, {n:,} events", events=n, memcpys=n // 10,
-                                              threshold=tg.T_PLAIN, n_lines=256)
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class Clocks:
@@ -182,18 +191,21 @@ class Clocks:
                                                         "than the sampling period)"}
 
 
+KERNEL_SOURCES = ("scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_stage.cuh", "scl_internal.cuh",
+                  "scl_exact.cuh", "scl_copy.cuh")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_stage.cuh", "scl_internal.cuh", "scl_exact.cuh"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2212_07597_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, units: int, streamed: int = 0):
+def traffic_for(kernel: str, units: float):
     """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json), if it
-    was taken on the current kernels: bytes per unit x units, where a unit is an event
-    (exact replay), a memcpy (copy kernels), or for the sketch an event streamed through
-    it (its unit plus its warm-up, `streamed`)."""
+    was taken on the current kernel sources: the captured bytes per algorithmic byte times
+    this launch's algorithmic bytes (`units`)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -204,62 +216,7 @@ def traffic_for(kernel: str, units: int, streamed: int = 0):
     k = d.get("kernels", {}).get(kernel)
     if not k or d.get("source_hash") != source_hash():
         return None
-    return k["dram_bytes_per_unit"] * (streamed if k.get("unit") == "streamed event" else units)
-
-
-def oracle_replay(tr, meta):
-    import oracle
-    o = oracle.Oracle(meta["threshold"], n_lines=meta["n_lines"])
-    o.replay_events(tr.delta, tr.addr, tr.line, tr.is_python)
-    o.replay_copies(tr.csize, tr.cline, tr.cpy)
-    return o
-
-
-def run_reference(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return 0
-    if args.workload in ("batched", "serving"):
-        # a bounded sample of the workload's traces, replayed one after another
-        from paper_2212_07597_gb300 import tracegen as tg
-        if args.workload == "batched":
-            lens = tg.batched_lengths(4096, seed=2)[:args.traces or 4096]
-            pick = list(range(0, len(lens), max(1, len(lens) // 16)))[:16]
-            trs = [tg.batched_trace(i, int(lens[i]), seed=2) for i in pick]
-            meta = {"threshold": tg.T_PLAIN, "n_lines": 4096, "memcpys": sum(len(t.csize) for t in trs),
-                    "workload": f"batched: sampled traces {pick}"}
-        else:
-            n_p = (args.segs or 16) * (args.events or 65536)
-            pick = list(range(0, args.procs or 512, 64))
-            trs = [tg.serving_process(p, n_p, seed=4, n_lines=1024) for p in pick]
-            meta = {"threshold": tg.T_PLAIN, "n_lines": 1024, "memcpys": sum(len(t.csize) for t in trs),
-                    "workload": f"serving: sampled processes {pick}"}
-        n = sum(t.n for t in trs)
-        meta["events"] = n
-        run = lambda: [oracle_replay(t, meta) for t in trs]
-    else:
-        tr, meta = make_trace(args.workload, 0, args.events)
-        n = meta["events"]
-        run = lambda: oracle_replay(tr, meta)
-    for _ in range(args.warmup):
-        run()
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        run()
-        ts.append(time.perf_counter() - t0)
-    tot = sum(ts)
-    v = n * args.steps / tot
-    line = {"impl": "reference", "metric": "alloc/free events replayed per second (bit-exact)", "value": v,
-            "unit": "events/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": meta["workload"], "threshold": meta["threshold"], "n_lines": meta["n_lines"]},
-            "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n:,} events (+{meta['memcpys']:,} memcpys) per step, sequential"},
-            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
+    return k["dram_bytes_per_alg_byte"] * units
 
 
 def measured_peak():
@@ -272,41 +229,37 @@ def measured_peak():
     return 6800.0, "of fallback"
 
 
-def roofline_of(ktimes, n, m, traffic=True, sketch_n=None):
-    """Dominant kernel of the path and its algorithmic GB/s over its CUDA-event time per launch.
-    The sketch and the exact replay take the events of every unit but the traces' first ones
-    (sketch_n; those are replayed by k_first).  The
-    dominant kernel is taken on the event path's stream: the copy-volume kernels run on a
-    lower-priority side stream beside it, so their event-timed spans include waits for SMs."""
-    dom = max((k for k in ktimes if k in EVENT_KERNELS), key=lambda k: ktimes[k][0])
-    d_ms, d_cnt = ktimes[dom]
-    units = n if dom in EVENT_KERNELS else m
-    if dom in EVENT_KERNELS and sketch_n is not None:
-        units = sketch_n
-    achieved = ALG_BYTES[dom] * units / (d_ms / d_cnt / 1e3) / 1e9
+def kernel_bytes(n, m, first_events):
+    """Algorithmic bytes each replay kernel reads per launch: k_phase1 replays the traces'
+    first units exactly (17 B/event), sketches the other units (8 B/event) and samples the
+    memcpys (13 B each); k_final replays the non-first units exactly (17 B/event)."""
+    rest = n - first_events
+    return {"phase1": EXACT_BYTES * first_events + SKETCH_BYTES * rest + COPY_BYTES * m,
+            "final": EXACT_BYTES * rest}
+
+
+def roofline_of(ktimes, n, m, first_events, launches_per_step=1, traffic=True):
+    """The dominant replay kernel (k_phase1 or k_final) and its algorithmic GB/s over its
+    CUDA-event time per launch, plus the same figures for the other one."""
+    per = kernel_bytes(n, m, first_events)
     peak, src = measured_peak()
-    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": src,
-            "traffic": traffic_for(dom, units) if traffic else None, "alg_bytes_per_unit": ALG_BYTES[dom]}
-
-
-def oracle_matches(ctx, tid, o, scl):
-    gl, wl = scl.scl_line_stats(ctx, tid), o.lines()
-    lk = scl.scl_leak_scores(ctx, tid)
-    num, den = o.leak_scores()
-    st, ost = scl.scl_trace_state(ctx, tid), o.state()
-    ok = all(np.array_equal(gl[k], wl[k]) for k in ("n_growth", "n_shrink", "A", "F", "A_py", "F_py", "net",
-                                                     "copy_samples", "copy_bytes"))
-    ok = ok and np.array_equal(lk["mallocs"], wl["mallocs"]) and np.array_equal(lk["frees"], wl["frees"])
-    ok = ok and np.array_equal(lk["num"], num) and np.array_equal(lk["den"], den)
-    ok = ok and all(st[k] == ost[k] for k in ("c", "A", "F", "footprint", "hwm", "n_events", "copy_counter"))
-    return ok and st["n_samples"] == len(o.samples())
+    ks = {}
+    for k in EVENT_KERNELS:
+        if k in ktimes and ktimes[k][1]:
+            ms = ktimes[k][0] / ktimes[k][1]
+            a = per[k] / launches_per_step / (ms / 1e3) / 1e9
+            ks[k] = {"ms": ms, "alg_bytes": per[k] / launches_per_step, "achieved": a, "frac": a / peak,
+                     "traffic": traffic_for(k, per[k] / launches_per_step) if traffic else None}
+    dom = max(ks, key=lambda k: ks[k]["ms"])
+    d = ks[dom]
+    return {"bound": "hbm", "kernel": dom, "achieved": d["achieved"], "peak": peak, "unit": "GB/s",
+            "frac": d["frac"], "peak_source": src, "traffic": d["traffic"], "alg_bytes": d["alg_bytes"],
+            "kernels": ks}
 
 
 def chunked(fn, items, workers):
-    """fn over items on a thread pool (the generators release the GIL), results in order,
-    a bounded number in flight."""
-    import concurrent.futures as cf
+    """fn over items on a thread pool (the generators and the oracle release the GIL in their
+    C calls), results in order, a bounded number in flight."""
     with cf.ThreadPoolExecutor(workers) as ex:
         for k in range(0, len(items), 2 * workers):
             yield from zip(items[k:k + 2 * workers], ex.map(fn, items[k:k + 2 * workers]))
@@ -316,12 +269,158 @@ def pad16(x):
     return (int(x) + 15) // 16 * 16
 
 
-def run_batched(args):
-    """4,096 independent traces (log-uniform 10k-4M events, 4,096 lines, leak injection in
-    every 100th) replayed by one scl_replay_batch call per step, relaunched as a CUDA graph."""
-    import torch
-    from paper_2212_07597_gb300 import build as scl_build
+# ---------------------------------------------------------------- the oracle on the host
+
+def oracle_replay(tr, threshold, n_lines):
+    import oracle
+    o = oracle.Oracle(threshold, n_lines=n_lines)
+    o.replay_events(tr.delta, tr.addr, tr.line, tr.is_python)
+    o.replay_copies(tr.csize, tr.cline, tr.cpy)
+    return o
+
+
+def oracle_parallel(trs, threshold, n_lines, reps=1):
+    """The sequential oracle over independent traces, one thread per host core (each
+    replay is one C call that releases the GIL).  Returns (oracles, wall seconds per pass,
+    threads)."""
+    cores = host_cores()
+    walls, out = [], None
+    with cf.ThreadPoolExecutor(cores) as ex:
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            out = list(ex.map(lambda t: oracle_replay(t, threshold, n_lines), trs))
+            walls.append(time.perf_counter() - t0)
+    return out, walls, cores
+
+
+def full_match(ctx, tid, o, scl, samples=True):
+    """The trace's GPU results equal the oracle's: every sample record (all fields), the
+    per-line totals and leak scores, and the resident state."""
+    ok = True
+    if samples:
+        g, w = scl.scl_samples(ctx, tid), o.samples()
+        ok = len(g) == len(w) and all(np.array_equal(g[k], w[k]) for k in
+                                       ("idx", "A", "F", "A_py", "F_py", "footprint", "line", "kind", "is_python",
+                                        "is_hwm"))
+    gl, wl = scl.scl_line_stats(ctx, tid), o.lines()
+    ok = ok and all(np.array_equal(gl[k], wl[k]) for k in ("n_growth", "n_shrink", "A", "F", "A_py", "F_py", "net",
+                                                            "copy_samples", "copy_bytes"))
+    lk = scl.scl_leak_scores(ctx, tid)
+    num, den = o.leak_scores()
+    ok = ok and np.array_equal(lk["mallocs"], wl["mallocs"]) and np.array_equal(lk["frees"], wl["frees"])
+    ok = ok and np.array_equal(lk["num"], num) and np.array_equal(lk["den"], den)
+    st, ost = scl.scl_trace_state(ctx, tid), o.state()
+    ok = ok and all(st[k] == ost[k] for k in ("c", "A", "F", "A_py", "F_py", "footprint", "hwm", "n_events",
+                                              "copy_counter", "tracked_addr", "tracked_line"))
+    return ok and st["n_samples"] == len(o.samples())
+
+
+# ---------------------------------------------------------------- workloads
+
+def batched_spec(ntr, rank=0, events=0):
     from paper_2212_07597_gb300 import tracegen as tg
+    lens = tg.batched_lengths(4096, seed=2 + rank)[:ntr].astype(np.int64)
+    if events:
+        lens = np.minimum(lens, events)
+    return lens, lens // 10
+
+
+def batched_config(ntr, lens, mlen):
+    from paper_2212_07597_gb300 import tracegen as tg
+    return {"workload": f"batched: {ntr:,} traces, {int(lens.sum()):,} events, {int(mlen.sum()):,} memcpys, "
+                        f"log-uniform 10k-4M, 4,096 lines, leak injection every 100th trace",
+            "threshold": tg.T_PLAIN, "n_lines": 4096, "memcpys": int(mlen.sum()),
+            "l2": f"inputs larger than L2 ({(EVENT_BYTES * lens.sum() + COPY_BYTES * mlen.sum()) / 1e9:.0f} GB), "
+                  "no flush"}
+
+
+def batched_sample(lens):
+    """A stratified sample of the batch's traces: 512 evenly spaced ranks of the length order
+    (shortest and longest included) and every leaking trace (every 100th)."""
+    order = np.argsort(lens, kind="stable")
+    k = min(512, len(lens))
+    pick = {int(order[int(round(r))]) for r in np.linspace(0, len(lens) - 1, k)}
+    pick |= {i for i in range(0, len(lens), 100)}
+    return sorted(pick)
+
+
+def parity_subset(lens, sample):
+    """Traces whose full sample arrays are compared: shortest, longest, median, every leaking
+    trace of the sample, and 16 more spread over the length order."""
+    srt = sorted(sample, key=lambda i: (lens[i], i))
+    pick = {srt[0], srt[-1], srt[len(srt) // 2]} | {i for i in sample if i % 100 == 0}
+    pick |= {srt[int(round(r))] for r in np.linspace(0, len(srt) - 1, 16)}
+    return sorted(pick)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2212_07597_gb300 import tracegen as tg
+    if args.workload == "batched":
+        ntr = args.traces or 4096
+        lens, mlen = batched_spec(ntr, 0, args.events)
+        pick = batched_sample(lens)
+        trs = [t for _, t in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2), pick, host_cores())]
+        T, L = tg.T_PLAIN, 4096
+        config = batched_config(ntr, lens, mlen)
+        sample = f"{len(pick)} of the batch's traces (512 evenly spaced by length + the leaking ones)"
+    elif args.workload == "sweep":
+        per, n = (args.traces or 1024), (args.events or 1_000_000)
+        pick = list(range(0, per, max(1, per // 64)))[:64]
+        trs = [(T, tg.sweep_trace(i, T, n=n)) for T in tg.SWEEP_THRESHOLDS for i in pick]
+        config = sweep_config(per, n)
+        sample = f"{len(pick)} traces of each threshold's batch"
+        T, L = None, 256
+    elif args.workload == "serving":
+        P, S, Lseg = args.procs or 512, args.segs or 16, args.events or 65536
+        pick = list(range(0, P, 8))
+        trs = [tg.serving_process(p, S * Lseg, seed=4, n_lines=1024) for p in pick]
+        T, L = tg.T_PLAIN, 1024
+        config = serving_config(P, S, Lseg)
+        sample = f"{len(pick)} of {P} processes, whole"
+    else:
+        tr, meta = make_trace(args.workload, 0, args.events)
+        trs, T, L = [tr], meta["threshold"], meta["n_lines"]
+        config = meta["config"]
+        sample = "the whole trace (the replay of one trace is sequential)"
+    n = sum(t[1].n if isinstance(t, tuple) else t.n for t in trs)
+    m = sum(len(t[1].csize) if isinstance(t, tuple) else len(t.csize) for t in trs)
+
+    def run():
+        if T is None:   # sweep: each trace under its own threshold
+            cores = host_cores()
+            t0 = time.perf_counter()
+            with cf.ThreadPoolExecutor(cores) as ex:
+                list(ex.map(lambda p: oracle_replay(p[1], p[0], L), trs))
+            return time.perf_counter() - t0, cores
+        _, walls, cores = oracle_parallel(trs, T, L)
+        return walls[0], cores
+
+    config = dict(config, parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
+    for _ in range(args.warmup):
+        run()
+    ts = []
+    cores = 1
+    for _ in range(args.steps):
+        w, cores = run()
+        ts.append(w)
+    tot = sum(ts)
+    v = n * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample}: {n:,} events + {m:,} memcpys per step, one thread per core"},
+            "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def init_dist_and_lib():
+    import torch
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
@@ -329,13 +428,74 @@ def run_batched(args):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
+    from paper_2212_07597_gb300 import build as scl_build
     scl_build.build()
     from paper_2212_07597_gb300 import scl
+    return ws, rank, scl
+
+
+def barrier_fn(ws):
+    import torch
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+    return barrier
+
+
+def timed(step, steps, warmup, stream, barrier, clocks_on):
+    """W untimed steps, then K steps between CUDA events on the replay stream (barrier and
+    synchronise on both sides).  Returns (ms for the K steps, clock record)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        step()
+    barrier()
+    clocks = Clocks(torch.cuda.current_device()) if clocks_on else None
+    if clocks:
+        clocks.warm(step, torch.cuda.synchronize)
+    barrier()
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    barrier()
+    if clocks:
+        clocks.end()
+    return e0.elapsed_time(e1), (clocks.stop() if clocks else None)
+
+
+def tuning_dict(t, ms=None):
+    d = {"unit_events": t.unit_events, "first_events": t.first_events, "phase1_warps": t.warps_per_block,
+         "warmup_events": t.ext_events, "final_warps": t.final_warps, "fixup": t.fixup}
+    if ms is not None:
+        d["ms"] = ms
+    return d
+
+
+def profile_steps(scl, ctx, step, k=2):
+    """Per-kernel CUDA-event times over k plain (not graph) steps."""
+    scl.scl_profile_reset(ctx)
+    scl.scl_profile_enable(ctx, True)
+    for _ in range(k):
+        step()
+    scl.scl_profile_enable(ctx, False)
+    kt = scl.scl_kernel_times(ctx)
+    return kt, int(sum(c for _, c in kt.values())) // k
+
+
+def run_batched(args):
+    """4,096 independent traces replayed by one scl_replay_batch call per step, relaunched as a
+    CUDA graph, after scl_autotune."""
+    import torch
+    from paper_2212_07597_gb300 import tracegen as tg
+    ws, rank, scl = init_dist_and_lib()
     ntr = args.traces or 4096
-    lens = tg.batched_lengths(4096, seed=2 + rank)[:ntr].astype(np.int64)
-    if args.events:
-        lens = np.minimum(lens, args.events)
-    mlen = lens // 10
+    lens, mlen = batched_spec(ntr, rank, args.events)
     eo = np.concatenate([[0], np.cumsum([pad16(x) for x in lens])])
     co = np.concatenate([[0], np.cumsum([pad16(x) for x in mlen])])
     N, M = int(eo[-1]), int(co[-1])
@@ -347,8 +507,8 @@ def run_batched(args):
             torch.empty(M, dtype=torch.uint8, device=dev)]
     views = (np.int64, np.int64, np.int32, np.uint8)
     t_gen = time.perf_counter()
-    workers = min(32, os.cpu_count() or 4)
-    for i, tr in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2 + rank), list(range(ntr)), workers):
+    for i, tr in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2 + rank), list(range(ntr)),
+                         min(32, host_cores())):
         a, b = int(eo[i]), int(co[i])
         for c, x, v in zip(cols[:4], (tr.delta, tr.addr, tr.line, tr.is_python), views):
             c[a:a + len(x)].copy_(torch.from_numpy(x.view(v)))
@@ -357,100 +517,83 @@ def run_batched(args):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     ptr = [c.data_ptr() for c in cols]
-    segs = []
-    for i in range(ntr):
-        a, b = int(eo[i]), int(co[i])
-        segs.append(scl.segment(i, ptr[0] + 8 * a, ptr[1] + 8 * a, ptr[2] + 4 * a, ptr[3] + a,
-                                ptr[4] + 8 * b, ptr[5] + 4 * b, ptr[6] + b, n=int(lens[i]), m=int(mlen[i])))
+
+    def seg(i, p=ptr, e=eo, c=co):
+        a, b = int(e[i]), int(c[i])
+        return scl.segment(i, p[0] + 8 * a, p[1] + 8 * a, p[2] + 4 * a, p[3] + a, p[4] + 8 * b, p[5] + 4 * b,
+                           p[6] + b, n=int(lens[i]), m=int(mlen[i]))
+    segs = [seg(i) for i in range(ntr)]
     ctx = scl.scl_replay_init(scl.config(threshold=tg.T_PLAIN, n_lines=4096, max_traces=ntr,
-                                         sample_log_capacity=1 << 16))
+                                         sample_log_capacity=1 << 14))
     stream = torch.cuda.Stream()
     tuned = None
     if not args.no_tune:
+        t_tune = time.perf_counter()
         best, best_ms = scl.scl_autotune(ctx, segs, stream)
-        tuned = {"unit_events": best.unit_events, "sketch_warps": best.warps_per_block,
-                 "warmup_events": best.ext_events, "final_warps": best.final_warps, "ms": best_ms}
+        tuned = dict(tuning_dict(best, best_ms), seconds=time.perf_counter() - t_tune)
     scl.scl_graph_enable(ctx, True)
 
     def step():
         scl.scl_trace_reset(ctx, scl.SCL_ALL_TRACES, stream)
         scl.scl_replay_batch(ctx, segs, stream)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    scl.scl_sync(ctx)
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
-    if clocks:
-        clocks.warm(step, torch.cuda.synchronize)
-    barrier()
-    if clocks:
-        clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    barrier()
-    if clocks:
-        clocks.end()
-    clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1)
+    barrier = barrier_fn(ws)
+    ms, clk = timed(step, args.steps, args.warmup, stream, barrier, rank == 0 and not args.no_clocks)
     scl.scl_sync(ctx)
     value, tmax = job_throughput(ms, n_tot * args.steps, dev)
     bstats = scl.scl_batch_stats(ctx)
 
     # per-kernel times (profiling replaces the graph by plain launches) for the roofline
-    scl.scl_profile_reset(ctx)
-    scl.scl_profile_enable(ctx, True)
-    psteps = 2
-    for _ in range(psteps):
-        step()
-    scl.scl_profile_enable(ctx, False)
-    ktimes = scl.scl_kernel_times(ctx)
-    launches_per_step = sum(c for _, c in ktimes.values()) // psteps
-    roof = roofline_of(ktimes, n_tot, m_tot, traffic=False, sketch_n=n_tot - bstats["first_events"])
+    ktimes, launches_per_step = profile_steps(scl, ctx, step)
+    roof = roofline_of(ktimes, n_tot, m_tot, bstats["first_events"], traffic=True)
+    path_gbs = (EVENT_BYTES * n_tot + COPY_BYTES * m_tot) / (tmax / args.steps / 1e3) / 1e9
+    peak, peak_src = measured_peak()
 
-    # the plain per-trace path looped over the same traces on the same GPU
-    def loop_step():
-        scl.scl_trace_reset(ctx, scl.SCL_ALL_TRACES, stream)
-        for sg in segs:
-            scl.scl_replay_batch(ctx, [sg], stream)
+    # the plain per-trace path looped on the same GPU (one call per trace) over a stratified
+    # subset of 256 traces: that path's pace is set per call, so the subset stands for the batch
+    loop = None
+    if not args.no_loop:
+        sub = batched_sample(lens)[::2][:256]
+        sub_n = int(lens[sub].sum())
+        scl.scl_graph_enable(ctx, False)
 
-    scl.scl_graph_enable(ctx, False)
-    loop_step()
-    barrier()
-    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0.record(stream)
-    loop_step()
-    l1.record(stream)
-    barrier()
-    loop_ms = l0.elapsed_time(l1)
+        def loop_step():
+            scl.scl_trace_reset(ctx, scl.SCL_ALL_TRACES, stream)
+            for i in sub:
+                scl.scl_replay_batch(ctx, [segs[i]], stream)
+        loop_step()
+        barrier()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        loop_step()
+        l1.record(stream)
+        barrier()
+        loop_ms = l0.elapsed_time(l1)
+        loop = {"value": sub_n / (loop_ms / 1e3), "unit": "events/s", "ms": loop_ms, "calls": len(sub),
+                "events": sub_n, "sample": f"{len(sub)} traces spread over the length order, one call each"}
+        scl.scl_graph_enable(ctx, True)
 
-    # exactness and the oracle's pace on a sample of the traces (regenerated on the host)
+    # exactness and the oracle's pace on a stratified sample of the traces (regenerated on the host)
     cpu, parity = None, None
     if rank == 0 and not args.no_cpu:
         step()
         scl.scl_sync(ctx)
-        pick = sorted({0, 100, int(np.argmax(lens)), int(np.argmin(lens)), 1, ntr // 2, ntr - 1, (7 * ntr) // 9})
-        pick = [i for i in pick if i < ntr]
-        oks, el, ev = [], 0.0, 0
-        for i in pick:
-            tr = tg.batched_trace(i, int(lens[i]), seed=2 + rank)
-            t0 = time.perf_counter()
-            o = oracle_replay(tr, {"threshold": tg.T_PLAIN, "n_lines": 4096})
-            el += time.perf_counter() - t0
-            ev += int(lens[i])
-            oks.append(oracle_matches(ctx, i, o, scl))
-        cpu = {"value": ev / el, "unit": "events/s", "cores": 1, "kind": "oracle",
-               "sample": f"traces {pick} ({ev:,} events), sequential, {el:.1f} s"}
-        parity = f"bit-exact vs oracle on {len(pick)} sampled traces" if all(oks) else \
-            f"MISMATCH vs oracle on traces {[i for i, k in zip(pick, oks) if not k]}"
+        pick = batched_sample(lens)
+        trs = [t for _, t in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2 + rank), pick, host_cores())]
+        os_, walls, cores = oracle_parallel(trs, tg.T_PLAIN, 4096, reps=3)
+        ev = int(lens[pick].sum())
+        wall = statistics.median(walls)
+        cpu = {"value": ev / wall, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(pick)} of the batch's traces (512 evenly spaced by length + the leaking ones): "
+                         f"{ev:,} events + {int(mlen[pick].sum()):,} memcpys, one thread per core, median of "
+                         f"3 passes ({wall:.2f} s each)"}
+        full = set(parity_subset(lens, pick))
+        bad = [i for i, o in zip(pick, os_) if not full_match(ctx, i, o, scl, samples=i in full)]
+        parity = {"status": "bit-exact" if not bad else "MISMATCH", "traces": len(pick),
+                  "full_sample_arrays": len(full),
+                  "compared": "every sample record (all fields) of the shortest, longest, median, leaking and "
+                              "16 spread traces; per-line totals, leak scores and state of all sampled traces",
+                  "mismatched": bad[:20]}
 
     # end to end on a subset: pinned host arrays through scl_replay_batch_host
     e2e = None
@@ -459,9 +602,7 @@ def run_batched(args):
         hcols = [c[:int(eo[len(sub)])].cpu().pin_memory() for c in cols[:4]] + \
                 [c[:int(co[len(sub)])].cpu().pin_memory() for c in cols[4:]]
         hp = [c.data_ptr() for c in hcols]
-        hsegs = [scl.segment(i, hp[0] + 8 * int(eo[i]), hp[1] + 8 * int(eo[i]), hp[2] + 4 * int(eo[i]),
-                             hp[3] + int(eo[i]), hp[4] + 8 * int(co[i]), hp[5] + 4 * int(co[i]), hp[6] + int(co[i]),
-                             n=int(lens[i]), m=int(mlen[i])) for i in sub]
+        hsegs = [seg(i, hp) for i in sub]
         sub_n = int(lens[:len(sub)].sum())
         h2d = sum(int(lens[i]) * 21 + int(mlen[i]) * 13 for i in sub)
         d2h = len(sub) * 4096 * (scl.LINE_STAT_DTYPE.itemsize + scl.LEAK_DTYPE.itemsize)
@@ -487,22 +628,19 @@ def run_batched(args):
                          f"stats and leak scores of every trace out"}
 
     if rank == 0:
-        line = {"metric": "alloc/free events replayed per second (bit-exact)", "value": value, "unit": "events/s",
-                "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
-                "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": f"batched: {ntr:,} traces, {n_tot:,} events, {m_tot:,} memcpys, "
-                                       f"log-uniform 10k-4M, 4,096 lines, leak injection every 100th trace",
-                           "threshold": tg.T_PLAIN, "n_lines": 4096,
-                           "l2": f"inputs larger than L2 ({(21 * N + 13 * M) / 1e9:.0f} GB), no flush",
-                           "graph": "one scl_replay_batch per step, relaunched as a CUDA graph",
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        config = dict(batched_config(ntr, lens, mlen),
+                      parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
+        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": tmax / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": config,
+                "graph": "one scl_replay_batch per step, relaunched as a CUDA graph",
                 "tuning": tuned,
-                "per_trace_loop": {"value": n_tot / (loop_ms / 1e3), "unit": "events/s", "ms_per_step": loop_ms,
-                                   "calls_per_step": ntr},
-                "hbm_gbs_path": (PATH_BYTES_PER_EVENT * n_tot + PATH_BYTES_PER_COPY * m_tot) / (tmax / args.steps / 1e3) / 1e9,
+                "hbm_path": {"bytes_per_step": EVENT_BYTES * n_tot + COPY_BYTES * m_tot, "achieved": path_gbs,
+                             "peak": peak, "frac": path_gbs / peak, "unit": "GB/s", "peak_source": peak_src,
+                             "alg_bytes": "21 B per event + 13 B per memcpy"},
                 "roofline": dict(roof, measured="per-kernel CUDA events over 2 profiled steps after the timed region"),
-                "kernels_ms_per_step": {k: v[0] / psteps for k, v in ktimes.items()},
+                "per_trace_loop": loop,
+                "kernels_ms_per_step": {k: v[0] / 2 for k, v in ktimes.items()},
                 "gpu_launches": launches_per_step * args.steps, "batch": bstats,
                 "generation_s": t_gen, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "parity": parity}
         print(json.dumps(line), flush=True)
@@ -512,21 +650,108 @@ def run_batched(args):
     return 0
 
 
+def sweep_config(per, n):
+    return {"workload": f"sweep: {per:,} traces x {n:,} events at each of 4 thresholds (4 GiB mallocs, "
+                        f"adversarial +-(T-1), malloc-only 4 KiB, 70% frees)",
+            "thresholds": [1, 1_048_573, 10_485_767, 104_857_601], "n_lines": 256, "memcpys_per_trace": n // 10,
+            "l2": f"inputs larger than L2 ({per * n * 21 / 1e9:.0f} GB per threshold), no flush"}
+
+
+def run_sweep(args):
+    """The threshold sweep: for each T a batch of 1,024 traces of 1M events in four families,
+    one scl_replay_batch each; a step replays the four batches (one resident at a time, each
+    timed over the same K steps, summed)."""
+    import torch
+    from paper_2212_07597_gb300 import tracegen as tg
+    ws, rank, scl = init_dist_and_lib()
+    per, n = args.traces or 1024, args.events or 1_000_000
+    m = n // 10
+    dev = torch.device("cuda", torch.cuda.current_device())
+    barrier = barrier_fn(ws)
+    total_ms, per_T, clk, launches, bad, t_gen = 0.0, {}, None, 0, [], 0.0
+    pick = list(range(0, per, max(1, per // 64)))[:64]
+    ocpu_ev, ocpu_wall, cores = 0, 0.0, 1
+    for T in tg.SWEEP_THRESHOLDS:
+        cols = [torch.empty(per * n, dtype=torch.int64, device=dev), torch.empty(per * n, dtype=torch.int64, device=dev),
+                torch.empty(per * n, dtype=torch.int32, device=dev), torch.empty(per * n, dtype=torch.uint8, device=dev),
+                torch.empty(per * m, dtype=torch.int64, device=dev), torch.empty(per * m, dtype=torch.int32, device=dev),
+                torch.empty(per * m, dtype=torch.uint8, device=dev)]
+        t0 = time.perf_counter()
+        for i, tr in chunked(lambda i: tg.sweep_trace(i, T, n=n, seed=3 + rank), list(range(per)), min(32, host_cores())):
+            for c, x, v in zip(cols, (tr.delta, tr.addr, tr.line, tr.is_python, tr.csize, tr.cline, tr.cpy),
+                               (np.int64, np.int64, np.int32, np.uint8, np.int64, np.int32, np.uint8)):
+                k = n if c.numel() == per * n else m
+                c[i * k:(i + 1) * k].copy_(torch.from_numpy(x.view(v)))
+        torch.cuda.synchronize()
+        t_gen += time.perf_counter() - t0
+        p = [c.data_ptr() for c in cols]
+        segs = [scl.segment(i, p[0] + 8 * i * n, p[1] + 8 * i * n, p[2] + 4 * i * n, p[3] + i * n,
+                            p[4] + 8 * i * m, p[5] + 4 * i * m, p[6] + i * m, n=n, m=m) for i in range(per)]
+        ctx = scl.scl_replay_init(scl.config(threshold=T, n_lines=256, max_traces=per))
+        stream = torch.cuda.Stream()
+        tuned = None
+        if not args.no_tune:
+            best, best_ms = scl.scl_autotune(ctx, segs, stream)
+            tuned = tuning_dict(best, best_ms)
+        scl.scl_graph_enable(ctx, True)
+
+        def step():
+            scl.scl_trace_reset(ctx, scl.SCL_ALL_TRACES, stream)
+            scl.scl_replay_batch(ctx, segs, stream)
+        ms, c = timed(step, args.steps, args.warmup, stream, barrier, rank == 0 and not args.no_clocks and T == 1)
+        clk = clk or c
+        scl.scl_sync(ctx)
+        kt, lps = profile_steps(scl, ctx, step, 1)
+        launches += lps * args.steps
+        total_ms += ms
+        bst = scl.scl_batch_stats(ctx)
+        per_T[str(T)] = {"ms_per_step": ms / args.steps, "events_per_s": per * n * args.steps / (ms / 1e3),
+                         "tuning": tuned, "walked_units": bst["walked"], "searched_units": bst["searched"],
+                         "kernels_ms": {k: v[0] for k, v in kt.items()}}
+        if rank == 0 and not args.no_cpu:
+            step()
+            scl.scl_sync(ctx)
+            trs = [tg.sweep_trace(i, T, n=n, seed=3 + rank) for i in pick]
+            os_, walls, cores = oracle_parallel(trs, T, 256)
+            ocpu_ev += len(pick) * n
+            ocpu_wall += walls[0]
+            bad += [(T, i) for i, o in zip(pick, os_) if not full_match(ctx, i, o, scl, samples=False)]
+        del ctx, cols
+        torch.cuda.empty_cache()
+    value, tmax = job_throughput(total_ms, 4 * per * n * args.steps, dev)
+    if rank == 0:
+        config = dict(sweep_config(per, n), parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
+        cpu = None if args.no_cpu else {
+            "value": ocpu_ev / ocpu_wall, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(pick)} traces of each threshold's batch (every {per // len(pick)}th), one thread per core"}
+        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": tmax / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": config,
+                "per_threshold": per_T, "gpu_launches": launches, "generation_s": t_gen, "clocks": clk,
+                "cpu_baseline": cpu,
+                "parity": None if args.no_cpu else {
+                    "status": "bit-exact" if not bad else "MISMATCH", "traces": 4 * len(pick),
+                    "compared": "per-line totals, leak scores, resident state and sample counts (the full sample "
+                                "arrays at this size are compared by tests/test_gpu_sweep.py)",
+                    "mismatched": bad[:20]},
+                "e2e": None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def serving_config(P, S, L):
+    return {"workload": f"serving: {P} processes x {S} segments of {L:,} events ({P * S * L:,} events, "
+                        f"{P * S * L // 10:,} memcpys), 1,024 lines, leak injection in 10%",
+            "threshold": 10_485_767, "n_lines": 1024, "arrivals": "Poisson, 2M segments/min (mean gap 30 us)",
+            "l2": "inputs copied from pinned host memory every step (larger than L2), no flush"}
+
+
 def run_serving(args):
     """512 processes pushing 64k-event segments, Poisson arrivals at 2M segments/min, served
     by scl_serve (continuous batching, copies overlapped with replay, state resident)."""
     import torch
-    from paper_2212_07597_gb300 import build as scl_build
     from paper_2212_07597_gb300 import tracegen as tg
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    scl_build.build()
-    from paper_2212_07597_gb300 import scl
+    ws, rank, scl = init_dist_and_lib()
     P, S, L = args.procs or 512, args.segs or 16, args.events or 65536
     NL = 1024
     n_p = S * L
@@ -539,8 +764,8 @@ def run_serving(args):
     hn = [c.numpy() for c in hcols]
     t_gen = time.perf_counter()
     seed = 4 + rank
-    workers = min(32, os.cpu_count() or 4)
-    for p, tr in chunked(lambda p: tg.serving_process(p, n_p, seed=seed, n_lines=NL), list(range(P)), workers):
+    for p, tr in chunked(lambda p: tg.serving_process(p, n_p, seed=seed, n_lines=NL), list(range(P)),
+                         min(32, host_cores())):
         for h, x in zip(hn[:4], (tr.delta, tr.addr, tr.line, tr.is_python)):
             h[p * n_p:(p + 1) * n_p] = x.view(h.dtype)
         for h, x in zip(hn[4:], (tr.csize, tr.cline, tr.cpy)):
@@ -572,12 +797,7 @@ def run_serving(args):
         scl.scl_sync(ctx)
         return scl.scl_serve(ctx, reqs, realtime=realtime)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
+    barrier = barrier_fn(ws)
     for _ in range(max(3, args.warmup)):
         serve(False)
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
@@ -608,44 +828,34 @@ def run_serving(args):
     wall = sum(walls)
     value, tmax = job_throughput(wall * 1e3, N * args.steps, "cuda")
 
-    # per-kernel times of one saturated pass for the roofline (profiling on)
+    # per-kernel times of one saturated pass (profiling on)
     scl.scl_profile_reset(ctx)
     scl.scl_profile_enable(ctx, True)
     serve(False)
     scl.scl_profile_enable(ctx, False)
     ktimes = scl.scl_kernel_times(ctx)
     nb = max(1, ktimes.get("final", (0, 1))[1])
-    roof = roofline_of({k: v for k, v in ktimes.items()}, N // nb, M // nb, traffic=False)
+    first_per_batch = min(P, 256) * 65536   # a batch's first units, at most one per process
+    roof = roofline_of(ktimes, N, M, min(N, first_per_batch * nb), traffic=False)
 
     cpu, parity = None, None
     if rank == 0 and not args.no_cpu:
         serve(False)
-        pick = sorted({0, 1, 10, P // 2, P - 1, (3 * P) // 7})
-        pick = [p for p in pick if p < P]
-        oks, el = [], 0.0
-        for p in pick:
-            tr = tg.serving_process(p, n_p, seed=seed, n_lines=NL)
-            t0 = time.perf_counter()
-            o = oracle_replay(tr, {"threshold": tg.T_PLAIN, "n_lines": NL})
-            el += time.perf_counter() - t0
-            oks.append(oracle_matches(ctx, p, o, scl))
-        cpu = {"value": len(pick) * n_p / el, "unit": "events/s", "cores": 1, "kind": "oracle",
-               "sample": f"processes {pick} ({len(pick) * n_p:,} events), sequential, {el:.1f} s"}
-        parity = f"bit-exact vs oracle on {len(pick)} sampled processes" if all(oks) else \
-            f"MISMATCH vs oracle on processes {[p for p, k in zip(pick, oks) if not k]}"
+        pick = list(range(0, P, 8))
+        trs = [tg.serving_process(p, n_p, seed=seed, n_lines=NL) for p in pick]
+        os_, walls_o, cores = oracle_parallel(trs, tg.T_PLAIN, NL)
+        bad = [p for p, o in zip(pick, os_) if not full_match(ctx, p, o, scl, samples=p % 64 == 0)]
+        cpu = {"value": len(pick) * n_p / walls_o[0], "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(pick)} of {P} processes ({len(pick) * n_p:,} events), one thread per core"}
+        parity = {"status": "bit-exact" if not bad else "MISMATCH", "traces": len(pick), "mismatched": bad[:20],
+                  "compared": "per-line totals, leak scores, state; full sample arrays of every 64th process"}
 
     if rank == 0:
         h2d = 17 * N + 13 * M   # the event line column is read in place (pinned), not moved
-        line = {"metric": "alloc/free events replayed per second (bit-exact)", "value": value, "unit": "events/s",
-                "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
-                "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": f"serving: {P} processes x {S} segments of {L:,} events "
-                                       f"({N:,} events, {M:,} memcpys), 1,024 lines, leak injection in 10%",
-                           "threshold": tg.T_PLAIN, "n_lines": NL,
-                           "arrivals": "Poisson, 2M segments/min (mean gap 30 us)",
-                           "l2": "inputs copied from pinned host memory every step (larger than L2), no flush",
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        config = dict(serving_config(P, S, L), parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
+        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": tmax / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": config,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "max": float(lat.max()), "requests": int(lat.size),
                                "offered_events_per_s": L * 2e6 / 60,
@@ -653,8 +863,7 @@ def run_serving(args):
                                "batches_per_pass": float(np.mean(rt_batches))},
                 "saturated_batches_per_pass": float(np.mean(batches)),
                 "roofline": dict(roof, measured="per-kernel CUDA events over one profiled saturated pass",
-                                 note="units = a batch's events on average; the traces' first units of each "
-                                      "batch go to k_first instead, so this is an upper bound"),
+                                 note="first units counted as at most one 64k segment per process per batch"),
                 "kernels_ms_per_pass": {k: v[0] for k, v in ktimes.items()},
                 "gpu_launches": int(sum(c for _, c in ktimes.values())) * args.steps,
                 "generation_s": t_gen, "clocks": clk,
@@ -669,26 +878,27 @@ def run_serving(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "serving":
-        return run_serving(args)
-    import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+def make_trace(workload: str, rank: int, n_override: int = 0):
+    from paper_2212_07597_gb300 import tracegen as tg
+    if workload == "long_256m":
+        n = n_override or (1 << 28)
+        tr = tg.long_trace(n, seed=1 + rank)
+        name = f"single long trace, {n:,} events"
     else:
-        torch.cuda.set_device(0)
-    from paper_2212_07597_gb300 import build as scl_build
-    scl_build.build()
-    from paper_2212_07597_gb300 import scl
+        n = n_override or 1_000_000
+        tr = tg.plain_trace(n, seed=rank)
+        name = f"plain trace, {n:,} events"
+    m = len(tr.csize)
+    config = {"workload": name, "threshold": tg.T_PLAIN, "n_lines": 256, "memcpys": m,
+              "l2": f"inputs larger than L2 ({(EVENT_BYTES * n + COPY_BYTES * m) / 1e9:.1f} GB per step), no flush"
+              if n >= 1 << 24 else "inputs smaller than L2, so no flush is claimed: a lower bound of HBM time"}
+    return tr, {"events": n, "threshold": tg.T_PLAIN, "n_lines": 256, "config": config}
 
+
+def run_single(args):
+    """One trace (long_256m or plain_1m), one scl_replay_batch per step."""
+    import torch
+    ws, rank, scl = init_dist_and_lib()
     tr, meta = make_trace(args.workload, rank, args.events)
     n, m = meta["events"], len(tr.csize)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -699,76 +909,22 @@ def main():
     tuned = None
     if args.tune:
         best, best_ms = scl.scl_autotune(ctx, [seg], stream)
-        tuned = {"unit_events": best.unit_events, "sketch_warps": best.warps_per_block,
-                 "warmup_events": best.ext_events, "final_warps": best.final_warps, "ms": best_ms}
+        tuned = tuning_dict(best, best_ms)
 
     def step():
         scl.scl_trace_reset(ctx, 0, stream)
         scl.scl_replay_batch(ctx, [seg], stream)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
-        step()
-    scl.scl_sync(ctx)
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
-    if clocks:
-        clocks.warm(step, torch.cuda.synchronize)
-    scl.scl_sync(ctx)
-    scl.scl_profile_reset(ctx)
-    scl.scl_profile_enable(ctx, True)
-    barrier()
-    if clocks:
-        clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    barrier()
-    if clocks:
-        clocks.end()
-    clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1)
-    scl.scl_profile_enable(ctx, False)
-    ktimes = scl.scl_kernel_times(ctx)
+    barrier = barrier_fn(ws)
+    ms, clk = timed(step, args.steps, args.warmup, stream, barrier, rank == 0 and not args.no_clocks)
     scl.scl_sync(ctx)
     bstats = scl.scl_batch_stats(ctx)
-
     value, tmax = job_throughput(ms, n * args.steps, dev)
+    ktimes, launches_per_step = profile_steps(scl, ctx, step)
+    roof = roofline_of(ktimes, n, m, bstats["first_events"])
+    peak, peak_src = measured_peak()
+    path_gbs = (EVENT_BYTES * n + COPY_BYTES * m) * args.steps / (ms / 1e3) / 1e9
 
-    # dominant kernel and its roofline
-    launches = sum(c for _, c in ktimes.values())
-    dom = max((k for k in ktimes if k in EVENT_KERNELS), key=lambda k: ktimes[k][0])   # see roofline_of
-    d_ms, d_cnt = ktimes[dom]
-    per_launch_units = n if dom in EVENT_KERNELS else m
-    if dom in EVENT_KERNELS:   # the trace's first unit is replayed exactly by k_first instead
-        per_launch_units = n - bstats["first_events"]
-    alg = ALG_BYTES[dom] * per_launch_units
-    achieved = alg / (d_ms / d_cnt / 1e3) / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "of measured" if peak else "of fallback"
-    peak = peak or 6800.0
-    path_gbs = (PATH_BYTES_PER_EVENT * n + PATH_BYTES_PER_COPY * m) * args.steps / (ms / 1e3) / 1e9
-    # both event-path kernels (the dominant one above, and the other), same arithmetic
-    ev_roof = {}
-    for k in EVENT_KERNELS:
-        if k in ktimes and ktimes[k][1]:
-            u = n - bstats["first_events"]
-            a_k = ALG_BYTES[k] * u / (ktimes[k][0] / ktimes[k][1] / 1e3) / 1e9
-            ev_roof[k] = {"ms": ktimes[k][0] / ktimes[k][1], "achieved": a_k, "frac": a_k / peak,
-                          "traffic": traffic_for(k, u, bstats["sketch_events"])}
-
-    # end to end through the host entry point
     e2e = None
     if not args.no_e2e:
         pins = [torch.from_numpy(a).pin_memory() for a in (tr.delta, tr.addr, tr.line, tr.is_python, tr.csize,
@@ -825,55 +981,43 @@ def main():
                 "note": "rate-based sampling (Section 3.2 baseline) on the same trace; ms includes "
                         "the synchronising read-back of the counts"}
 
-    # oracle on this host: timed baseline and exact check of the last GPU step
-    cpu = None
-    parity = None
+    # the oracle on this host (one trace is sequential: one core) and the exact check of the
+    # last GPU step: every sample record, the line totals, leak scores and state
+    cpu, parity = None, None
     if rank == 0 and not args.no_cpu:
         step()
         scl.scl_sync(ctx)
         t0 = time.perf_counter()
-        o = oracle_replay(tr, meta)
+        o = oracle_replay(tr, meta["threshold"], meta["n_lines"])
         el = time.perf_counter() - t0
         cpu = {"value": n / el, "unit": "events/s", "cores": 1, "kind": "oracle",
                "sample": f"whole {n:,}-event trace (+{m:,} memcpys), one sequential pass, {el:.1f} s"}
-        gl, wl = scl.scl_line_stats(ctx, 0), o.lines()
-        lk = scl.scl_leak_scores(ctx, 0)
-        num, den = o.leak_scores()
-        st, ost = scl.scl_trace_state(ctx, 0), o.state()
-        ok = all(np.array_equal(gl[k], wl[k]) for k in ("n_growth", "n_shrink", "A", "F", "A_py", "F_py", "net",
-                                                         "copy_samples", "copy_bytes"))
-        ok = ok and np.array_equal(lk["mallocs"], wl["mallocs"]) and np.array_equal(lk["frees"], wl["frees"])
-        ok = ok and np.array_equal(lk["num"], num) and np.array_equal(lk["den"], den)
-        ok = ok and all(st[k] == ost[k] for k in ("c", "A", "F", "footprint", "hwm", "n_events", "copy_counter"))
-        ok = ok and st["n_samples"] == len(o.samples())
-        parity = "bit-exact vs oracle" if ok else "MISMATCH vs oracle"
+        ok = full_match(ctx, 0, o, scl, samples=True)
+        parity = {"status": "bit-exact" if ok else "MISMATCH", "samples": len(o.samples()),
+                  "compared": "every sample record (all fields), per-line totals, leak scores, state"}
 
     if rank == 0:
-        line = {"metric": "alloc/free events replayed per second (bit-exact)", "value": value, "unit": "events/s",
-                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-                "data": "synthetic",
-                "config": {"workload": meta["workload"], "threshold": meta["threshold"], "n_lines": meta["n_lines"],
-                           "memcpys": m,
-                           "l2": f"inputs larger than L2 ({(PATH_BYTES_PER_EVENT * n + PATH_BYTES_PER_COPY * m) / 1e9:.1f} GB "
-                                 "per step), no flush",
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-                "hbm_gbs_path": path_gbs,
-                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_source": peak_src,
-                             "traffic": traffic_for(dom, per_launch_units, bstats["sketch_events"]),
-                             "alg_bytes_per_unit": ALG_BYTES[dom]},
-                "roofline_event_kernels": ev_roof,
-                "kernels_ms_per_step": {k: v[0] / max(1, v[1]) * (v[1] / args.steps) for k, v in ktimes.items()},
-                "tuning": tuned,
-                "gpu_launches": launches,
-                "batch": bstats,
+        config = dict(meta["config"], parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
+        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": tmax / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": config,
+                "hbm_path": {"achieved": path_gbs, "peak": peak, "frac": path_gbs / peak, "unit": "GB/s",
+                             "peak_source": peak_src, "alg_bytes": "21 B per event + 13 B per memcpy"},
+                "roofline": roof, "kernels_ms_per_step": {k: v[0] / 2 for k, v in ktimes.items()},
+                "tuning": tuned, "gpu_launches": launches_per_step * args.steps, "batch": bstats,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "rate_based": rate}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return {"batched": run_batched, "sweep": run_sweep, "serving": run_serving}.get(args.workload, run_single)(args)
 
 
 if __name__ == "__main__":

@@ -96,9 +96,14 @@ typedef struct {
     uint64_t spin_limit;          /* iterations before a device wait reports SCL_ETIMEOUT (0: 1<<26) */
     uint64_t sample_log_capacity; /* samples kept per trace for scl_samples (0: keep none) */
     uint32_t sample_budget_shift; /* record space per work unit = (events >> shift) + 64; 0 never
-                                     overflows (needed when T is tiny), default 4 */
+                                     overflows; default SCL_BUDGET_AUTO: floor(log2 T) - 16, clamped
+                                     to 0..4 (0 for T < 2^17, so T = 1 never overflows); a batch whose
+                                     records overflow returns SCL_EOVERFLOW, and the context doubles the
+                                     space of later batches (shift - 1, down to 0) */
     uint32_t unit_events;         /* events per work unit (multiple of 1024; 0: one unit per resident warp) */
 } scl_config;
+
+#define SCL_BUDGET_AUTO 0xffffffffu   /* sample_budget_shift picked from T */
 
 /* Fill *cfg with the defaults listed above. */
 int scl_config_default(scl_config *cfg);
@@ -227,12 +232,15 @@ int scl_state_import(scl_ctx *ctx, uint32_t trace, const void *buf, uint64_t n);
 #define SCL_ALL_TRACES 0xffffffffu
 int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
 
-/* Tuning: events per work unit, warps per block of the sketch and of the exact replay,
- * warm-up events.  scl_autotune times scl_replay_batch on the given segments (median of
- * three after a warm-up run) for 32 candidate settings (units 0/64k/128k/256k, replay
- * warps 10/14, sketch warps 8/16, warm-up 16k/32k), restoring the touched traces' state
- * before every run and at the end; it keeps the fastest setting in the context (read it
- * back with scl_tuning_get).  It allocates one device buffer for the saved states. */
+/* Tuning: events per work unit (the chunk of a trace whose entering counter the sketch
+ * speculates), first-unit length, warps per block of phase 1 and of the exact replay,
+ * warm-up events, fix-up strategy.  scl_autotune times scl_replay_batch on the given
+ * segments (median of three after a warm-up run) and searches one setting at a time,
+ * twice over: unit 32k/64k/128k/256k/512k, first unit unit/512k/1M/1.25M/1.5M, phase-1
+ * warps 8/12/16, replay warps 10/14, warm-up 16k/32k, fix-up 0/1.  It restores the
+ * touched traces' state before every run and at the end, keeps the fastest setting in the
+ * context (read it back with scl_tuning_get), and allocates one device buffer for the
+ * saved states. */
 typedef struct {
     uint32_t unit_events;    /* events per work unit (multiple of 1024; 0 = one unit per resident warp) */
     uint32_t warps_per_block;/* sketch warps per thread block (1..16) */
@@ -241,6 +249,9 @@ typedef struct {
     uint32_t first_events;   /* length of each trace's first unit, replayed exactly in one pass from the
                                 trace's resident state (multiple of 1024; 0 = unit_events); with fewer
                                 traces than SMs a first unit is one warm-up long instead */
+    uint32_t fixup;          /* how the exact replay of a sketched unit finds its samples once its entry is
+                                known: 0 = from every reset the sketch listed for that run (default),
+                                1 = by searching each step's prefix sums for crossings */
 } scl_tuning;
 int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);

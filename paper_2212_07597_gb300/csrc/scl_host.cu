@@ -33,6 +33,7 @@ struct ProfEntry {
 
 struct scl_ctx {
     scl_config cfg{};
+    uint32_t shift = 4;   // record budget in effect (cfg.sample_budget_shift, resolved and grown)
     int device = 0;
     int num_sms = 0;
     std::string err;
@@ -183,6 +184,8 @@ int check_device_error(scl_ctx *c) {
         return fail(c, SCL_EINTERNAL, "internal consistency check failed (site %u, %llu)", w.detail0,
                     (unsigned long long)w.detail1);
     case E_OVERFLOW:
+        // a unit's records did not fit: give later batches twice the space
+        if (w.detail0 == 3 && c->shift > 0) --c->shift;
         return fail(c, SCL_EOVERFLOW,
                     "record space overflow or uint64 copy-count overflow (site %u, unit/tile %llu); "
                     "lower sample_budget_shift", w.detail0, (unsigned long long)w.detail1);
@@ -413,7 +416,7 @@ int scl_config_default(scl_config *cfg) {
     cfg->leak_rule = 0;
     cfg->spin_limit = 0;
     cfg->sample_log_capacity = 0;
-    cfg->sample_budget_shift = 4;
+    cfg->sample_budget_shift = SCL_BUDGET_AUTO;
     cfg->unit_events = 0;
     return SCL_OK;
 }
@@ -458,7 +461,8 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     c->cfg = *cfg_in;
     scl_config &cfg = c->cfg;
     if (cfg.threshold < 1 || cfg.copy_multiple < 1 || cfg.n_lines == 0 || cfg.max_traces == 0 ||
-        cfg.leak_rule > 1 || cfg.sample_budget_shift > 20 || (cfg.unit_events % UNIT_ALIGN) != 0) {
+        cfg.leak_rule > 1 || (cfg.sample_budget_shift > 20 && cfg.sample_budget_shift != SCL_BUDGET_AUTO) ||
+        (cfg.unit_events % UNIT_ALIGN) != 0) {
         int r = fail(c, SCL_EINVAL, "invalid config (threshold >= 1, copy_multiple >= 1, n_lines >= 1, "
                                     "max_traces >= 1, leak_rule in {0,1}, unit_events multiple of 1024)");
         scl_replay_free(c);
@@ -471,6 +475,14 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
         return r;
     }
     if (cfg.spin_limit == 0) cfg.spin_limit = 1ull << 26;
+    if (cfg.sample_budget_shift == SCL_BUDGET_AUTO) {
+        // a sample needs |A - F| >= T, so the smaller T, the denser the samples can be
+        int lg = 0;
+        while (lg < 62 && (int64_t(1) << (lg + 1)) <= cfg.threshold) ++lg;
+        c->shift = (uint32_t)std::min(4, std::max(0, lg - 16));
+    } else {
+        c->shift = cfg.sample_budget_shift;
+    }
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     const size_t L = cfg.n_lines, NTr = cfg.max_traces;
@@ -530,9 +542,11 @@ int scl_tuning_get(const scl_ctx *c, scl_tuning *out) {
 int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
     if (!c || !t) return SCL_EINVAL;
     if (t->unit_events % UNIT_ALIGN || t->first_events % UNIT_ALIGN || t->warps_per_block < 1 ||
-        t->warps_per_block > 16 || t->final_warps < 1 || t->final_warps > 14 || (t->ext_events % 256))
+        t->warps_per_block > 16 || t->final_warps < 1 || t->final_warps > 14 || (t->ext_events % 256) ||
+        t->fixup > 1)
         return fail(c, SCL_EINVAL, "tuning: unit_events and first_events multiples of 1024 (0: default), "
-                                   "warps_per_block 1..16, final_warps 1..14, ext_events multiple of %d", 256);
+                                   "warps_per_block 1..16, final_warps 1..14, ext_events multiple of %d, fixup 0/1",
+                    256);
     c->tune = *t;
     return SCL_OK;
 }
@@ -591,7 +605,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         UE = std::max<uint64_t>(UE, 32768);
         UE = std::min<uint64_t>(UE, 1ull << 22);
     }
-    const uint32_t shift = cfg.sample_budget_shift;
+    const uint32_t shift = c->shift;
     std::vector<Unit> units;
     std::vector<BTrace> bts(nbt);
     std::vector<CompactGroup> cgroups;
@@ -633,7 +647,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 // reset lists: one reset per 32 events covers the thresholds worth listing;
                 // a run with more resets leaves its unit to the crossing search
                 U.lst0 = lst_total;
-                U.lst_cap = (uint32_t)((U.len >> 5) + 64);
+                // (a first unit is replayed exactly in phase 1 and needs none)
+                U.lst_cap = c->tune.fixup || units.size() == B.u0 ? 0u : (uint32_t)((U.len >> 5) + 64);
                 units.push_back(U);
                 gidx += U.len;
                 rec_total += U.rec_cap;
@@ -1171,27 +1186,39 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     // save the resident state of every trace the segments touch; restore it after each trial
+    // (traces with consecutive ids are copied as one range)
     std::vector<uint32_t> tr;
     for (uint32_t i = 0; i < nsegs; ++i)
-        if (segs[i].trace_id < c->cfg.max_traces &&
-            std::find(tr.begin(), tr.end(), segs[i].trace_id) == tr.end())
-            tr.push_back(segs[i].trace_id);
+        if (segs[i].trace_id < c->cfg.max_traces) tr.push_back(segs[i].trace_id);
+    std::sort(tr.begin(), tr.end());
+    tr.erase(std::unique(tr.begin(), tr.end()), tr.end());
+    std::vector<std::pair<uint32_t, uint32_t>> ranges;   // (first trace, count)
+    for (uint32_t t : tr) {
+        if (!ranges.empty() && ranges.back().first + ranges.back().second == t) ++ranges.back().second;
+        else ranges.push_back({t, 1});
+    }
     const size_t L = c->cfg.n_lines;
-    const size_t per = sizeof(DevTrace) + sizeof(LineRow) * L;
     void *save = nullptr;
-    CK(cudaMalloc(&save, per * std::max<size_t>(1, tr.size())), "autotune state copy");
+    const size_t nt = std::max<size_t>(1, tr.size());
+    CK(cudaMalloc(&save, (sizeof(DevTrace) + sizeof(LineRow) * L) * nt), "autotune state copy");
+    DevTrace *save_t = static_cast<DevTrace *>(save);
+    LineRow *save_l = reinterpret_cast<LineRow *>(save_t + nt);
     std::vector<uint64_t> h_ev(tr.size());
     auto copy_state = [&](bool to_save) -> cudaError_t {
-        for (size_t i = 0; i < tr.size(); ++i) {
-            char *b = static_cast<char *>(save) + i * per;
-            DevTrace *t = c->traces + tr[i];
-            LineRow *l = c->lines + (size_t)tr[i] * L;
-            cudaError_t e = to_save ? cudaMemcpyAsync(b, t, sizeof(DevTrace), cudaMemcpyDeviceToDevice, s)
-                                    : cudaMemcpyAsync(t, b, sizeof(DevTrace), cudaMemcpyDeviceToDevice, s);
+        size_t k = 0;
+        for (const auto &r : ranges) {
+            DevTrace *t = c->traces + r.first;
+            LineRow *l = c->lines + (size_t)r.first * L;
+            const size_t bt = sizeof(DevTrace) * r.second, bl = sizeof(LineRow) * L * r.second;
+            cudaError_t e = to_save ? cudaMemcpyAsync(save_t + k, t, bt, cudaMemcpyDeviceToDevice, s)
+                                    : cudaMemcpyAsync(t, save_t + k, bt, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess)
-                e = to_save ? cudaMemcpyAsync(b + sizeof(DevTrace), l, sizeof(LineRow) * L, cudaMemcpyDeviceToDevice, s)
-                            : cudaMemcpyAsync(l, b + sizeof(DevTrace), sizeof(LineRow) * L, cudaMemcpyDeviceToDevice, s);
+                e = to_save ? cudaMemcpyAsync(save_l + k * L, l, bl, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpyAsync(l, save_l + k * L, bl, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
+            k += r.second;
+        }
+        for (size_t i = 0; i < tr.size(); ++i) {
             if (to_save) h_ev[i] = c->h_events[tr[i]];
             else c->h_events[tr[i]] = h_ev[i];
         }
@@ -1207,37 +1234,51 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     scl_tuning best = keep;
     double best_ms = 1e300;
     int rc = copy_state(true) == cudaSuccess ? SCL_OK : SCL_ECUDA;
-    const uint32_t units[] = {0, 65536, 131072, 262144};
+    // one timed setting: median of three runs after a warm-up run, each from the saved state
+    std::vector<std::pair<scl_tuning, double>> seen;
+    auto measure = [&](const scl_tuning &t) -> double {
+        for (const auto &p : seen)
+            if (memcmp(&p.first, &t, sizeof t) == 0) return p.second;
+        c->tune = t;
+        std::vector<float> ts;
+        for (int rep = 0; rep < 4 && !rc; ++rep) {
+            if (copy_state(false) != cudaSuccess) { rc = SCL_ECUDA; break; }
+            cudaEventRecord(e0, s);
+            rc = scl_replay_batch(c, segs, nsegs, stream);
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SCL_ECUDA; break; }
+            if ((rc = check_device_error(c))) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ts.push_back(ms);   // the first run warms up
+        }
+        if (rc) return 1e300;
+        std::sort(ts.begin(), ts.end());
+        const double med = ts[ts.size() / 2];
+        seen.push_back({t, med});
+        if (med < best_ms) { best_ms = med; best = t; }
+        return med;
+    };
+    // coordinate descent, two passes: each setting in turn takes its best value with the
+    // others held at the best found so far
+    const uint32_t units[] = {32768, 65536, 131072, 262144, 524288};
+    const uint32_t firsts[] = {0, 524288, 1048576, 1310720, 1572864};
+    const uint32_t pwarps[] = {8, 12, (uint32_t)PHASE1_MAX_WARPS};
     const uint32_t fwarps[] = {10, 14};
-    const uint32_t swarps[] = {8, (uint32_t)PHASE1_MAX_WARPS};
     const uint32_t warm[] = {16384, 32768};
-    for (uint32_t ue : units)
-        for (uint32_t fw : fwarps)
-            for (uint32_t sw : swarps)
-                for (uint32_t wm : warm) {
-                    if (rc) break;
-                    c->tune.unit_events = ue;
-                    c->tune.final_warps = fw;
-                    c->tune.warps_per_block = sw;
-                    c->tune.ext_events = wm;
-                    std::vector<float> ts;
-                    for (int rep = 0; rep < 4 && !rc; ++rep) {
-                        if (copy_state(false) != cudaSuccess) { rc = SCL_ECUDA; break; }
-                        cudaEventRecord(e0, s);
-                        rc = scl_replay_batch(c, segs, nsegs, stream);
-                        cudaEventRecord(e1, s);
-                        if (rc) break;
-                        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SCL_ECUDA; break; }
-                        if ((rc = check_device_error(c))) break;
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep > 0) ts.push_back(ms);   // the first run warms up
-                    }
-                    if (rc) break;
-                    std::sort(ts.begin(), ts.end());
-                    const double med = ts[ts.size() / 2];
-                    if (med < best_ms) { best_ms = med; best = c->tune; }
-                }
+    const uint32_t fixups[] = {0, 1};
+    scl_tuning start = keep;
+    if (start.ext_events == 0) start.ext_events = 32768;
+    measure(start);
+    for (int pass = 0; pass < 2 && !rc; ++pass) {
+        for (uint32_t v : units) { scl_tuning t = best; t.unit_events = v; if (!rc) measure(t); }
+        for (uint32_t v : firsts) { scl_tuning t = best; t.first_events = v; if (!rc) measure(t); }
+        for (uint32_t v : pwarps) { scl_tuning t = best; t.warps_per_block = v; if (!rc) measure(t); }
+        for (uint32_t v : fwarps) { scl_tuning t = best; t.final_warps = v; if (!rc) measure(t); }
+        for (uint32_t v : warm) { scl_tuning t = best; t.ext_events = v; if (!rc) measure(t); }
+        for (uint32_t v : fixups) { scl_tuning t = best; t.fixup = v; if (!rc) measure(t); }
+    }
     if (copy_state(false) != cudaSuccess && !rc) rc = SCL_ECUDA;
     cudaStreamSynchronize(s);
     cudaEventDestroy(e0);

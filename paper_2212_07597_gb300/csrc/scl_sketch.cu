@@ -158,7 +158,7 @@ __device__ bool sketch_unit(SketchRing &sm, uint32_t &phase, int u, const Unit *
     const bool active = leader == lane;
     // the first NL distinct runs record every reset (for the exact replay)
     const uint32_t rank = (uint32_t)__popc(__ballot_sync(FULL, active) & ((1u << lane) - 1u));
-    const uint32_t myslot = active && rank < (uint32_t)NL ? rank : NO_LIST;
+    const uint32_t myslot = active && rank < (uint32_t)NL && U.lst_cap ? rank : NO_LIST;
     SRes *L = myslot != NO_LIST ? lists + U.lst0 + (uint64_t)myslot * U.lst_cap : nullptr;
     Cand *C = cand + (size_t)u * K + lane;
     uint32_t n = 0;

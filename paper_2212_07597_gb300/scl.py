@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libscl.so")
 
 SCL_OK, SCL_EINVAL, SCL_ENOMEM, SCL_ECUDA, SCL_ETIMEOUT, SCL_EOVERFLOW, SCL_ERANGE = 0, -1, -2, -3, -4, -5, -6
 SCL_ALL_TRACES = 0xFFFFFFFF
+SCL_BUDGET_AUTO = 0xFFFFFFFF
 _NAMES = {-1: "SCL_EINVAL", -2: "SCL_ENOMEM", -3: "SCL_ECUDA", -4: "SCL_ETIMEOUT", -5: "SCL_EOVERFLOW",
           -6: "SCL_ERANGE", -7: "SCL_EINTERNAL"}
 
@@ -85,7 +86,7 @@ REQUEST_RESULT_DTYPE = np.dtype([("done_ns", "<u8"), ("latency_ns", "<u8"), ("ba
 class scl_tuning(ctypes.Structure):
     _fields_ = [("unit_events", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
                 ("ext_events", ctypes.c_uint32), ("final_warps", ctypes.c_uint32),
-                ("first_events", ctypes.c_uint32)]
+                ("first_events", ctypes.c_uint32), ("fixup", ctypes.c_uint32)]
 
 
 SAMPLE_DTYPE = np.dtype([
@@ -347,8 +348,8 @@ def scl_tuning_get(ctx: Context) -> scl_tuning:
 
 
 def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int = 16, ext_events: int = 0,
-                   final_warps: int = 14, first_events: int = 0) -> None:
-    t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps, first_events)
+                   final_warps: int = 14, first_events: int = 0, fixup: int = 0) -> None:
+    t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps, first_events, fixup)
     _check(ctx, load().scl_tuning_set(ctx.handle, ctypes.byref(t)))
 
 

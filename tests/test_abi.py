@@ -68,7 +68,7 @@ def test_struct_layouts_match_c_compiler(tmp_path):
 def test_config_defaults_without_gpu():
     cfg = scl.config()
     assert cfg.threshold == 10_485_767 and cfg.copy_multiple == 2 and cfg.n_lines == 256
-    assert cfg.sample_budget_shift == 4 and cfg.leak_rule == 0
+    assert cfg.sample_budget_shift == scl.SCL_BUDGET_AUTO and cfg.leak_rule == 0
 
 
 def test_init_fails_loudly_without_gpu():

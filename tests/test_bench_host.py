@@ -1,45 +1,70 @@
-"""The bench's host-side arithmetic on CPU: the dominant-kernel roofline and the scaling of
-the committed ncu traffic table to a launch."""
+"""The bench's host-side arithmetic on CPU: the per-kernel rooflines, the scaling of the
+committed ncu traffic table to a launch, the stratified trace samples and the throughput
+aggregation."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
 
 
-def test_roofline_takes_an_event_path_kernel_and_its_own_units():
-    # the copy kernel's span is the longest (it waits beside the event path) but is not chosen
-    kt = {"sketch": (8.0, 10), "final": (9.0, 10), "copy_apply": (20.0, 10), "scan": (1.0, 10)}
-    r = bench.roofline_of(kt, n=1_000_000, m=100_000, traffic=False, sketch_n=900_000)
-    assert r["kernel"] == "final"
-    # 17 B per event over the events the exact replay takes (first units excluded), per launch
-    assert r["achieved"] == pytest.approx(17.0 * 900_000 / (0.9 / 1e3) / 1e9)
+def test_roofline_takes_the_longer_replay_kernel_with_its_own_bytes():
+    # k_phase1 reads 17 B per first-unit event, 8 B per sketched event, 13 B per memcpy;
+    # k_final 17 B per event of the other units
+    n, m, first = 1_000_000, 100_000, 400_000
+    kt = {"phase1": (8.0, 2), "final": (3.0, 2), "compact": (1.0, 2), "reset": (0.5, 2)}
+    r = bench.roofline_of(kt, n=n, m=m, first_events=first, traffic=False)
+    assert r["kernel"] == "phase1"
+    alg = 17.0 * first + 8.0 * (n - first) + 13.0 * m
+    assert r["alg_bytes"] == pytest.approx(alg)
+    assert r["achieved"] == pytest.approx(alg / (4.0 / 1e3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["kernels"]["final"]["achieved"] == pytest.approx(17.0 * (n - first) / (1.5 / 1e3) / 1e9)
     assert r["traffic"] is None
 
 
-def test_traffic_table_matches_the_kernel_sources_or_is_withheld(tmp_path, monkeypatch):
-    d = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+def test_traffic_table_matches_the_kernel_sources_or_is_withheld(monkeypatch):
+    path = os.path.join(bench.ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        assert bench.traffic_for("phase1", 1000.0) is None
+        return
+    d = json.load(open(path))
     k = d["kernels"]
-    for name, unit in (("sketch", "streamed event"), ("final", "event"), ("copy_apply", "memcpy")):
-        assert k[name]["unit"] == unit
-    # the table is read only when its hash is the current sources'
+    for name in ("phase1", "final"):
+        assert k[name]["dram_bytes_per_alg_byte"] == pytest.approx(k[name]["dram_bytes"] / k[name]["alg_bytes"])
     if d["source_hash"] == bench.source_hash():
-        assert bench.traffic_for("sketch", 10, streamed=1000) == pytest.approx(k["sketch"]["dram_bytes_per_unit"] * 1000)
-        assert bench.traffic_for("final", 1000) == pytest.approx(k["final"]["dram_bytes_per_unit"] * 1000)
+        assert bench.traffic_for("final", 1000.0) == pytest.approx(k["final"]["dram_bytes_per_alg_byte"] * 1000.0)
     # a changed kernel source withholds the figure
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
-    assert bench.traffic_for("final", 1000) is None
+    assert bench.traffic_for("final", 1000.0) is None
 
 
-def test_measured_traffic_is_close_to_the_algorithmic_bytes():
-    d = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["kernels"]
-    assert d["sketch"]["dram_bytes_per_unit"] == pytest.approx(bench.ALG_BYTES["sketch"], rel=0.05)
-    assert d["final"]["dram_bytes_per_unit"] == pytest.approx(bench.ALG_BYTES["final"], rel=0.05)
-    assert d["copy_apply"]["dram_bytes_per_unit"] == pytest.approx(bench.ALG_BYTES["copy_apply"], rel=0.05)
+def test_batched_sample_spans_the_lengths_and_keeps_every_leaking_trace():
+    lens, mlen = bench.batched_spec(4096)
+    pick = bench.batched_sample(lens)
+    assert int(np.argmin(lens)) in pick and int(np.argmax(lens)) in pick
+    assert all(i in pick for i in range(0, 4096, 100))
+    assert 512 <= len(pick) <= 512 + 41
+    # the sample's length distribution follows the batch's (evenly spaced ranks)
+    assert abs(np.median(lens[pick]) / np.median(lens) - 1) < 0.05
+    sub = bench.parity_subset(lens, pick)
+    assert int(np.argmin(lens)) in sub and int(np.argmax(lens)) in sub
+    assert all(i in sub for i in range(0, 4096, 100))
+
+
+def test_reference_and_gpu_arms_name_the_same_configuration():
+    lens, mlen = bench.batched_spec(4096)
+    a = bench.batched_config(4096, lens, mlen)
+    b = bench.batched_config(4096, *bench.batched_spec(4096))
+    assert a == b and a["memcpys"] == int(mlen.sum()) and a["n_lines"] == 4096
 
 
 def test_aggregate_is_all_events_over_the_slowest_rank():
     v, t = bench.aggregate([10.0, 20.0], [1000, 3000])
     assert t == 20.0 and v == pytest.approx(4000 / 0.020)
+
+
+def test_default_workload_is_the_batched_configuration():
+    assert bench.parse([]).workload == "batched"

@@ -275,10 +275,12 @@ def test_autotune_restores_state_and_keeps_results_exact():
     seg, kb = scl.trace_segment(0, b)
     best, ms = scl.scl_autotune(ctx, [seg])
     assert ms > 0 and best.final_warps in (10, 14) and best.ext_events in (16384, 32768)
+    assert best.unit_events in (0, 32768, 65536, 131072, 262144, 524288) and best.fixup in (0, 1)
+    assert best.first_events in (0, 524288, 1048576, 1310720, 1572864) and best.warps_per_block in (8, 12, 16)
     assert scl.scl_state_export(ctx, 0) == before
     t = scl.scl_tuning_get(ctx)
-    assert (t.unit_events, t.final_warps, t.warps_per_block, t.ext_events) == \
-        (best.unit_events, best.final_warps, best.warps_per_block, best.ext_events)
+    fields = ("unit_events", "final_warps", "warps_per_block", "ext_events", "first_events", "fixup")
+    assert [getattr(t, f) for f in fields] == [getattr(best, f) for f in fields]
     scl.scl_replay_batch(ctx, [seg])
     scl.scl_sync(ctx)
     assert_same(ctx, 0, oracle_of(tr, 1_048_573), samples=False)
