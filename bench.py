@@ -71,6 +71,8 @@ def parse(argv=None):
     p.add_argument("--procs", type=int, default=0, help="serving: processes (default 512)")
     p.add_argument("--segs", type=int, default=0, help="serving: segments per process (default 16)")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    p.add_argument("--tuning", default="", help="fixed tuning instead of the autotuner: unit,phase1_warps,"
+                                                "warmup,final_warps,first,fixup (e.g. 524288,16,32768,10,1572864,0)")
     p.add_argument("--tune", action="store_true", help="long/plain: run the autotuner before timing")
     p.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     p.add_argument("--no-rate", action="store_true", help="long/plain: skip the rate-based sampling comparison")
@@ -527,7 +529,10 @@ def run_batched(args):
                                          sample_log_capacity=1 << 14))
     stream = torch.cuda.Stream()
     tuned = None
-    if not args.no_tune:
+    if args.tuning:
+        scl.scl_tuning_set(ctx, *[int(x) for x in args.tuning.split(",")])
+        tuned = dict(tuning_dict(scl.scl_tuning_get(ctx)), fixed=True)
+    elif not args.no_tune:
         t_tune = time.perf_counter()
         best, best_ms = scl.scl_autotune(ctx, segs, stream)
         tuned = dict(tuning_dict(best, best_ms), seconds=time.perf_counter() - t_tune)

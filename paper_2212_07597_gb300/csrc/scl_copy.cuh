@@ -30,9 +30,9 @@ __device__ __forceinline__ unsigned long long add_carry(unsigned long long a, un
     return r;
 }
 
+// the value, then the flag with release semantics: a reader that acquires the flag sees it
 __device__ __forceinline__ void cs_publish(CopyStatus *st, unsigned long long v, bool inclusive) {
     if (inclusive) st->incl = v; else st->agg = v;
-    __threadfence();
     st_release(&st->flag, inclusive ? CS_INCL : CS_AGG);
 }
 
