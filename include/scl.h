@@ -235,7 +235,9 @@ int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
 /* Tuning: events per work unit (the chunk of a trace whose entering counter the sketch
  * speculates), first-unit length, warps per block of phase 1 and of the exact replay,
  * warm-up events, fix-up strategy.  scl_autotune times scl_replay_batch on the given
- * segments (median of three after a warm-up run) and searches one setting at a time,
+ * segments (a warm-up call, then the mean of three calls issued back to back, so that each
+ * call's host-side planning overlaps the previous call's device work as in repeated use;
+ * the results of these calls are discarded) and searches one setting at a time,
  * twice over: unit 32k/64k/128k/256k/512k, first unit unit/512k/1M/1.25M/1.5M, phase-1
  * warps 8/12/16, replay warps 10/14, warm-up 16k/32k, fix-up 0/1.  It restores the
  * touched traces' state before every run and at the end, keeps the fastest setting in the

@@ -16,6 +16,8 @@
 // first unit of each trace in a batch, whose entry is the trace's resident state; that
 // caller also wants the facts the sketch records for a candidate run (FIRST = true).
 #pragma once
+#include <type_traits>
+
 #include "scl_stage.cuh"
 
 namespace scl {
@@ -39,7 +41,6 @@ struct ExactRun {                // FIRST only: the run's facts, as the sketch r
     uint32_t garg, targ;
     int32_t last;                // last reset position (-1: none)
     int64_t P;                   // unit total
-    int64_t umax, umin;          // extremes of the unit-local prefix
 };
 
 // Replays unit U; writes its records to out[0 .. cap) and returns false if a wait timed
@@ -67,8 +68,8 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
     uint32_t tslot = 0;
     uint32_t enter_hit = 0;
     uint32_t n = 0;
-    // FIRST: the run's facts (lane-uniform except the extremes, reduced at the end)
-    int64_t gmax = INT64_MIN, tmax = INT64_MIN, umax = INT64_MIN, umin = INT64_MAX;
+    // FIRST: the run's facts (lane-uniform)
+    int64_t gmax = INT64_MIN, tmax = INT64_MIN;
     uint32_t garg = 0, targ = 0;
     int32_t last = -1;
 
@@ -87,22 +88,31 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         const uint32_t dn = lo <= 0 ? 0u : (1u << lo) - 1u;
         return up & ~dn;
     };
-    // bit k: event k of this lane is a free of the tracked block
+    // bit k: event k of this lane is a free of the tracked block (screened on the low address
+    // word; a step with a candidate is tested on the full address)
     auto free_bits = [&](const StepIn<E> &in) -> uint32_t {
         uint32_t b = 0;
         if (tk) {
+            const uint32_t tlo = (uint32_t)taddr;
 #pragma unroll
-            for (int k = 0; k < E; ++k) b |= (in.d[k] < 0 && in.a[k] == taddr) ? 1u << k : 0u;
+            for (int k = 0; k < E; ++k) b |= ((int32_t)(in.d[k] >> 32) < 0 && (uint32_t)in.a[k] == tlo) ? 1u << k : 0u;
+            if (__any_sync(FULL, b != 0)) {
+                b = 0;
+#pragma unroll
+                for (int k = 0; k < E; ++k) b |= (in.d[k] < 0 && in.a[k] == taddr) ? 1u << k : 0u;
+            }
         }
         return b;
     };
-    // add the warp's events at step positions (after, upto] to the window totals
-    auto fold = [&](const StepIn<E> &in, bool fits, uint32_t m) {
+    // add the warp's events at step positions (after, upto] (lane bits m; ALL: every event)
+    // to the window totals
+    auto fold = [&](const StepIn<E> &in, bool fits, uint32_t m, auto all) {
+        constexpr bool ALL = decltype(all)::value;
         if (fits) {
             int32_t sA = 0, sApy = 0, sSpy = 0;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const int32_t x = (m >> k) & 1u ? (int32_t)in.d[k] : 0;
+                const int32_t x = ALL || ((m >> k) & 1u) ? (int32_t)in.d[k] : 0;
                 const int32_t ps = max(x, 0);
                 const int32_t py = (int32_t)min(py_of(in, k), 1u);
                 sA += ps;
@@ -116,7 +126,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
             int64_t sA = 0, sApy = 0, sSpy = 0;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                const int64_t x = (m >> k) & 1u ? in.d[k] : 0;
+                const int64_t x = ALL || ((m >> k) & 1u) ? in.d[k] : 0;
                 const int64_t ps = x > 0 ? x : 0;
                 sA += ps;
                 if (py_of(in, k)) { sApy += ps; sSpy += x; }
@@ -131,7 +141,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
     // Returns true if the sample started tracking its block.
     auto close = [&](const StepIn<E> &in, bool fits, int after, int r, uint32_t rel0, int64_t cr,
                      int64_t Pr) -> bool {
-        fold(in, fits, range(after, r));
+        fold(in, fits, range(after, r), std::false_type{});
         const int fl = r / E, kf = r % E;
         uint64_t av = in.a[0];
         uint32_t pyv = py_of(in, 0);
@@ -169,7 +179,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
     };
     // every event of the step joins the open window (no sample in it)
     auto whole_step = [&](const StepIn<E> &in, bool fits) {
-        fold(in, fits, 0xffu);
+        fold(in, fits, 0xffu, std::true_type{});
         if (tk && __any_sync(FULL, free_bits(in) != 0)) hit_tracked();
     };
 
@@ -226,7 +236,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                 }
             }
             if (tk && __any_sync(FULL, (fb & range(after, STEP - 1)) != 0)) hit_tracked();
-            fold(in, fits, range(after, STEP - 1));
+            fold(in, fits, range(after, STEP - 1), std::false_type{});
             return false;
         };
         ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, kstep);
@@ -240,11 +250,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
             if (t32 && fits) {
                 StepPrefix32<E> sp;
                 int32_t *xq32 = reinterpret_cast<int32_t *>(sm.xq);
-                step_prefix32(in, lane, sp, xq32);
-                if (FIRST) {
-                    umax = P + sp.lmax > umax ? P + sp.lmax : umax;
-                    umin = P + sp.lmin < umin ? P + sp.lmin : umin;
-                }
+                step_prefix32(in, lane, sp, (int32_t *)nullptr);
                 const int32_t T32 = (int32_t)T;
                 int32_t b = (int32_t)c;
                 if (__ballot_sync(FULL, b + sp.lmax >= T32 || b + sp.lmin <= -T32) == 0) {
@@ -253,6 +259,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                     P += sp.tot;
                     return false;
                 }
+                publish_prefix32(sp, lane, xq32);
                 uint32_t fb = free_bits(in);
                 int after = -1;
                 while (true) {
@@ -264,17 +271,13 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                     b = -Qr;
                     after = r;
                 }
-                fold(in, true, range(after, STEP - 1));
+                fold(in, true, range(after, STEP - 1), std::false_type{});
                 c = b + sp.tot;
                 P += sp.tot;
                 return false;
             }
             StepPrefix<E> sp;
             step_prefix(in, lane, sp, sm.xq);
-            if (FIRST) {
-                umax = P + sp.lmax > umax ? P + sp.lmax : umax;
-                umin = P + sp.lmin < umin ? P + sp.lmin : umin;
-            }
             if (__ballot_sync(FULL, c + sp.lmax >= T || c + sp.lmin <= -T) == 0) {
                 whole_step(in, fits);
                 c += sp.tot;
@@ -294,7 +297,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                 b = -Qr;
                 after = r;
             }
-            fold(in, fits, range(after, STEP - 1));
+            fold(in, fits, range(after, STEP - 1), std::false_type{});
             c = b + sp.tot;
             P += sp.tot;
             return false;
@@ -307,8 +310,6 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
     n_out = n;
     if (FIRST) {
         R->gmax = gmax; R->garg = garg; R->tmax = tmax; R->targ = targ; R->last = last; R->P = P;
-        R->umax = warp_max(umax);
-        R->umin = warp_min(umin);
     }
     return ok;
 }

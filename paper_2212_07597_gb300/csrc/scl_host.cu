@@ -1234,31 +1234,33 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     scl_tuning best = keep;
     double best_ms = 1e300;
     int rc = copy_state(true) == cudaSuccess ? SCL_OK : SCL_ECUDA;
-    // one timed setting: median of three runs after a warm-up run, each from the saved state
+    // one timed setting: a warm-up call, then three calls back to back (each plans on the host
+    // while the previous one runs, as repeated calls do), from the saved state; the figure is
+    // the mean of the three.  The state is restored again at the end.
     std::vector<std::pair<scl_tuning, double>> seen;
     auto measure = [&](const scl_tuning &t) -> double {
         for (const auto &p : seen)
             if (memcmp(&p.first, &t, sizeof t) == 0) return p.second;
         c->tune = t;
-        std::vector<float> ts;
-        for (int rep = 0; rep < 4 && !rc; ++rep) {
-            if (copy_state(false) != cudaSuccess) { rc = SCL_ECUDA; break; }
-            cudaEventRecord(e0, s);
-            rc = scl_replay_batch(c, segs, nsegs, stream);
+        if (copy_state(false) != cudaSuccess) rc = SCL_ECUDA;
+        if (!rc) rc = scl_replay_batch(c, segs, nsegs, stream);
+        if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = SCL_ECUDA;
+        if (!rc) rc = check_device_error(c);
+        constexpr int REPS = 3;
+        if (!rc) cudaEventRecord(e0, s);
+        for (int rep = 0; rep < REPS && !rc; ++rep) rc = scl_replay_batch(c, segs, nsegs, stream);
+        if (!rc) {
             cudaEventRecord(e1, s);
-            if (rc) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SCL_ECUDA; break; }
-            if ((rc = check_device_error(c))) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) ts.push_back(ms);   // the first run warms up
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = SCL_ECUDA;
         }
+        if (!rc) rc = check_device_error(c);
         if (rc) return 1e300;
-        std::sort(ts.begin(), ts.end());
-        const double med = ts[ts.size() / 2];
-        seen.push_back({t, med});
-        if (med < best_ms) { best_ms = med; best = t; }
-        return med;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / REPS;
+        seen.push_back({t, per});
+        if (per < best_ms) { best_ms = per; best = t; }
+        return per;
     };
     // coordinate descent, two passes: each setting in turn takes its best value with the
     // others held at the best found so far

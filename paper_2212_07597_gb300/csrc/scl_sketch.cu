@@ -269,7 +269,8 @@ __device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__
     C->list = NO_LIST; C->pad = 0;
     if (lane == 0) {
         UnitSum S;   // window totals are filled by k_totals, for the units that need them
-        S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = R.umin; S.maxQ = R.umax;
+        // (a first unit's prefix extremes are never needed: its entry is exact)
+        S.total = R.P; S.totA = 0; S.totApy = 0; S.totSpy = 0; S.minQ = INT64_MIN; S.maxQ = INT64_MAX;
         usum[u] = S;
         uout[u] = O;
         if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);

@@ -311,6 +311,19 @@ __device__ __forceinline__ int swz32(int i) {
     return (r << 3) | ((((k >> 2) ^ (r >> 2)) & 1) << 2) | (k & 3);
 }
 
+// Publish this lane's EL step prefixes (ex + lp) to xq for first_cross (staged layout).
+template <int EL>
+__device__ __forceinline__ void publish_prefix32(const StepPrefix32<EL> &sp, int lane, int32_t *xq) {
+    static_assert(EL == 8, "32-bit rows hold 8 prefixes");
+    int4 *dst = reinterpret_cast<int4 *>(xq + lane * EL);
+    const int s = (lane >> 2) & 1;
+    dst[s] = make_int4(sp.ex + sp.lp[0], sp.ex + sp.lp[1], sp.ex + sp.lp[2], sp.ex + sp.lp[3]);
+    dst[s ^ 1] = make_int4(sp.ex + sp.lp[4], sp.ex + sp.lp[5], sp.ex + sp.lp[6], sp.ex + sp.lp[7]);
+    __syncwarp();
+}
+
+// The 32-bit step prefixes; with xq != nullptr they are also published for first_cross
+// (a caller that first tests whether the step crosses at all may publish them itself).
 template <int EL>
 __device__ __forceinline__ void step_prefix32(const StepIn<EL> &in, int lane, StepPrefix32<EL> &sp, int32_t *xq) {
     static_assert(EL == 8, "32-bit rows hold 8 prefixes");
@@ -334,11 +347,7 @@ __device__ __forceinline__ void step_prefix32(const StepIn<EL> &in, int lane, St
     sp.tot = __shfl_sync(FULL, incl, 31);
     sp.lmax = mx + sp.ex;
     sp.lmin = mn + sp.ex;
-    int4 *dst = reinterpret_cast<int4 *>(xq + lane * EL);
-    const int s = (lane >> 2) & 1;
-    dst[s] = make_int4(sp.ex + sp.lp[0], sp.ex + sp.lp[1], sp.ex + sp.lp[2], sp.ex + sp.lp[3]);
-    dst[s ^ 1] = make_int4(sp.ex + sp.lp[4], sp.ex + sp.lp[5], sp.ex + sp.lp[6], sp.ex + sp.lp[7]);
-    __syncwarp();
+    if (xq) publish_prefix32(sp, lane, xq);
 }
 
 // first_cross on the 32-bit form (same contract)
