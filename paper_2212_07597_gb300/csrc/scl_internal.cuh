@@ -227,7 +227,7 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// -------- mbarrier + bulk copy (cp.async.bulk, global -> shared, no multicast)
+// -------- mbarrier and asynchronous copies (global -> shared)
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -243,23 +243,6 @@ __device__ __forceinline__ void mbar_inval(uint64_t *bar) {
 
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
 }
 
 // 16-byte asynchronous global -> shared copy (cp.async, L2 only), and an arrival on an
@@ -288,8 +271,6 @@ __device__ __forceinline__ int swz_el(int i) {   // element i of a tile -> its s
     const int r = i / EL, k = i % EL;
     return r * EL + (swz_chunk_el<EL>(r, k >> 1) << 1) + (k & 1);
 }
-__device__ __forceinline__ int swz_chunk(int r, int c) { return swz_chunk_el<8>(r, c); }
-__device__ __forceinline__ int swz8(int i) { return swz_el<8>(i); }
 
 // Bounded wait for phase `parity` of the barrier, called by all 32 lanes of a warp.
 // Every lane polls (so each observes the phase completion); the answer is agreed by
