@@ -56,7 +56,7 @@ COPY_BYTES = 13.0        # size 8 + line 4 + flag 1 per memcpy
 EXACT_BYTES = 17.0       # an exact replay reads delta, addr and flag (the line only at samples)
 SKETCH_BYTES = 8.0       # the candidate counters read delta (warm-up re-reads are overhead)
 ALG_BYTES = {"sketch": SKETCH_BYTES, "final": EXACT_BYTES, "first": EXACT_BYTES, "copy": COPY_BYTES}
-EVENT_KERNELS = ("phase1", "final")
+EVENT_KERNELS = ("phase1", "final", "copy")
 
 
 def parse(argv=None):
@@ -233,16 +233,16 @@ def measured_peak():
 
 def kernel_bytes(n, m, first_events):
     """Algorithmic bytes each replay kernel reads per launch: k_phase1 replays the traces'
-    first units exactly (17 B/event), sketches the other units (8 B/event) and samples the
-    memcpys (13 B each); k_final replays the non-first units exactly (17 B/event)."""
+    first units exactly (17 B/event) and sketches the other units (8 B/event); k_final
+    replays the non-first units exactly (17 B/event); k_copy samples the memcpys (13 B each)."""
     rest = n - first_events
-    return {"phase1": EXACT_BYTES * first_events + SKETCH_BYTES * rest + COPY_BYTES * m,
-            "final": EXACT_BYTES * rest}
+    return {"phase1": EXACT_BYTES * first_events + SKETCH_BYTES * rest, "final": EXACT_BYTES * rest,
+            "copy": COPY_BYTES * m}
 
 
 def roofline_of(ktimes, n, m, first_events, launches_per_step=1, traffic=True):
-    """The dominant replay kernel (k_phase1 or k_final) and its algorithmic GB/s over its
-    CUDA-event time per launch, plus the same figures for the other one."""
+    """The dominant replay kernel (k_phase1, k_final or k_copy) and its algorithmic GB/s over
+    its CUDA-event time per launch, plus the same figures for the others."""
     per = kernel_bytes(n, m, first_events)
     peak, src = measured_peak()
     ks = {}

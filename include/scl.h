@@ -35,8 +35,9 @@
  *     call stores the needed count in *n_out and returns SCL_ERANGE.
  *   - All arithmetic is exact 64-bit integer arithmetic.  The caller keeps the
  *     running sums of a trace's deltas inside int64 (the library does not
- *     check every event); a copy byte count that overflows uint64 and record
- *     space that runs out are reported as SCL_EOVERFLOW.
+ *     check every event); a memcpy whose size plus the running copy counter
+ *     (below T_c) passes 2^64, and record space that runs out, are reported as
+ *     SCL_EOVERFLOW.
  *   - Line ids are read, and checked, where the method uses them: at the
  *     events that trigger a sample and at memcpy events.
  *   - A context is not thread-safe: one host thread drives it at a time.

@@ -19,9 +19,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_objs")
 LIB = os.path.join(HERE, "libscl.so")
-SOURCES = ["scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_host.cu", "scl_noalloc.cu", "scl_serve.cu",
-           "scl_rate.cu"]
-HEADERS = ["scl_internal.cuh", "scl_launch.h", "scl_stage.cuh", "scl_exact.cuh", "scl_copy.cuh", "scl_views.h"]
+SOURCES = ["scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_copy.cu", "scl_host.cu", "scl_noalloc.cu",
+           "scl_serve.cu", "scl_rate.cu"]
+HEADERS = ["scl_internal.cuh", "scl_launch.h", "scl_stage.cuh", "scl_exact.cuh", "scl_views.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,273 @@
+// scl_copy.cu -- the copy-volume sampler of Section 3.5, one thread block per tile of memcpys.
+//
+// Per trace, the memcpy byte counts are summed into a running counter that starts at the
+// trace's resident copy counter C0 (< T_c); memcpy j takes
+//     q_j = floor((C0 + S_j) / T_c) - floor((C0 + S_(j-1)) / T_c)
+// samples (S the inclusive prefix sum of the sizes), each worth T_c copied bytes, counted
+// for its line and flag.  Only the counter modulo T_c matters for q_j: with r_j the counter
+// before memcpy j (below T_c), q_j = floor((r_j + size_j) / T_c), and r_(j+1) is the
+// remainder.  So every sum here is kept modulo T_c (two residues add to less than 2^64, as
+// T_c < 2^63) and no division is needed unless a size is at least 8 T_c.
+//
+// A trace's memcpys are cut into tiles of COPY_TILE, taken by blocks in rounds over the
+// traces (every trace's first tile, then every second one, ...).  A block loads its tile
+// into registers (each thread CB_PER consecutive memcpys; 13 bytes per memcpy, read once),
+// sums it, publishes the sum, finds the counter entering the tile from its predecessors'
+// published sums and prefixes (a decoupled look-back: a predecessor publishes its sum
+// before it waits on anything, and it took its ticket earlier, so every wait ends; waits
+// are bounded), publishes its own prefix, and applies the samples; counts of lines below
+// CB_HOT gather in shared memory and reach the trace's counts once per tile.
+#include <algorithm>
+
+#include "scl_internal.cuh"
+#include "scl_launch.h"
+
+namespace scl {
+
+constexpr int CB_THREADS = 256;
+constexpr int CB_PER = COPY_TILE / CB_THREADS;   // memcpys per thread (16)
+constexpr uint32_t CB_HOT = 1024;                // lines counted in shared memory per tile
+constexpr uint32_t CS_AGG = 1u, CS_INCL = 2u;
+
+struct CopyStatus {               // one per tile, cleared before each batch
+    unsigned long long agg;       // the tile's bytes modulo T_c (valid from CS_AGG on)
+    unsigned long long incl;      // the counter after the tile, modulo T_c (CS_INCL)
+    unsigned int flag;
+    unsigned int pad;
+};
+
+struct CopyTask {                 // the tile a block works on, read by thread 0
+    CopyTile ct;
+    uint32_t t, c0, last, trace;
+    unsigned long long C0;
+    int valid;
+};
+
+struct alignas(16) CopyBlockSmem {
+    uint32_t hot[2 * CB_HOT];     // [line][flag] sample counts of the tile (32 bits: see below)
+    unsigned long long wsum[CB_THREADS / 32];
+    unsigned long long base;
+    CopyTask task[2];             // the current tile and the next
+    int ok;
+};
+
+// (a + b) mod T_c for a, b < T_c <= 2^63
+__device__ __forceinline__ unsigned long long madd(unsigned long long a, unsigned long long b, unsigned long long Tc) {
+    const unsigned long long s = a + b;
+    return s >= Tc ? s - Tc : s;
+}
+
+// the value, then the flag with release semantics: a reader that acquires the flag sees it
+__device__ __forceinline__ void cs_publish(CopyStatus *st, unsigned long long v, bool inclusive) {
+    if (inclusive) st->incl = v; else st->agg = v;
+    st_release(&st->flag, inclusive ? CS_INCL : CS_AGG);
+}
+
+__device__ void copy_fetch(const LaunchCopy &a, CopyTask &k) {
+    const int it = (int)atomicAdd(a.queue, 1u);
+    k.valid = it < a.nctiles;
+    if (!k.valid) return;
+    k.t = a.corder[it];
+    k.ct = a.ctiles[k.t];
+    const BTrace B = a.bts[k.ct.bt];
+    k.c0 = B.c0;
+    k.last = B.c0 + B.nc - 1;
+    k.trace = B.trace;
+    k.C0 = a.traces[B.trace].copy_counter;
+}
+
+__global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
+    __shared__ CopyBlockSmem sm;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    CopyStatus *status = static_cast<CopyStatus *>(a.cstatus);
+    const unsigned long long Tc = a.Tc;
+    const bool small = Tc <= (1ull << 60);
+    const unsigned long long Tc2 = 2 * Tc, Tc4 = 4 * Tc, Tc8 = 8 * Tc;   // (small: no overflow)
+    const uint32_t hot = a.n_lines < CB_HOT ? a.n_lines : CB_HOT;
+    for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) sm.hot[i] = 0u;
+    if (tid == 0) copy_fetch(a, sm.task[0]);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const CopyTask &K = sm.task[cur];
+        if (!K.valid) break;
+        const CopyTile ct = K.ct;
+        const uint32_t len = ct.len, t = K.t;
+        // ---- this thread's CB_PER consecutive memcpys, loaded into registers
+        const uint32_t e0 = (uint32_t)tid * CB_PER;
+        unsigned long long v[CB_PER];
+        uint32_t ln[CB_PER];
+        uint32_t pw[CB_PER / 4];
+        const bool vec = e0 + CB_PER <= len &&
+                         ((reinterpret_cast<uintptr_t>(ct.size) | reinterpret_cast<uintptr_t>(ct.line) |
+                           reinterpret_cast<uintptr_t>(ct.py)) & 15u) == 0;
+        if (vec) {
+            const ulonglong2 *ps = reinterpret_cast<const ulonglong2 *>(ct.size + e0);
+#pragma unroll
+            for (int q = 0; q < CB_PER / 2; ++q) { const ulonglong2 x = __ldg(ps + q); v[2 * q] = x.x; v[2 * q + 1] = x.y; }
+            const uint4 *pl = reinterpret_cast<const uint4 *>(ct.line + e0);
+#pragma unroll
+            for (int q = 0; q < CB_PER / 4; ++q) {
+                const uint4 x = __ldg(pl + q);
+                ln[4 * q] = x.x; ln[4 * q + 1] = x.y; ln[4 * q + 2] = x.z; ln[4 * q + 3] = x.w;
+            }
+            const uint4 y = __ldg(reinterpret_cast<const uint4 *>(ct.py + e0));
+            pw[0] = y.x; pw[1] = y.y; pw[2] = y.z; pw[3] = y.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < CB_PER; ++k) {
+                const bool in = e0 + k < len;
+                v[k] = in ? ct.size[e0 + k] : 0ull;
+                ln[k] = in ? ct.line[e0 + k] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < CB_PER / 4; ++q) {
+                uint32_t x = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) x |= (e0 + 4 * q + b < len ? (uint32_t)ct.py[e0 + 4 * q + b] : 0u) << (8 * b);
+                pw[q] = x;
+            }
+        }
+        // the next tile's ticket and description, while this one's loads are in flight
+        if (tid == 0) copy_fetch(a, sm.task[cur ^ 1]);
+        // ---- this thread's bytes, modulo T_c
+        unsigned long long ls = 0;
+#pragma unroll
+        for (int k = 0; k < CB_PER; ++k) {
+            unsigned long long r = v[k];
+            if (r >= Tc8 || !small) {
+                r %= Tc;
+            } else {
+                if (r >= Tc4) r -= Tc4;
+                if (r >= Tc2) r -= Tc2;
+                if (r >= Tc) r -= Tc;
+            }
+            ls = madd(ls, r, Tc);
+        }
+        // block exclusive scan of the threads' residues
+        unsigned long long x = ls;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x = madd(x, y, Tc);
+        }
+        if (lane == 31) sm.wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            const unsigned long long y = lane < CB_THREADS / 32 ? sm.wsum[lane] : 0ull;
+            unsigned long long yi = y;
+#pragma unroll
+            for (int o = 1; o < CB_THREADS / 32; o <<= 1) {
+                const unsigned long long z = __shfl_up_sync(FULL, yi, o);
+                if (lane >= o) yi = madd(yi, z, Tc);
+            }
+            const unsigned long long s = __shfl_sync(FULL, yi, CB_THREADS / 32 - 1);   // the tile's bytes mod T_c
+            if (lane < CB_THREADS / 32) sm.wsum[lane] = yi >= y ? yi - y : yi + (Tc - y);   // exclusive
+            // ---- the counter entering the tile (warp 0)
+            bool ok = true;
+            unsigned long long base = K.C0;
+            if (t == K.c0) {
+                if (lane == 0) cs_publish(&status[t], madd(K.C0, s, Tc), true);
+            } else {
+                if (lane == 0) cs_publish(&status[t], s, false);
+                unsigned long long acc = 0;
+                int64_t p = (int64_t)t - 1;   // newest predecessor not yet accounted for
+                while (true) {
+                    // lane j looks at tile p - j (tiles before the trace's first count as its start)
+                    const int64_t q = p - lane;
+                    unsigned int f = CS_INCL;
+                    unsigned long long val = 0;
+                    if (q >= (int64_t)K.c0) {
+                        unsigned long long n = 0;
+                        while ((f = ld_acquire(&status[q].flag)) == 0 && n < a.spin) ++n;
+                        if (f == CS_INCL) val = status[q].incl;
+                        else if (f == CS_AGG) val = status[q].agg;
+                    } else if (q == (int64_t)K.c0 - 1) {
+                        val = K.C0;
+                    }
+                    if (!__all_sync(FULL, f != 0)) {
+                        if (lane == 0) set_error(a.err, E_TIMEOUT, 20, t);
+                        ok = false;
+                        break;
+                    }
+                    // the nearest predecessor with a prefix ends the look-back
+                    const unsigned done = __ballot_sync(FULL, f == CS_INCL);
+                    const int stop = done ? __ffs(done) - 1 : 32;
+                    unsigned long long wv = lane <= stop ? val : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) wv = madd(wv, __shfl_xor_sync(FULL, wv, o), Tc);
+                    acc = madd(acc, wv, Tc);
+                    if (done) break;
+                    p -= 32;
+                }
+                base = acc;
+                if (ok && lane == 0) cs_publish(&status[t], madd(base, s, Tc), true);
+            }
+            if (lane == 0) {
+                sm.base = base;
+                sm.ok = ok;
+                // the trace's last tile gives its counter after the batch (for the state fold)
+                if (ok && t == K.last) a.btres[ct.bt].copy_end = madd(base, s, Tc);
+            }
+        }
+        __syncthreads();
+        if (!sm.ok) break;   // a wait gave up (uniform over the block)
+        // ---- samples at each of this thread's memcpys, from the counter before the first
+        unsigned long long rem = madd(madd(sm.base, sm.wsum[w], Tc), x >= ls ? x - ls : x + (Tc - ls), Tc);
+        unsigned long long *gc = a.copies + (uint64_t)K.trace * a.n_lines * 2;
+        int ovf = 0;
+#pragma unroll
+        for (int k = 0; k < CB_PER; ++k) {
+            const unsigned long long sz = v[k];
+            ovf |= rem + sz < rem;   // the sequential count would pass 2^64 here
+            unsigned long long qn;
+            if (sz >= Tc8 || !small) {
+                qn = sz / Tc;
+                const unsigned long long r2 = rem + sz % Tc;   // < 2 T_c: fits
+                qn += r2 >= Tc;
+                rem = r2 >= Tc ? r2 - Tc : r2;
+            } else {
+                // rem + sz < 9 T_c <= 9 * 2^60 fits: the quotient (at most 8) bit by bit
+                rem += sz;
+                qn = 0;
+                if (rem >= Tc8) { rem -= Tc8; qn = 8; }
+                if (rem >= Tc4) { rem -= Tc4; qn += 4; }
+                if (rem >= Tc2) { rem -= Tc2; qn += 2; }
+                if (rem >= Tc) { rem -= Tc; qn += 1; }
+            }
+            if (!qn) continue;
+            const uint32_t l = ln[k];
+            if (l >= a.n_lines) {
+                set_error(a.err, E_RANGE, l, (unsigned long long)(e0 + k));
+                continue;
+            }
+            const int f = ((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0;
+            // the shared table takes counts of at most 8 per memcpy, so a tile adds at most
+            // 4,096 x 8 per entry and the 32-bit counts cannot wrap; larger ones go to global
+            if (l < hot && qn <= 8) atomicAdd(&sm.hot[2 * l + f], (uint32_t)qn);
+            else atomicAdd(&gc[2 * l + f], qn);
+        }
+        if (__syncthreads_or(ovf) && tid == 0) set_error(a.err, E_OVERFLOW, 7, t);
+        for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) {
+            const uint32_t c = sm.hot[i];
+            if (c) {
+                atomicAdd(&gc[i], (unsigned long long)c);
+                sm.hot[i] = 0u;
+            }
+        }
+        __syncthreads();   // the table and this tile's task slot are reused
+    }
+}
+
+size_t copy_status_bytes(size_t ntiles) { return sizeof(CopyStatus) * ntiles; }
+
+cudaError_t launch_copy(const LaunchCopy &a, cudaStream_t s) {
+    if (!a.nctiles) return cudaSuccess;
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copy, CB_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(a.nctiles, std::max(1, bps) * a.num_sms));
+    k_copy<<<blocks, CB_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace scl

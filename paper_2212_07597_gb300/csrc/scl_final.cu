@@ -11,27 +11,28 @@ namespace scl {
 
 using FinalRing = Ring<true, 3, 256, 8>;
 
-// 14 warps per block at most (128 registers, a few spilled on cold paths: a cap of 136
-// registers left blocks of only 12 warps on an SM, and the replay ran 40% longer)
-__global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ units, int nunits,
-                                                  const UnitTrue *__restrict__ utrue,
-                                                  const UnitPlan *__restrict__ uplan, const SRes *__restrict__ lists,
-                                                  FRec *recs, UnitOut *uout, int64_t T, unsigned *queue, ErrWord *err,
-                                                  unsigned long long spin, unsigned long long *stats) {
+// 14 warps per block at most (128 registers: a cap of 136 registers left blocks of only 12
+// warps on an SM, and the replay ran 40% longer)
+__global__ void __launch_bounds__(32 * 14) k_final(const LaunchFinal a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FinalRing &sm = reinterpret_cast<FinalRing *>(smem_raw)[warp];
+    const Unit *__restrict__ units = a.units;
+    const int nunits = a.nunits;
+    const int64_t T = a.T;
+    ErrWord *err = a.err;
+    const unsigned long long spin = a.spin;
     ring_init(sm, lane);
     uint32_t phase = 0;
     while (true) {
         int u = 0;
-        if (lane == 0) u = (int)atomicAdd(queue, 1u);
+        if (lane == 0) u = (int)atomicAdd(a.queue, 1u);
         u = __shfl_sync(FULL, u, 0);
         if (u >= nunits) break;
         const Unit U = units[u];
         if (U.first) continue;   // replayed by k_phase1
-        const UnitTrue Tu = utrue[u];
-        const UnitPlan Pl = uplan[u];
+        const UnitTrue Tu = a.utrue[u];
+        const UnitPlan Pl = a.uplan[u];
         ExactIn in0;
         // ---- the open window entering the unit: totals of whole units (from k_scan) plus
         // the tail of the unit that holds the last reset before this one
@@ -52,16 +53,16 @@ __global__ void __launch_bounds__(32 * 14) k_final(const Unit *__restrict__ unit
         in0.fpb = Pl.fp_base;
         in0.tk = Pl.enter_kind;
         in0.taddr = Pl.enter_addr;
-        in0.list = Tu.list != NO_LIST ? lists + U.lst0 + (uint64_t)Tu.list * U.lst_cap : nullptr;
+        in0.list = Tu.list != NO_LIST ? a.lists + U.lst0 + (uint64_t)Tu.list * U.lst_cap : nullptr;
         in0.nres = Tu.n;
         in0.exit_c = Tu.exit_c;
-        if (!in0.list && lane == 0) atomicAdd(&stats[5], 1ull);
+        if (!in0.list && lane == 0) atomicAdd(&a.stats[5], 1ull);
         UnitOut O;
         uint32_t n = 0;
-        const bool ok = exact_unit<false>(sm, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O,
+        const bool ok = exact_unit<false>(sm, phase, U, in0, a.recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O,
                                           (ExactRun *)nullptr);
         if (lane == 0) {
-            uout[u] = O;
+            a.uout[u] = O;
             if (n > U.rec_cap) set_error(err, E_OVERFLOW, 3, (unsigned long long)u);
             if (ok && n != Tu.n) set_error(err, E_INTERNAL, 10, (unsigned long long)u);
         }
@@ -88,11 +89,11 @@ cudaError_t launch_wait_selftest(ErrWord *err, unsigned long long limit, cudaStr
 }
 
 cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s) {
+    if (!a.nunits) return cudaSuccess;
     const size_t smem = sizeof(FinalRing) * a.warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_final<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a.units, a.nunits, a.utrue, a.uplan, a.lists, a.recs,
-                                                           a.uout, a.T, a.queue, a.err, a.spin, a.stats);
+    k_final<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ using namespace scl;
 
 namespace {
 
-constexpr uint32_t STATE_MAGIC = 0x53434c31u;   // "SCL1"
+constexpr uint32_t STATE_MAGIC = 0x53434c32u;   // "SCL2"
 
 struct DevBuf {
     void *p = nullptr;
@@ -41,6 +41,7 @@ struct scl_ctx {
     // resident state
     DevTrace *traces = nullptr;
     LineRow *lines = nullptr;
+    unsigned long long *copies = nullptr;   // copy-volume samples [trace][line][flag]
     Sample *log = nullptr;
     ErrWord *errw = nullptr;
     void *scores = nullptr;
@@ -264,7 +265,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
     a.ngroups = q.ngroups;
     a.err = c->errw;
-    if (nunits || q.nctiles) {
+    if (nunits) {
         LaunchSketch k;
         k.units = d_units;
         k.nunits = nunits;
@@ -290,34 +291,26 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         k.num_sms = c->num_sms;
         k.order = reinterpret_cast<const uint32_t *>(dp + q.o_ord);
         k.nitems = nunits;
-        k.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
-        k.nctiles = q.nctiles;
-        k.cstatus = c->ctsum.p;
-        k.btres = static_cast<BTraceRes *>(c->btres.p);
-        k.lines = c->lines;
-        k.n_lines = cfg.n_lines;
-        k.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
         // spread the units over all SMs: fewer warps per block when units are few
-        const int items = nunits + q.nctiles;
         k.warps_per_block = std::max(1, std::min(std::min((int)c->tune.warps_per_block, PHASE1_MAX_WARPS),
-                                                 (items + c->num_sms - 1) / c->num_sms));
+                                                 (nunits + c->num_sms - 1) / c->num_sms));
         int bps = 0;
         if (phase1_occupancy(k.warps_per_block, &bps) || bps < 1) bps = 1;
-        k.blocks = std::max(1, std::min(bps * c->num_sms, (items + k.warps_per_block - 1) / k.warps_per_block));
+        k.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + k.warps_per_block - 1) / k.warps_per_block));
         {
             // the traces' first units replayed exactly and the other units sketched, from one queue
             Prof p(c, s, "phase1");
             CK(launch_phase1(k, s), "launch phase 1");
         }
-        if (nunits) {
-            {
-                Prof p(c, s, "match");
-                CK(launch_match(k, s), "launch match");
-            }
-            {
-                Prof p(c, s, "chain");
-                CK(launch_chain(k, s), "launch chain");
-            }
+        {
+            Prof p(c, s, "match");
+            CK(launch_match(k, s), "launch match");
+        }
+        {
+            Prof p(c, s, "chain");
+            CK(launch_chain(k, s), "launch chain");
+        }
+        {
             Prof p(c, s, "totals");
             CK(launch_totals(k, s), "launch totals");
         }
@@ -348,6 +341,26 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
         Prof p(c, s, "final");
         CK(launch_final(f, s), "launch final");
+    }
+    if (q.nctiles) {
+        // ---- the copy-volume sampler (Section 3.5)
+        LaunchCopy k;
+        k.corder = reinterpret_cast<const uint32_t *>(dp + q.o_ord) + nunits;
+        k.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
+        k.nctiles = q.nctiles;
+        k.cstatus = c->ctsum.p;
+        k.bts = d_bts;
+        k.traces = c->traces;
+        k.btres = static_cast<BTraceRes *>(c->btres.p);
+        k.copies = c->copies;
+        k.n_lines = cfg.n_lines;
+        k.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
+        k.queue = c->queue + 3;
+        k.err = c->errw;
+        k.spin = cfg.spin_limit;
+        k.num_sms = c->num_sms;
+        Prof p(c, s, "copy");
+        CK(launch_copy(k, s), "launch copy");
     }
     {
         Prof p(c, s, "compact");
@@ -434,6 +447,7 @@ void scl_replay_free(scl_ctx *c) {
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
+    cudaFree(c->copies);
     if (c->log) cudaFree(c->log);
     cudaFree(c->errw);
     cudaFree(c->scores);
@@ -488,6 +502,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
     const size_t L = cfg.n_lines, NTr = cfg.max_traces;
     if (e == cudaSuccess) e = cudaMalloc(&c->traces, sizeof(DevTrace) * NTr);
     if (e == cudaSuccess) e = cudaMalloc(&c->lines, sizeof(LineRow) * L * NTr);
+    if (e == cudaSuccess) e = cudaMalloc(&c->copies, sizeof(unsigned long long) * 2 * L * NTr);
     if (e == cudaSuccess && cfg.sample_log_capacity)
         e = cudaMalloc(&c->log, sizeof(Sample) * cfg.sample_log_capacity * NTr);
     if (e == cudaSuccess) e = cudaMalloc(&c->errw, sizeof(ErrWord));
@@ -516,7 +531,7 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
         return r;
     }
     if (e == cudaSuccess)
-        e = launch_reset(c->traces, c->lines, 0, cfg.max_traces, cfg.n_lines, cfg.initial_footprint, cfg.copy_phase,
+        e = launch_reset(c->traces, c->lines, c->copies, 0, cfg.max_traces, cfg.n_lines, cfg.initial_footprint, cfg.copy_phase,
                          nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -654,9 +669,9 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 rec_total += U.rec_cap;
                 lst_total += (uint64_t)NL * U.lst_cap;
             }
-            for (uint64_t off = 0; off < g.cp.n; off += COPY_WTILE) {
+            for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
                 CopyTile T;
-                T.len = (uint32_t)std::min<uint64_t>(COPY_WTILE, g.cp.n - off);
+                T.len = (uint32_t)std::min<uint64_t>(COPY_TILE, g.cp.n - off);
                 T.size = g.cp.size + off;
                 T.line = g.cp.line + off;
                 T.py = g.cp.is_python + off;
@@ -946,8 +961,12 @@ int scl_line_stats(scl_ctx *c, uint32_t trace, scl_line_stat *out, uint32_t cap,
     *n_out = L;
     if (cap < L) return fail(c, SCL_ERANGE, "output holds %u rows, %u needed", cap, L);
     std::vector<LineRow> rows(L);
+    std::vector<unsigned long long> cps(2 * (size_t)L);
     CK(cudaMemcpy(rows.data(), c->lines + (uint64_t)trace * L, sizeof(LineRow) * L, cudaMemcpyDeviceToHost),
        "read line stats");
+    CK(cudaMemcpy(cps.data(), c->copies + (uint64_t)trace * L * 2, sizeof(unsigned long long) * 2 * L,
+                  cudaMemcpyDeviceToHost),
+       "read copy samples");
     // copy bytes are samples * T_c (Section 3.5): formed here, not kept on the device
     const uint64_t Tc = (uint64_t)c->cfg.copy_multiple * (uint64_t)c->cfg.threshold;
     for (uint32_t l = 0; l < L; ++l) {
@@ -955,8 +974,8 @@ int scl_line_stats(scl_ctx *c, uint32_t trace, scl_line_stat *out, uint32_t cap,
         const LineRow &x = rows[l];
         o.n_growth = x.n_growth; o.n_shrink = x.n_shrink;
         o.A = x.A; o.F = x.F; o.A_py = x.A_py; o.F_py = x.F_py; o.net = x.net;
-        o.copy_samples[0] = x.copy_samples[0]; o.copy_samples[1] = x.copy_samples[1];
-        o.copy_bytes[0] = x.copy_samples[0] * Tc; o.copy_bytes[1] = x.copy_samples[1] * Tc;
+        o.copy_samples[0] = cps[2 * l]; o.copy_samples[1] = cps[2 * l + 1];
+        o.copy_bytes[0] = cps[2 * l] * Tc; o.copy_bytes[1] = cps[2 * l + 1] * Tc;
     }
     return SCL_OK;
 }
@@ -1020,7 +1039,8 @@ struct StateHeader {
 int scl_state_export(scl_ctx *c, uint32_t trace, void *buf, uint64_t cap, uint64_t *n_out) {
     if (!c || !n_out) return SCL_EINVAL;
     if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
-    const uint64_t need = sizeof(StateHeader) + sizeof(DevTrace) + sizeof(LineRow) * (uint64_t)c->cfg.n_lines;
+    const uint64_t L = c->cfg.n_lines;
+    const uint64_t need = sizeof(StateHeader) + sizeof(DevTrace) + (sizeof(LineRow) + 16) * L;
     *n_out = need;
     if (!buf) return SCL_OK;
     if (cap < need) return fail(c, SCL_ERANGE, "state needs %llu bytes", (unsigned long long)need);
@@ -1030,8 +1050,11 @@ int scl_state_export(scl_ctx *c, uint32_t trace, void *buf, uint64_t cap, uint64
     char *p = static_cast<char *>(buf);
     memcpy(p, &h, sizeof h);
     CK(cudaMemcpy(p + sizeof h, c->traces + trace, sizeof(DevTrace), cudaMemcpyDeviceToHost), "export");
-    CK(cudaMemcpy(p + sizeof h + sizeof(DevTrace), c->lines + (uint64_t)trace * c->cfg.n_lines,
-                  sizeof(LineRow) * c->cfg.n_lines, cudaMemcpyDeviceToHost),
+    CK(cudaMemcpy(p + sizeof h + sizeof(DevTrace), c->lines + (uint64_t)trace * L, sizeof(LineRow) * L,
+                  cudaMemcpyDeviceToHost),
+       "export");
+    CK(cudaMemcpy(p + sizeof h + sizeof(DevTrace) + sizeof(LineRow) * L, c->copies + (uint64_t)trace * L * 2, 16 * L,
+                  cudaMemcpyDeviceToHost),
        "export");
     return SCL_OK;
 }
@@ -1039,7 +1062,8 @@ int scl_state_export(scl_ctx *c, uint32_t trace, void *buf, uint64_t cap, uint64
 int scl_state_import(scl_ctx *c, uint32_t trace, const void *buf, uint64_t n) {
     if (!c || !buf) return SCL_EINVAL;
     if (trace >= c->cfg.max_traces) return fail(c, SCL_EINVAL, "trace %u out of range", trace);
-    const uint64_t need = sizeof(StateHeader) + sizeof(DevTrace) + sizeof(LineRow) * (uint64_t)c->cfg.n_lines;
+    const uint64_t L = c->cfg.n_lines;
+    const uint64_t need = sizeof(StateHeader) + sizeof(DevTrace) + (sizeof(LineRow) + 16) * L;
     StateHeader h;
     if (n < sizeof h) return fail(c, SCL_EINVAL, "state buffer too short");
     memcpy(&h, buf, sizeof h);
@@ -1053,8 +1077,11 @@ int scl_state_import(scl_ctx *c, uint32_t trace, const void *buf, uint64_t n) {
     memcpy(&t, p + sizeof h, sizeof t);
     if (c->cfg.sample_log_capacity == 0) t.n_samples = t.n_samples;  // counts are kept; records are not
     CK(cudaMemcpy(c->traces + trace, &t, sizeof t, cudaMemcpyHostToDevice), "import");
-    CK(cudaMemcpy(c->lines + (uint64_t)trace * c->cfg.n_lines, p + sizeof h + sizeof t,
-                  sizeof(LineRow) * c->cfg.n_lines, cudaMemcpyHostToDevice),
+    CK(cudaMemcpy(c->lines + (uint64_t)trace * L, p + sizeof h + sizeof t, sizeof(LineRow) * L,
+                  cudaMemcpyHostToDevice),
+       "import");
+    CK(cudaMemcpy(c->copies + (uint64_t)trace * L * 2, p + sizeof h + sizeof t + sizeof(LineRow) * L, 16 * L,
+                  cudaMemcpyHostToDevice),
        "import");
     c->h_events[trace] = t.n_events;
     return SCL_OK;
@@ -1069,7 +1096,8 @@ int scl_trace_reset(scl_ctx *c, uint32_t trace, void *stream) {
     const uint32_t t0 = all ? 0 : trace, nt = all ? c->cfg.max_traces : 1;
     {
         Prof p(c, s, "reset");
-        CK(launch_reset(c->traces, c->lines, t0, nt, c->cfg.n_lines, c->cfg.initial_footprint, c->cfg.copy_phase, s),
+        CK(launch_reset(c->traces, c->lines, c->copies, t0, nt, c->cfg.n_lines, c->cfg.initial_footprint,
+                        c->cfg.copy_phase, s),
            "launch reset");
     }
     for (uint32_t t = t0; t < t0 + nt; ++t) c->h_events[t] = 0;
@@ -1200,9 +1228,10 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     const size_t L = c->cfg.n_lines;
     void *save = nullptr;
     const size_t nt = std::max<size_t>(1, tr.size());
-    CK(cudaMalloc(&save, (sizeof(DevTrace) + sizeof(LineRow) * L) * nt), "autotune state copy");
+    CK(cudaMalloc(&save, (sizeof(DevTrace) + (sizeof(LineRow) + 16) * L) * nt), "autotune state copy");
     DevTrace *save_t = static_cast<DevTrace *>(save);
     LineRow *save_l = reinterpret_cast<LineRow *>(save_t + nt);
+    unsigned long long *save_c = reinterpret_cast<unsigned long long *>(save_l + nt * L);
     std::vector<uint64_t> h_ev(tr.size());
     auto copy_state = [&](bool to_save) -> cudaError_t {
         size_t k = 0;
@@ -1215,6 +1244,11 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
             if (e == cudaSuccess)
                 e = to_save ? cudaMemcpyAsync(save_l + k * L, l, bl, cudaMemcpyDeviceToDevice, s)
                             : cudaMemcpyAsync(l, save_l + k * L, bl, cudaMemcpyDeviceToDevice, s);
+            unsigned long long *cc = c->copies + (size_t)r.first * L * 2;
+            const size_t bc = 16 * L * r.second;
+            if (e == cudaSuccess)
+                e = to_save ? cudaMemcpyAsync(save_c + k * L * 2, cc, bc, cudaMemcpyDeviceToDevice, s)
+                            : cudaMemcpyAsync(cc, save_c + k * L * 2, bc, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
             k += r.second;
         }

@@ -19,8 +19,7 @@ constexpr int STEP = 32 * E;       // events per walker step
 constexpr int TILE = 256;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
 constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
-constexpr int COPY_TILE = 4096;    // memcpy events per block of the allocation-free copy sampler
-constexpr int COPY_WTILE = 1024;   // memcpy events per warp tile of the replay's copy sampler
+constexpr int COPY_TILE = 4096;    // memcpy events per block of the copy samplers
 constexpr int SMEM_LINES_MAX = 1024;  // per-line tables kept in shared memory up to this L
 
 // error codes mirrored from scl.h
@@ -36,13 +35,13 @@ struct DevTrace {                   // one per trace slot
     uint64_t n_events, n_copies, n_samples, copy_counter;
 };
 
-struct LineRow {                    // one per (trace, line); same field order as scl_line_stat + leak pair
+struct LineRow {                    // one per (trace, line): sample totals (scl_line_stat order) + leak pair
     unsigned long long n_growth, n_shrink;
     long long A, F, A_py, F_py, net;
-    unsigned long long copy_samples[2], copy_bytes[2];   // copy_bytes unused (samples * T_c at query)
     unsigned long long mallocs, frees;
 };
-constexpr int LINE_WORDS = 13;
+// the copy-volume samples of a (trace, line) live in their own array, [trace][line][flag]
+// (16 bytes per line): the copy sampler's updates then touch a compact per-trace block
 
 struct Sample {                     // layout of scl_sample (56 bytes)
     uint64_t idx;
@@ -176,7 +175,7 @@ struct BTraceRes {
     int64_t last_cross_unit;                    // unit of the batch's last crossing (-1: none)
     uint64_t last_cross_idx;                    // its trace index
     uint32_t pending_hit, pad;                  // the block tracked before the batch was freed before the first crossing
-    uint64_t copy_total;                        // bytes copied in the batch
+    uint64_t copy_end;                          // copy counter after the batch (< T_c)
 };
 
 struct ErrWord {

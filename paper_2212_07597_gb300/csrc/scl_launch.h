@@ -30,15 +30,8 @@ struct LaunchSketch {
     const DevTrace *traces;
     int64_t T;
     uint32_t warmup;
-    const uint32_t *order;   // phase-1 work: unit indices, longest work first, then copy tile indices
-    int nitems;              // units (the copy tiles follow them in the queue)
-    const CopyTile *ctiles;  // the copy-volume sampler's warp tiles, trace by trace
-    int nctiles;
-    void *cstatus;           // CopyStatus per tile (look-back), cleared before the batch
-    BTraceRes *btres;
-    LineRow *lines;
-    uint32_t n_lines;
-    uint64_t Tc;
+    const uint32_t *order;   // phase-1 work: unit indices, longest work first
+    int nitems;
     unsigned *queue;     // [0] phase 1, [2] final
     ErrWord *err;
     unsigned long long spin;
@@ -60,6 +53,23 @@ struct LaunchFinal {
     ErrWord *err;
     unsigned long long spin;
     int blocks, warps_per_block;
+};
+
+struct LaunchCopy {           // the copy-volume sampler (scl_copy.cu)
+    const uint32_t *corder;      // tile indices in rounds over the traces
+    const CopyTile *ctiles;
+    int nctiles;
+    void *cstatus;               // look-back state per tile, cleared before the batch
+    const BTrace *bts;
+    const DevTrace *traces;
+    BTraceRes *btres;
+    unsigned long long *copies;  // resident copy-volume samples [trace][line][flag]
+    uint32_t n_lines;
+    uint64_t Tc;
+    unsigned *queue;             // tile tickets
+    ErrWord *err;
+    unsigned long long spin;
+    int num_sms;
 };
 
 struct CompactGroup {
@@ -95,6 +105,7 @@ int phase1_occupancy(int warps_per_block, int *blocks_per_sm);
 int final_occupancy(int warps_per_block, int *blocks_per_sm);
 cudaError_t launch_phase1(const LaunchSketch &a, cudaStream_t s);
 size_t copy_status_bytes(size_t ntiles);   // look-back state of the copy-volume tiles
+cudaError_t launch_copy(const LaunchCopy &a, cudaStream_t s);
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s);
 cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s);
@@ -108,8 +119,8 @@ cudaError_t launch_mark(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_epi(const LaunchPost &a, cudaStream_t s);
 cudaError_t launch_state(const LaunchPost &a, cudaStream_t s);
 
-cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
-                         int64_t F0, uint64_t phase, cudaStream_t s);
+cudaError_t launch_reset(DevTrace *traces, LineRow *lines, unsigned long long *copies, uint32_t trace0,
+                         uint32_t ntr, uint32_t n_lines, int64_t F0, uint64_t phase, cudaStream_t s);
 cudaError_t launch_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines, uint32_t rule, void *out,
                           cudaStream_t s);
 cudaError_t launch_timeline(const Sample *log, uint64_t n, uint32_t line, void *scratch, uint64_t cap,

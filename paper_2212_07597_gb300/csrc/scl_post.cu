@@ -496,18 +496,20 @@ __global__ void k_state(LaunchPost a) {
         st.n_samples += BR.n_samples;
     }
     if (B.n_cp) {
-        st.copy_counter = (st.copy_counter + BR.copy_total) % a.Tc;
+        st.copy_counter = BR.copy_end;
         st.n_copies += B.n_cp;
     }
 }
 
 // ---------------------------------------------------------------- reset / scores
-__global__ void k_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
-                        int64_t F0, uint64_t phase) {
+__global__ void k_reset(DevTrace *traces, LineRow *lines, unsigned long long *copies, uint32_t trace0, uint32_t ntr,
+                        uint32_t n_lines, int64_t F0, uint64_t phase) {
     unsigned long long *rows = reinterpret_cast<unsigned long long *>(lines + (uint64_t)trace0 * n_lines);
     const uint64_t nw = (uint64_t)ntr * n_lines * (sizeof(LineRow) / 8);
     const uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = i0; i < nw; i += stride) rows[i] = 0;
+    unsigned long long *cc = copies + (uint64_t)trace0 * n_lines * 2;
+    for (uint64_t i = i0; i < (uint64_t)ntr * n_lines * 2; i += stride) cc[i] = 0;
     for (uint64_t k = i0; k < ntr; k += stride) {
         DevTrace t;
         t.c = t.A = t.F = t.A_py = t.F_py = 0;
@@ -683,13 +685,13 @@ cudaError_t launch_state(const LaunchPost &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(DevTrace *traces, LineRow *lines, uint32_t trace0, uint32_t ntr, uint32_t n_lines,
-                         int64_t F0, uint64_t phase, cudaStream_t s) {
-    const uint64_t nw = (uint64_t)ntr * n_lines * (sizeof(LineRow) / 8);
+cudaError_t launch_reset(DevTrace *traces, LineRow *lines, unsigned long long *copies, uint32_t trace0,
+                         uint32_t ntr, uint32_t n_lines, int64_t F0, uint64_t phase, cudaStream_t s) {
+    const uint64_t nw = (uint64_t)ntr * n_lines * (sizeof(LineRow) / 8 + 2);
     uint64_t blocks = (std::max<uint64_t>(nw, ntr) + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    k_reset<<<(int)blocks, 256, 0, s>>>(traces, lines, trace0, ntr, n_lines, F0, phase);
+    k_reset<<<(int)blocks, 256, 0, s>>>(traces, lines, copies, trace0, ntr, n_lines, F0, phase);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,6 @@
 #include <algorithm>
 #include <cstddef>
 
-#include "scl_copy.cuh"
 #include "scl_exact.cuh"
 #include "scl_launch.h"
 
@@ -114,7 +113,6 @@ static_assert(SketchRing::kTL == SKETCH_TILE, "the host counts warm-up events in
 union alignas(128) Phase1Smem {
     SketchRing s;
     FirstRing f;
-    CopySmem c;
 };
 constexpr size_t PHASE1_WARP_SMEM = sizeof(Phase1Smem);
 static_assert(PHASE1_WARP_SMEM % 128 == 0, "per-warp slices laid end to end stay aligned");
@@ -278,51 +276,35 @@ __device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__
     return true;
 }
 
-// Phase 1, one persistent kernel: every warp takes work from one queue -- the units
-// (`order`, longest work first), then the copy-volume tiles in rounds over the traces (a
-// trace's tiles in order) -- replaying a
-// trace's first unit exactly, sketching every other unit, and sampling memcpy tiles, so the
-// latency-bound candidate counters and the bandwidth-bound passes share the SMs, a long
-// first unit starts early, and the short copy tiles fill the end.
+// Phase 1, one persistent kernel: every warp takes units from one queue (`order`, longest
+// work first), replaying a trace's first unit exactly and sketching every other unit, so the
+// latency-bound candidate counters and the exact replays share the SMs and a long first unit
+// starts early.
 __global__ void __launch_bounds__(32 * PHASE1_MAX_WARPS, 1) k_phase1(const LaunchSketch a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Phase1Smem &sm = *reinterpret_cast<Phase1Smem *>(smem_raw + (size_t)warp * PHASE1_WARP_SMEM);
-    int cur = -1;   // staging area in use: 0 sketch ring, 1 exact ring, 2 copy tile
+    int cur = -1;   // ring in use: 0 sketch, 1 exact
     uint32_t phase = 0;
-    CopyStatus *cstatus = static_cast<CopyStatus *>(a.cstatus);
     while (true) {
         int it = 0;
         if (lane == 0) it = (int)atomicAdd(a.queue, 1u);
         it = __shfl_sync(FULL, it, 0);
-        if (it >= a.nitems + a.nctiles) break;
-        const int u = it < a.nitems ? (int)a.order[it] : -1;
-        const int want = u < 0 ? 2 : a.units[u].first ? 1 : 0;
+        if (it >= a.nitems) break;
+        const int u = (int)a.order[it];
+        const int want = a.units[u].first ? 1 : 0;
         if (want != cur) {
             if (cur == 0) ring_release(sm.s, lane);
             if (cur == 1) ring_release(sm.f, lane);
-            if (cur == 2) copy_smem_release(sm.c, lane);
-            if (want == 0) ring_init(sm.s, lane);
-            if (want == 1) ring_init(sm.f, lane);
-            if (want == 2) copy_smem_init(sm.c, lane);
+            if (want == 0) ring_init(sm.s, lane); else ring_init(sm.f, lane);
             cur = want;
             phase = 0;
         }
-        bool ok;
-        if (want == 2) {
-            const uint32_t t = a.order[it];
-            const CopyTile ct = a.ctiles[t];
-            const BTrace B = a.bts[ct.bt];
-            ok = copy_tile(sm.c, phase, ct, t, B.c0, cstatus, a.traces[B.trace].copy_counter, a.Tc, a.n_lines,
-                           a.lines + (uint64_t)B.trace * a.n_lines, t + 1 == B.c0 + B.nc ? a.btres + ct.bt : nullptr,
-                           a.err, a.spin, lane);
-        } else if (want == 1) {
-            ok = first_unit(sm.f, phase, u, a.units, a.usum, a.cand, a.recs, a.uout, a.traces, a.T, a.err, a.spin,
-                            lane);
-        } else {
-            ok = sketch_unit(sm.s, phase, u, a.units, a.usum, a.cand, a.lists, a.T, a.warmup, a.err, a.spin, lane);
-        }
-        if (!ok) break;   // a wait timed out: leave (the staging area may not be reusable)
+        const bool ok = want ? first_unit(sm.f, phase, u, a.units, a.usum, a.cand, a.recs, a.uout, a.traces, a.T,
+                                          a.err, a.spin, lane)
+                             : sketch_unit(sm.s, phase, u, a.units, a.usum, a.cand, a.lists, a.T, a.warmup, a.err,
+                                           a.spin, lane);
+        if (!ok) break;   // a wait timed out: leave (the ring may not be reusable)
     }
 }
 
@@ -761,15 +743,13 @@ cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s) {
 }
 
 cudaError_t launch_phase1(const LaunchSketch &a, cudaStream_t s) {
-    if (!a.nitems && !a.nctiles) return cudaSuccess;
+    if (!a.nitems) return cudaSuccess;
     const size_t smem = PHASE1_WARP_SMEM * a.warps_per_block;
     cudaError_t e = cudaFuncSetAttribute(k_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_phase1<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
     return cudaGetLastError();
 }
-
-size_t copy_status_bytes(size_t ntiles) { return sizeof(CopyStatus) * ntiles; }
 
 cudaError_t launch_match(const LaunchSketch &a, cudaStream_t s) {
     const int threads = a.nunits * K;

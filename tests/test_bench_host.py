@@ -11,17 +11,18 @@ import bench
 
 
 def test_roofline_takes_the_longer_replay_kernel_with_its_own_bytes():
-    # k_phase1 reads 17 B per first-unit event, 8 B per sketched event, 13 B per memcpy;
-    # k_final 17 B per event of the other units
+    # k_phase1 reads 17 B per first-unit event and 8 B per sketched event; k_final 17 B per
+    # event of the other units; k_copy 13 B per memcpy
     n, m, first = 1_000_000, 100_000, 400_000
-    kt = {"phase1": (8.0, 2), "final": (3.0, 2), "compact": (1.0, 2), "reset": (0.5, 2)}
+    kt = {"phase1": (8.0, 2), "final": (3.0, 2), "copy": (0.6, 2), "compact": (1.0, 2), "reset": (0.5, 2)}
     r = bench.roofline_of(kt, n=n, m=m, first_events=first, traffic=False)
     assert r["kernel"] == "phase1"
-    alg = 17.0 * first + 8.0 * (n - first) + 13.0 * m
+    alg = 17.0 * first + 8.0 * (n - first)
     assert r["alg_bytes"] == pytest.approx(alg)
     assert r["achieved"] == pytest.approx(alg / (4.0 / 1e3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["kernels"]["final"]["achieved"] == pytest.approx(17.0 * (n - first) / (1.5 / 1e3) / 1e9)
+    assert r["kernels"]["copy"]["achieved"] == pytest.approx(13.0 * m / (0.3 / 1e3) / 1e9)
     assert r["traffic"] is None
 
 
