@@ -194,7 +194,7 @@ class Clocks:
 
 
 KERNEL_SOURCES = ("scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_stage.cuh", "scl_internal.cuh",
-                  "scl_exact.cuh", "scl_copy.cuh")
+                  "scl_exact.cuh", "scl_copy.cu")
 
 
 def source_hash() -> str:
@@ -252,7 +252,9 @@ def roofline_of(ktimes, n, m, first_events, launches_per_step=1, traffic=True):
             a = per[k] / launches_per_step / (ms / 1e3) / 1e9
             ks[k] = {"ms": ms, "alg_bytes": per[k] / launches_per_step, "achieved": a, "frac": a / peak,
                      "traffic": traffic_for(k, per[k] / launches_per_step) if traffic else None}
-    dom = max(ks, key=lambda k: ks[k]["ms"])
+    # the copy-volume kernel runs on a side stream beside the event path, so its CUDA-event
+    # span includes waiting for SMs: the dominant kernel is taken on the event path
+    dom = max((k for k in ks if k != "copy"), key=lambda k: ks[k]["ms"])
     d = ks[dom]
     return {"bound": "hbm", "kernel": dom, "achieved": d["achieved"], "peak": peak, "unit": "GB/s",
             "frac": d["frac"], "peak_source": src, "traffic": d["traffic"], "alg_bytes": d["alg_bytes"],

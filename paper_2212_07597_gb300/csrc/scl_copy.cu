@@ -18,6 +18,7 @@
 // are bounded), publishes its own prefix, and applies the samples; counts of lines below
 // CB_HOT gather in shared memory and reach the trace's counts once per tile.
 #include <algorithm>
+#include <cstddef>
 
 #include "scl_internal.cuh"
 #include "scl_launch.h"
@@ -36,10 +37,8 @@ struct CopyStatus {               // one per tile, cleared before each batch
     unsigned int pad;
 };
 
-struct CopyTask {                 // the tile a block works on, read by thread 0
+struct alignas(16) CopyTask {     // the tile a block works on, written by thread 0 (16-byte stores)
     CopyTile ct;
-    uint32_t t, c0, last, trace;
-    unsigned long long C0;
     int valid;
 };
 
@@ -50,6 +49,9 @@ struct alignas(16) CopyBlockSmem {
     CopyTask task[2];             // the current tile and the next
     int ok;
 };
+
+static_assert(offsetof(CopyBlockSmem, task) % 16 == 0 && sizeof(CopyTask) % 16 == 0 && offsetof(CopyTask, ct) == 0,
+              "the tile records are copied with 16-byte stores");
 
 // (a + b) mod T_c for a, b < T_c <= 2^63
 __device__ __forceinline__ unsigned long long madd(unsigned long long a, unsigned long long b, unsigned long long Tc) {
@@ -63,17 +65,14 @@ __device__ __forceinline__ void cs_publish(CopyStatus *st, unsigned long long v,
     st_release(&st->flag, inclusive ? CS_INCL : CS_AGG);
 }
 
-__device__ void copy_fetch(const LaunchCopy &a, CopyTask &k) {
-    const int it = (int)atomicAdd(a.queue, 1u);
-    k.valid = it < a.nctiles;
+// the tile of ticket `it` (its description is one 48-byte record of the plan)
+__device__ __forceinline__ void copy_job(const LaunchCopy &a, unsigned it, CopyTask &k) {
+    k.valid = it < (unsigned)a.nctiles;
     if (!k.valid) return;
-    k.t = a.corder[it];
-    k.ct = a.ctiles[k.t];
-    const BTrace B = a.bts[k.ct.bt];
-    k.c0 = B.c0;
-    k.last = B.c0 + B.nc - 1;
-    k.trace = B.trace;
-    k.C0 = a.traces[B.trace].copy_counter;
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.ctiles + it);
+    uint4 *dst = reinterpret_cast<uint4 *>(&k.ct);
+    const uint4 x = __ldg(src), y = __ldg(src + 1), z = __ldg(src + 2);
+    dst[0] = x; dst[1] = y; dst[2] = z;
 }
 
 __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
@@ -85,13 +84,21 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
     const unsigned long long Tc2 = 2 * Tc, Tc4 = 4 * Tc, Tc8 = 8 * Tc;   // (small: no overflow)
     const uint32_t hot = a.n_lines < CB_HOT ? a.n_lines : CB_HOT;
     for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) sm.hot[i] = 0u;
-    if (tid == 0) copy_fetch(a, sm.task[0]);
+    // thread 0 holds the ticket of the tile after the next one, so the ticket's round trip
+    // overlaps a whole tile and only the record's load overlaps the tile's own loads.  (A
+    // block takes tickets in order and works its tiles in that order, and a tile waits only
+    // on tiles of lower tickets: the lowest unfinished ticket can always proceed.)
+    unsigned tk = 0;
+    if (tid == 0) {
+        copy_job(a, atomicAdd(a.queue, 1u), sm.task[0]);
+        tk = atomicAdd(a.queue, 1u);
+    }
     __syncthreads();
     for (int cur = 0;; cur ^= 1) {
         const CopyTask &K = sm.task[cur];
         if (!K.valid) break;
         const CopyTile ct = K.ct;
-        const uint32_t len = ct.len, t = K.t;
+        const uint32_t len = ct.len, t = ct.t;
         // ---- this thread's CB_PER consecutive memcpys, loaded into registers
         const uint32_t e0 = (uint32_t)tid * CB_PER;
         unsigned long long v[CB_PER];
@@ -128,20 +135,43 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
             }
         }
         // the next tile's ticket and description, while this one's loads are in flight
-        if (tid == 0) copy_fetch(a, sm.task[cur ^ 1]);
-        // ---- this thread's bytes, modulo T_c
-        unsigned long long ls = 0;
+        if (tid == 0) {
+            copy_job(a, tk, sm.task[cur ^ 1]);
+            tk = atomicAdd(a.queue, 1u);
+        }
+        // ---- this thread's bytes, modulo T_c.  When 8 T_c < 2^31 and every size of the thread
+        // is below 8 T_c, each residue, sum and remainder below fits 32 bits (the same
+        // arithmetic in half the instructions)
+        bool n32 = Tc8 < (1ull << 31);
 #pragma unroll
-        for (int k = 0; k < CB_PER; ++k) {
-            unsigned long long r = v[k];
-            if (r >= Tc8 || !small) {
-                r %= Tc;
-            } else {
-                if (r >= Tc4) r -= Tc4;
-                if (r >= Tc2) r -= Tc2;
-                if (r >= Tc) r -= Tc;
+        for (int k = 0; k < CB_PER; ++k) n32 &= v[k] < Tc8;
+        unsigned long long ls = 0;
+        if (n32) {
+            const uint32_t t1 = (uint32_t)Tc, t2 = (uint32_t)Tc2, t4 = (uint32_t)Tc4;
+            uint32_t s32 = 0;
+#pragma unroll
+            for (int k = 0; k < CB_PER; ++k) {
+                uint32_t r = (uint32_t)v[k];
+                if (r >= t4) r -= t4;
+                if (r >= t2) r -= t2;
+                if (r >= t1) r -= t1;
+                s32 += r;
+                if (s32 >= t1) s32 -= t1;
             }
-            ls = madd(ls, r, Tc);
+            ls = s32;
+        } else {
+#pragma unroll
+            for (int k = 0; k < CB_PER; ++k) {
+                unsigned long long r = v[k];
+                if (r >= Tc8 || !small) {
+                    r %= Tc;
+                } else {
+                    if (r >= Tc4) r -= Tc4;
+                    if (r >= Tc2) r -= Tc2;
+                    if (r >= Tc) r -= Tc;
+                }
+                ls = madd(ls, r, Tc);
+            }
         }
         // block exclusive scan of the threads' residues
         unsigned long long x = ls;
@@ -152,7 +182,7 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
         }
         if (lane == 31) sm.wsum[w] = x;
         __syncthreads();
-        if (w == 0) {
+    if (w == 0) {
             const unsigned long long y = lane < CB_THREADS / 32 ? sm.wsum[lane] : 0ull;
             unsigned long long yi = y;
 #pragma unroll
@@ -164,9 +194,11 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
             if (lane < CB_THREADS / 32) sm.wsum[lane] = yi >= y ? yi - y : yi + (Tc - y);   // exclusive
             // ---- the counter entering the tile (warp 0)
             bool ok = true;
-            unsigned long long base = K.C0;
-            if (t == K.c0) {
-                if (lane == 0) cs_publish(&status[t], madd(K.C0, s, Tc), true);
+            unsigned long long base = 0;
+            if (t == ct.c0) {
+                // the trace's first tile: the resident counter enters it
+                base = a.traces[ct.trace].copy_counter;
+                if (lane == 0) cs_publish(&status[t], madd(base, s, Tc), true);
             } else {
                 if (lane == 0) cs_publish(&status[t], s, false);
                 unsigned long long acc = 0;
@@ -176,13 +208,13 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                     const int64_t q = p - lane;
                     unsigned int f = CS_INCL;
                     unsigned long long val = 0;
-                    if (q >= (int64_t)K.c0) {
+                    if (q >= (int64_t)ct.c0) {
                         unsigned long long n = 0;
                         while ((f = ld_acquire(&status[q].flag)) == 0 && n < a.spin) ++n;
                         if (f == CS_INCL) val = status[q].incl;
                         else if (f == CS_AGG) val = status[q].agg;
-                    } else if (q == (int64_t)K.c0 - 1) {
-                        val = K.C0;
+                    } else if (q == (int64_t)ct.c0 - 1) {
+                        val = a.traces[ct.trace].copy_counter;
                     }
                     if (!__all_sync(FULL, f != 0)) {
                         if (lane == 0) set_error(a.err, E_TIMEOUT, 20, t);
@@ -206,17 +238,44 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                 sm.base = base;
                 sm.ok = ok;
                 // the trace's last tile gives its counter after the batch (for the state fold)
-                if (ok && t == K.last) a.btres[ct.bt].copy_end = madd(base, s, Tc);
+                if (ok && t == ct.last) a.btres[ct.bt].copy_end = madd(base, s, Tc);
             }
         }
         __syncthreads();
         if (!sm.ok) break;   // a wait gave up (uniform over the block)
         // ---- samples at each of this thread's memcpys, from the counter before the first
         unsigned long long rem = madd(madd(sm.base, sm.wsum[w], Tc), x >= ls ? x - ls : x + (Tc - ls), Tc);
-        unsigned long long *gc = a.copies + (uint64_t)K.trace * a.n_lines * 2;
+        unsigned long long *gc = a.copies + (uint64_t)ct.trace * a.n_lines * 2;
         int ovf = 0;
+        auto count = [&](int k, uint32_t qn) {
+            const uint32_t l = ln[k];
+            if (l >= a.n_lines) {
+                set_error(a.err, E_RANGE, l, (unsigned long long)(e0 + k));
+                return;
+            }
+            const int f = ((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0;
+            // the shared table takes counts of at most 8 per memcpy, so a tile adds at most
+            // 4,096 x 8 per entry and the 32-bit counts cannot wrap; larger ones go to global
+            if (l < hot && qn <= 8) atomicAdd(&sm.hot[2 * l + f], qn);
+            else atomicAdd(&gc[2 * l + f], (unsigned long long)qn);
+        };
+        if (n32) {
+            const uint32_t t1 = (uint32_t)Tc, t2 = (uint32_t)Tc2, t4 = (uint32_t)Tc4, t8 = (uint32_t)Tc8;
+            uint32_t r32 = (uint32_t)rem;
 #pragma unroll
-        for (int k = 0; k < CB_PER; ++k) {
+            for (int k = 0; k < CB_PER; ++k) {
+                // r32 + size < T_c + 8 T_c < 2^32: the quotient (at most 8) bit by bit
+                r32 += (uint32_t)v[k];
+                uint32_t qn = 0;
+                if (r32 >= t8) { r32 -= t8; qn = 8; }
+                if (r32 >= t4) { r32 -= t4; qn += 4; }
+                if (r32 >= t2) { r32 -= t2; qn += 2; }
+                if (r32 >= t1) { r32 -= t1; qn += 1; }
+                if (qn) count(k, qn);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CB_PER && !n32; ++k) {
             const unsigned long long sz = v[k];
             ovf |= rem + sz < rem;   // the sequential count would pass 2^64 here
             unsigned long long qn;
@@ -235,16 +294,16 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                 if (rem >= Tc) { rem -= Tc; qn += 1; }
             }
             if (!qn) continue;
-            const uint32_t l = ln[k];
-            if (l >= a.n_lines) {
-                set_error(a.err, E_RANGE, l, (unsigned long long)(e0 + k));
-                continue;
+            if (qn <= 8) {
+                count(k, (uint32_t)qn);
+            } else {
+                const uint32_t l = ln[k];
+                if (l >= a.n_lines) {
+                    set_error(a.err, E_RANGE, l, (unsigned long long)(e0 + k));
+                    continue;
+                }
+                atomicAdd(&gc[2 * l + (((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0)], qn);
             }
-            const int f = ((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0;
-            // the shared table takes counts of at most 8 per memcpy, so a tile adds at most
-            // 4,096 x 8 per entry and the 32-bit counts cannot wrap; larger ones go to global
-            if (l < hot && qn <= 8) atomicAdd(&sm.hot[2 * l + f], (uint32_t)qn);
-            else atomicAdd(&gc[2 * l + f], qn);
         }
         if (__syncthreads_or(ovf) && tid == 0) set_error(a.err, E_OVERFLOW, 7, t);
         for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) {

@@ -59,9 +59,11 @@ struct scl_ctx {
     size_t h_plan_cap = 0;
     cudaEvent_t plan_done = nullptr;
     bool plan_pending = false;
-    // the replay's kernels run on a high-priority stream forked from the caller's
-    cudaStream_t hi = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // the replay's kernels run on a high-priority stream forked from the caller's; the
+    // copy-volume sampler (Section 3.5), which shares nothing with the event path, runs on a
+    // side stream between the fork and a join before the state fold
+    cudaStream_t hi = nullptr, side = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_copy = nullptr, ev_fork = nullptr;
     // host-to-device staging of scl_replay_batch_host: pieces spread over several copy
     // streams (several copy engines at once), joined back before the replay
     static constexpr int NCS = 4;
@@ -265,6 +267,33 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
     a.ngroups = q.ngroups;
     a.err = c->errw;
+    // ---- the copy-volume sampler, on a side stream forked after phase 1 (before the scan when
+    // there are no units): beside the chain, the scans and the bandwidth-bound exact replay
+    // rather than the issue-bound phase 1 (its blocks take the room a replay block of up to 10
+    // warps leaves)
+    auto copy_pass = [&]() -> cudaError_t {
+        if (!q.nctiles) return cudaSuccess;
+        if (cudaError_t e = cudaEventRecord(c->ev_fork, s)) return e;
+        if (cudaError_t e = cudaStreamWaitEvent(c->side, c->ev_fork, 0)) return e;
+        LaunchCopy k;
+        k.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
+        k.nctiles = q.nctiles;
+        k.cstatus = c->ctsum.p;
+        k.traces = c->traces;
+        k.btres = static_cast<BTraceRes *>(c->btres.p);
+        k.copies = c->copies;
+        k.n_lines = cfg.n_lines;
+        k.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
+        k.queue = c->queue + 3;
+        k.err = c->errw;
+        k.spin = cfg.spin_limit;
+        k.num_sms = c->num_sms;
+        {
+            Prof p(c, c->side, "copy");
+            if (cudaError_t e = launch_copy(k, c->side)) return e;
+        }
+        return cudaEventRecord(c->ev_copy, c->side);
+    };
     if (nunits) {
         LaunchSketch k;
         k.units = d_units;
@@ -302,6 +331,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
             Prof p(c, s, "phase1");
             CK(launch_phase1(k, s), "launch phase 1");
         }
+        CK(copy_pass(), "copy pass");
         {
             Prof p(c, s, "match");
             CK(launch_match(k, s), "launch match");
@@ -314,6 +344,8 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
             Prof p(c, s, "totals");
             CK(launch_totals(k, s), "launch totals");
         }
+    } else {
+        CK(copy_pass(), "copy pass");
     }
     {
         Prof p(c, s, "scan");
@@ -342,26 +374,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         Prof p(c, s, "final");
         CK(launch_final(f, s), "launch final");
     }
-    if (q.nctiles) {
-        // ---- the copy-volume sampler (Section 3.5)
-        LaunchCopy k;
-        k.corder = reinterpret_cast<const uint32_t *>(dp + q.o_ord) + nunits;
-        k.ctiles = reinterpret_cast<const CopyTile *>(dp + q.o_ct);
-        k.nctiles = q.nctiles;
-        k.cstatus = c->ctsum.p;
-        k.bts = d_bts;
-        k.traces = c->traces;
-        k.btres = static_cast<BTraceRes *>(c->btres.p);
-        k.copies = c->copies;
-        k.n_lines = cfg.n_lines;
-        k.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
-        k.queue = c->queue + 3;
-        k.err = c->errw;
-        k.spin = cfg.spin_limit;
-        k.num_sms = c->num_sms;
-        Prof p(c, s, "copy");
-        CK(launch_copy(k, s), "launch copy");
-    }
+
     {
         Prof p(c, s, "compact");
         CK(launch_compact(a, s), "launch compact");
@@ -374,6 +387,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         Prof p(c, s, "epi");
         CK(launch_epi(a, s), "launch epi");
     }
+    if (q.nctiles) CK(cudaStreamWaitEvent(s, c->ev_copy, 0), "join the copy pass");
     {
         Prof p(c, s, "state");
         CK(launch_state(a, s), "launch state");
@@ -456,6 +470,9 @@ void scl_replay_free(scl_ctx *c) {
     if (c->h_plan) cudaFreeHost(c->h_plan);
     if (c->plan_done) cudaEventDestroy(c->plan_done);
     if (c->hi) cudaStreamDestroy(c->hi);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_copy) cudaEventDestroy(c->ev_copy);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     for (int i = 0; i < scl_ctx::NCS; ++i)
@@ -517,9 +534,12 @@ int scl_replay_init(scl_ctx **out, const scl_config *cfg_in) {
         int least = 0, greatest = 0;
         e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->hi, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     for (int i = 0; i < scl_ctx::NCS && e == cudaSuccess; ++i)
         e = cudaStreamCreateWithFlags(&c->cstream[i], cudaStreamNonBlocking);
     for (int i = 0; i <= scl_ctx::NCS && e == cudaSuccess; ++i)
@@ -670,12 +690,14 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 lst_total += (uint64_t)NL * U.lst_cap;
             }
             for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
-                CopyTile T;
+                CopyTile T{};
                 T.len = (uint32_t)std::min<uint64_t>(COPY_TILE, g.cp.n - off);
                 T.size = g.cp.size + off;
                 T.line = g.cp.line + off;
                 T.py = g.cp.is_python + off;
                 T.bt = bi;
+                T.t = (uint32_t)ctiles.size();
+                T.trace = B.trace;
                 ctiles.push_back(T);
             }
             B.n_ev += g.ev.n;
@@ -706,22 +728,27 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     // ---- copy tiles in rounds over the traces (every trace's first tile, then every second
     // tile, ...): a trace's tiles stay in order for the look-back, a predecessor was taken
     // long before, and the warps at work spread their counter updates over many traces
-    std::vector<uint32_t> corder;
+    std::vector<CopyTile> corder;
     corder.reserve(ctiles.size());
     {
         uint32_t maxnc = 0;
         for (const BTrace &B : bts) maxnc = std::max(maxnc, B.nc);
         for (uint32_t r = 0; r < maxnc; ++r)
             for (const BTrace &B : bts)
-                if (r < B.nc) corder.push_back(B.c0 + r);
+                if (r < B.nc) {
+                    CopyTile T = ctiles[B.c0 + r];
+                    T.c0 = B.c0;
+                    T.last = B.c0 + B.nc - 1;
+                    corder.push_back(T);
+                }
     }
-    // ---- plan blob: units | bts | groups | copy tiles | phase-1 order (units, then copy tiles)
+    // ---- plan blob: units | bts | groups | copy tiles (in their order) | phase-1 order
     const size_t o_units = 0;
     const size_t o_bts = al256(o_units + sizeof(Unit) * units.size());
     const size_t o_grp = al256(o_bts + sizeof(BTrace) * bts.size());
     const size_t o_ct = al256(o_grp + sizeof(CompactGroup) * cgroups.size());
     const size_t o_ord = al256(o_ct + sizeof(CopyTile) * ctiles.size());
-    const size_t blob = al256(o_ord + sizeof(uint32_t) * (p1order.size() + corder.size()));
+    const size_t blob = al256(o_ord + sizeof(uint32_t) * p1order.size());
     if (c->plan_pending) {
         CK(cudaEventSynchronize(c->plan_done), "wait for previous plan upload");
         c->plan_pending = false;
@@ -737,9 +764,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     memcpy(hp + o_units, units.data(), sizeof(Unit) * units.size());
     memcpy(hp + o_bts, bts.data(), sizeof(BTrace) * bts.size());
     memcpy(hp + o_grp, cgroups.data(), sizeof(CompactGroup) * cgroups.size());
-    memcpy(hp + o_ct, ctiles.data(), sizeof(CopyTile) * ctiles.size());
+    memcpy(hp + o_ct, corder.data(), sizeof(CopyTile) * corder.size());
     memcpy(hp + o_ord, p1order.data(), sizeof(uint32_t) * p1order.size());
-    memcpy(hp + o_ord + sizeof(uint32_t) * p1order.size(), corder.data(), sizeof(uint32_t) * corder.size());
 
     int r;
     if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;

@@ -75,12 +75,16 @@ struct BTrace {           // one per trace present in the batch
     uint32_t c0, nc;               // copy tiles
 };
 
-struct CopyTile {
+struct CopyTile {          // a tile of one trace's memcpys; the plan lists them in the order blocks take them
     const uint64_t *size;
     const uint32_t *line;
     const uint8_t *py;
     uint32_t len, bt;
+    uint32_t t;            // look-back slot: the tile's index among all tiles in trace order
+    uint32_t c0, last;     // slots of the trace's first and last tiles
+    uint32_t trace;        // trace slot
 };
+static_assert(sizeof(CopyTile) == 48, "three 16-byte loads per tile");
 
 // ---- sketch: K candidate counters per unit (one per lane)
 constexpr int K = 32;     // candidates per unit

@@ -56,11 +56,9 @@ struct LaunchFinal {
 };
 
 struct LaunchCopy {           // the copy-volume sampler (scl_copy.cu)
-    const uint32_t *corder;      // tile indices in rounds over the traces
-    const CopyTile *ctiles;
+    const CopyTile *ctiles;      // in the order blocks take them (rounds over the traces)
     int nctiles;
     void *cstatus;               // look-back state per tile, cleared before the batch
-    const BTrace *bts;
     const DevTrace *traces;
     BTraceRes *btres;
     unsigned long long *copies;  // resident copy-volume samples [trace][line][flag]

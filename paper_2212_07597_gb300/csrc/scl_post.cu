@@ -338,9 +338,9 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
         for (uint32_t i = threadIdx.x; i < a.n_lines * HCOLS; i += NT) hist[i] = 0;
         __syncthreads();
     }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if ((uint32_t)w < G.nu) {
-        const uint32_t u = G.u0 + w;
+    // the whole block walks each unit's records in turn (a group often holds a single unit)
+    for (uint32_t k = 0; k < G.nu; ++k) {
+        const uint32_t u = G.u0 + k;
         const Unit U = a.units[u];
         const UnitOut O = a.uout[u];
         const UnitPlan &Pn = a.uplan[u];
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
         LineRow *grow = a.lines + (uint64_t)U.trace * a.n_lines;
         FRec *rec = a.recs + U.rec0;
         const uint32_t cnt = O.count < U.rec_cap ? O.count : U.rec_cap;
-        for (uint32_t j = lane; j < cnt; j += 32) {
+        for (uint32_t j = threadIdx.x; j < cnt; j += NT) {
             const FRec r = rec[j];
             // the line of the sample's event (the replay leaves it to this pass); kept in the
             // record for the leak epilogue and the state fold
