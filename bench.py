@@ -68,6 +68,7 @@ def parse(argv=None):
     p.add_argument("--workload", default="batched", choices=["batched", "long_256m", "plain_1m", "sweep", "serving"])
     p.add_argument("--events", type=int, default=0, help="override a trace length (testing)")
     p.add_argument("--traces", type=int, default=0, help="batched / sweep: number of traces")
+    p.add_argument("--stride", type=int, default=1, help="batched: take every stride-th of the 4,096 traces")
     p.add_argument("--procs", type=int, default=0, help="serving: processes (default 512)")
     p.add_argument("--segs", type=int, default=0, help="serving: segments per process (default 16)")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner")
@@ -321,17 +322,24 @@ def full_match(ctx, tid, o, scl, samples=True):
 
 # ---------------------------------------------------------------- workloads
 
-def batched_spec(ntr, rank=0, events=0):
+def batched_ids(ntr, stride=1):
+    """Trace ids of a batched case: every stride-th of the 4,096 (stride > 1 keeps the batch's
+    length distribution in a smaller case, for profiling)."""
+    return np.arange(0, 4096, max(1, stride))[:ntr]
+
+
+def batched_spec(ntr, rank=0, events=0, stride=1):
     from paper_2212_07597_gb300 import tracegen as tg
-    lens = tg.batched_lengths(4096, seed=2 + rank)[:ntr].astype(np.int64)
+    lens = tg.batched_lengths(4096, seed=2 + rank)[batched_ids(ntr, stride)].astype(np.int64)
     if events:
         lens = np.minimum(lens, events)
     return lens, lens // 10
 
 
-def batched_config(ntr, lens, mlen):
+def batched_config(ntr, lens, mlen, stride=1):
     from paper_2212_07597_gb300 import tracegen as tg
-    return {"workload": f"batched: {ntr:,} traces, {int(lens.sum()):,} events, {int(mlen.sum()):,} memcpys, "
+    every = f" (every {stride}th of 4,096)" if stride > 1 else ""
+    return {"workload": f"batched: {ntr:,} traces{every}, {int(lens.sum()):,} events, {int(mlen.sum()):,} memcpys, "
                         f"log-uniform 10k-4M, 4,096 lines, leak injection every 100th trace",
             "threshold": tg.T_PLAIN, "n_lines": 4096, "memcpys": int(mlen.sum()),
             "l2": f"inputs larger than L2 ({(EVENT_BYTES * lens.sum() + COPY_BYTES * mlen.sum()) / 1e9:.0f} GB), "
@@ -363,12 +371,14 @@ def run_reference(args):
         return 0
     from paper_2212_07597_gb300 import tracegen as tg
     if args.workload == "batched":
-        ntr = args.traces or 4096
-        lens, mlen = batched_spec(ntr, 0, args.events)
+        ids = batched_ids(args.traces or 4096 // max(1, args.stride), args.stride)
+        ntr = len(ids)
+        lens, mlen = batched_spec(ntr, 0, args.events, args.stride)
         pick = batched_sample(lens)
-        trs = [t for _, t in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2), pick, host_cores())]
+        trs = [t for _, t in chunked(lambda i: tg.batched_trace(int(ids[i]), int(lens[i]), seed=2), pick,
+                                     host_cores())]
         T, L = tg.T_PLAIN, 4096
-        config = batched_config(ntr, lens, mlen)
+        config = batched_config(ntr, lens, mlen, args.stride)
         sample = f"{len(pick)} of the batch's traces (512 evenly spaced by length + the leaking ones)"
     elif args.workload == "sweep":
         per, n = (args.traces or 1024), (args.events or 1_000_000)
@@ -498,8 +508,9 @@ def run_batched(args):
     import torch
     from paper_2212_07597_gb300 import tracegen as tg
     ws, rank, scl = init_dist_and_lib()
-    ntr = args.traces or 4096
-    lens, mlen = batched_spec(ntr, rank, args.events)
+    ids = batched_ids(args.traces or 4096 // max(1, args.stride), args.stride)
+    ntr = len(ids)
+    lens, mlen = batched_spec(ntr, rank, args.events, args.stride)
     eo = np.concatenate([[0], np.cumsum([pad16(x) for x in lens])])
     co = np.concatenate([[0], np.cumsum([pad16(x) for x in mlen])])
     N, M = int(eo[-1]), int(co[-1])
@@ -511,7 +522,7 @@ def run_batched(args):
             torch.empty(M, dtype=torch.uint8, device=dev)]
     views = (np.int64, np.int64, np.int32, np.uint8)
     t_gen = time.perf_counter()
-    for i, tr in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2 + rank), list(range(ntr)),
+    for i, tr in chunked(lambda i: tg.batched_trace(int(ids[i]), int(lens[i]), seed=2 + rank), list(range(ntr)),
                          min(32, host_cores())):
         a, b = int(eo[i]), int(co[i])
         for c, x, v in zip(cols[:4], (tr.delta, tr.addr, tr.line, tr.is_python), views):
@@ -586,7 +597,8 @@ def run_batched(args):
         step()
         scl.scl_sync(ctx)
         pick = batched_sample(lens)
-        trs = [t for _, t in chunked(lambda i: tg.batched_trace(i, int(lens[i]), seed=2 + rank), pick, host_cores())]
+        trs = [t for _, t in chunked(lambda i: tg.batched_trace(int(ids[i]), int(lens[i]), seed=2 + rank), pick,
+                                     host_cores())]
         os_, walls, cores = oracle_parallel(trs, tg.T_PLAIN, 4096, reps=3)
         ev = int(lens[pick].sum())
         wall = statistics.median(walls)
@@ -635,7 +647,7 @@ def run_batched(args):
                          f"stats and leak scores of every trace out"}
 
     if rank == 0:
-        config = dict(batched_config(ntr, lens, mlen),
+        config = dict(batched_config(ntr, lens, mlen, args.stride),
                       parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
         line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": tmax / args.steps, "higher_is_better": True,
