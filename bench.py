@@ -73,7 +73,7 @@ def parse(argv=None):
     p.add_argument("--segs", type=int, default=0, help="serving: segments per process (default 16)")
     p.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     p.add_argument("--tuning", default="", help="fixed tuning instead of the autotuner: unit,phase1_warps,"
-                                                "warmup,final_warps,first,fixup (e.g. 524288,16,32768,10,1572864,0)")
+                                                "warmup,final_warps,first,fixup[,piece] (e.g. 524288,16,32768,10,1572864,0,65536)")
     p.add_argument("--tune", action="store_true", help="long/plain: run the autotuner before timing")
     p.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi clock sampling (profiler runs)")
     p.add_argument("--no-rate", action="store_true", help="long/plain: skip the rate-based sampling comparison")
@@ -485,7 +485,8 @@ def timed(step, steps, warmup, stream, barrier, clocks_on):
 
 def tuning_dict(t, ms=None):
     d = {"unit_events": t.unit_events, "first_events": t.first_events, "phase1_warps": t.warps_per_block,
-         "warmup_events": t.ext_events, "final_warps": t.final_warps, "fixup": t.fixup}
+         "warmup_events": t.ext_events, "final_warps": t.final_warps, "fixup": t.fixup,
+         "piece_events": t.piece_events}
     if ms is not None:
         d["ms"] = ms
     return d

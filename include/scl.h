@@ -239,8 +239,9 @@ int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
  * segments (a warm-up call, then the mean of three calls issued back to back, so that each
  * call's host-side planning overlaps the previous call's device work as in repeated use;
  * the results of these calls are discarded) and searches one setting at a time,
- * twice over: unit 32k/64k/128k/256k/512k, first unit unit/512k/1M/1.25M/1.5M, phase-1
- * warps 8/12/16, replay warps 10/14, warm-up 16k/32k, fix-up 0/1.  It restores the
+ * twice over: unit 32k/64k/128k/256k/512k/1M, first unit unit/512k/1M/1.25M/1.5M, phase-1
+ * warps 8/12/16, replay warps 10/14, warm-up 16k/32k, fix-up 0/1, replay pieces
+ * 32k/64k/128k/4M.  It restores the
  * touched traces' state before every run and at the end, keeps the fastest setting in the
  * context (read it back with scl_tuning_get), and allocates one device buffer for the
  * saved states. */
@@ -255,6 +256,10 @@ typedef struct {
     uint32_t fixup;          /* how the exact replay of a sketched unit finds its samples once its entry is
                                 known: 0 = from every reset the sketch listed for that run (default),
                                 1 = by searching each step's prefix sums for crossings */
+    uint32_t piece_events;   /* the exact replay of a sketched unit whose resets are listed is cut into
+                                pieces replayed in parallel, each ending at the first listed reset past
+                                the next multiple of piece_events (after a reset the counter and the
+                                window restart from zero); multiple of 256; 0 = 65536 */
 } scl_tuning;
 int scl_tuning_get(const scl_ctx *ctx, scl_tuning *out);
 int scl_tuning_set(scl_ctx *ctx, const scl_tuning *t);

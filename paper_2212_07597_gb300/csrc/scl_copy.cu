@@ -16,7 +16,8 @@
 // published sums and prefixes (a decoupled look-back: a predecessor publishes its sum
 // before it waits on anything, and it took its ticket earlier, so every wait ends; waits
 // are bounded), publishes its own prefix, and applies the samples; counts of lines below
-// CB_HOT gather in shared memory and reach the trace's counts once per tile.
+// CB_HOT gather in shared memory and reach the trace's counts when the block moves to
+// another trace's tile (a long trace's consecutive tiles share one flush).
 #include <algorithm>
 #include <cstddef>
 
@@ -28,14 +29,13 @@ namespace scl {
 constexpr int CB_THREADS = 256;
 constexpr int CB_PER = COPY_TILE / CB_THREADS;   // memcpys per thread (16)
 constexpr uint32_t CB_HOT = 1024;                // lines counted in shared memory per tile
-constexpr uint32_t CS_AGG = 1u, CS_INCL = 2u;
+constexpr uint32_t CB_FLUSH = 1024;              // tiles of one trace a block counts before a flush
 
-struct CopyStatus {               // one per tile, cleared before each batch
-    unsigned long long agg;       // the tile's bytes modulo T_c (valid from CS_AGG on)
-    unsigned long long incl;      // the counter after the tile, modulo T_c (CS_INCL)
-    unsigned int flag;
-    unsigned int pad;
-};
+// The look-back state of a tile is one 64-bit word, cleared before each batch, so a reader
+// gets flag and value in one load: 0 = nothing yet; 1 .. 2^63 - 1 = the tile's bytes modulo
+// T_c, plus one (its aggregate); 2^63 | v = the counter after the tile, modulo T_c (its
+// inclusive prefix).  Every residue is below T_c < 2^63, so both forms fit.
+constexpr unsigned long long CS_INCL = 1ull << 63;
 
 struct alignas(16) CopyTask {     // the tile a block works on, written by thread 0 (16-byte stores)
     CopyTile ct;
@@ -43,7 +43,7 @@ struct alignas(16) CopyTask {     // the tile a block works on, written by threa
 };
 
 struct alignas(16) CopyBlockSmem {
-    uint32_t hot[2 * CB_HOT];     // [line][flag] sample counts of the tile (32 bits: see below)
+    uint32_t hot[2 * CB_HOT];     // [line][flag] sample counts of the trace's tiles since the last flush
     unsigned long long wsum[CB_THREADS / 32];
     unsigned long long base;
     CopyTask task[2];             // the current tile and the next
@@ -59,10 +59,17 @@ __device__ __forceinline__ unsigned long long madd(unsigned long long a, unsigne
     return s >= Tc ? s - Tc : s;
 }
 
-// the value, then the flag with release semantics: a reader that acquires the flag sees it
-__device__ __forceinline__ void cs_publish(CopyStatus *st, unsigned long long v, bool inclusive) {
-    if (inclusive) st->incl = v; else st->agg = v;
-    st_release(&st->flag, inclusive ? CS_INCL : CS_AGG);
+// a tile's aggregate or inclusive prefix (the word carries everything a reader needs, so
+// relaxed ordering suffices)
+__device__ __forceinline__ void cs_publish(unsigned long long *st, unsigned long long v, bool inclusive) {
+    const unsigned long long w = inclusive ? (CS_INCL | v) : v + 1;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(st), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long cs_load(const unsigned long long *st) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(st) : "memory");
+    return w;
 }
 
 // the tile of ticket `it` (its description is one 48-byte record of the plan)
@@ -78,12 +85,24 @@ __device__ __forceinline__ void copy_job(const LaunchCopy &a, unsigned it, CopyT
 __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
     __shared__ CopyBlockSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    CopyStatus *status = static_cast<CopyStatus *>(a.cstatus);
+    unsigned long long *status = static_cast<unsigned long long *>(a.cstatus);
     const unsigned long long Tc = a.Tc;
     const bool small = Tc <= (1ull << 60);
     const unsigned long long Tc2 = 2 * Tc, Tc4 = 4 * Tc, Tc8 = 8 * Tc;   // (small: no overflow)
     const uint32_t hot = a.n_lines < CB_HOT ? a.n_lines : CB_HOT;
     for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) sm.hot[i] = 0u;
+    // the table holds counts of trace `held` from `nheld` tiles (block-uniform)
+    uint32_t held = 0xffffffffu, nheld = 0;
+    auto flush = [&]() {
+        unsigned long long *gc = a.copies + (uint64_t)held * a.n_lines * 2;
+        for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) {
+            const uint32_t c = sm.hot[i];
+            if (c) {
+                atomicAdd(&gc[i], (unsigned long long)c);
+                sm.hot[i] = 0u;
+            }
+        }
+    };
     // thread 0 holds the ticket of the tile after the next one, so the ticket's round trip
     // overlaps a whole tile and only the record's load overlaps the tile's own loads.  (A
     // block takes tickets in order and works its tiles in that order, and a tile waits only
@@ -98,6 +117,15 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
         const CopyTask &K = sm.task[cur];
         if (!K.valid) break;
         const CopyTile ct = K.ct;
+        if (ct.trace != held || nheld == CB_FLUSH) {
+            // another trace's counts (or enough tiles that the next could near 2^32) leave the
+            // table first; the barrier at the end of the tile orders the clearing before its use
+            if (held != 0xffffffffu) flush();
+            held = ct.trace;
+            nheld = 0;
+            __syncthreads();
+        }
+        ++nheld;
         const uint32_t len = ct.len, t = ct.t;
         // ---- this thread's CB_PER consecutive memcpys, loaded into registers
         const uint32_t e0 = (uint32_t)tid * CB_PER;
@@ -182,7 +210,7 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
         }
         if (lane == 31) sm.wsum[w] = x;
         __syncthreads();
-    if (w == 0) {
+        if (w == 0) {
             const unsigned long long y = lane < CB_THREADS / 32 ? sm.wsum[lane] : 0ull;
             unsigned long long yi = y;
 #pragma unroll
@@ -206,23 +234,28 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                 while (true) {
                     // lane j looks at tile p - j (tiles before the trace's first count as its start)
                     const int64_t q = p - lane;
-                    unsigned int f = CS_INCL;
-                    unsigned long long val = 0;
+                    unsigned long long wd = CS_INCL;   // (before the trace: its start)
                     if (q >= (int64_t)ct.c0) {
                         unsigned long long n = 0;
-                        while ((f = ld_acquire(&status[q].flag)) == 0 && n < a.spin) ++n;
-                        if (f == CS_INCL) val = status[q].incl;
-                        else if (f == CS_AGG) val = status[q].agg;
+                        // a predecessor publishes its aggregate a few microseconds after it
+                        // starts: poll with a short pause, so the waiting lanes leave the L2
+                        // to the stores they wait for
+                        while ((wd = cs_load(&status[q])) == 0 && n < a.spin) {
+                            ++n;
+                            __nanosleep(64);
+                        }
                     } else if (q == (int64_t)ct.c0 - 1) {
-                        val = a.traces[ct.trace].copy_counter;
+                        wd = CS_INCL | a.traces[ct.trace].copy_counter;
                     }
-                    if (!__all_sync(FULL, f != 0)) {
+                    if (!__all_sync(FULL, wd != 0)) {
                         if (lane == 0) set_error(a.err, E_TIMEOUT, 20, t);
                         ok = false;
                         break;
                     }
+                    const bool incl = (wd & CS_INCL) != 0;
+                    const unsigned long long val = incl ? wd & ~CS_INCL : wd - 1;
                     // the nearest predecessor with a prefix ends the look-back
-                    const unsigned done = __ballot_sync(FULL, f == CS_INCL);
+                    const unsigned done = __ballot_sync(FULL, incl);
                     const int stop = done ? __ffs(done) - 1 : 32;
                     unsigned long long wv = lane <= stop ? val : 0ull;
 #pragma unroll
@@ -254,8 +287,9 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                 return;
             }
             const int f = ((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0;
-            // the shared table takes counts of at most 8 per memcpy, so a tile adds at most
-            // 4,096 x 8 per entry and the 32-bit counts cannot wrap; larger ones go to global
+            // the shared table takes counts of at most 8 per memcpy, so CB_FLUSH tiles add at most
+            // 1,024 x 4,096 x 8 = 2^25 per entry and the 32-bit counts cannot wrap; larger
+            // counts go to global memory
             if (l < hot && qn <= 8) atomicAdd(&sm.hot[2 * l + f], qn);
             else atomicAdd(&gc[2 * l + f], (unsigned long long)qn);
         };
@@ -305,19 +339,13 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                 atomicAdd(&gc[2 * l + (((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0)], qn);
             }
         }
+        // (this barrier also ends every use of the tile's shared words before the next tile)
         if (__syncthreads_or(ovf) && tid == 0) set_error(a.err, E_OVERFLOW, 7, t);
-        for (uint32_t i = tid; i < 2 * hot; i += CB_THREADS) {
-            const uint32_t c = sm.hot[i];
-            if (c) {
-                atomicAdd(&gc[i], (unsigned long long)c);
-                sm.hot[i] = 0u;
-            }
-        }
-        __syncthreads();   // the table and this tile's task slot are reused
     }
+    if (held != 0xffffffffu) flush();
 }
 
-size_t copy_status_bytes(size_t ntiles) { return sizeof(CopyStatus) * ntiles; }
+size_t copy_status_bytes(size_t ntiles) { return sizeof(unsigned long long) * ntiles; }
 
 cudaError_t launch_copy(const LaunchCopy &a, cudaStream_t s) {
     if (!a.nctiles) return cudaSuccess;

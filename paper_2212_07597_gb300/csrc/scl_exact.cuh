@@ -22,16 +22,24 @@
 
 namespace scl {
 
-struct ExactIn {                 // the state entering the unit
+struct ExactIn {                 // the state entering the unit (or the piece of it replayed)
     int64_t c;                   // counter
     int64_t wA, wApy, wSpy;      // this lane's share of the open-window totals so far
     int64_t mark;                // high-water mark
     int64_t fpb;                 // footprint before the unit
-    uint32_t tk;                 // tracked block: 0 none, 1/2 entering (see UnitPlan), 3 own sample
+    uint32_t tk;                 // tracked block: 0 none, 1/2 entering (see UnitPlan), 3 a sample of the unit
+    uint32_t tslot;              // tk = 3: the record of that sample
     uint64_t taddr;
     const SRes *list;            // the unit's resets in order, or nullptr: search
     uint32_t nres;               // resets listed
     int64_t exit_c;              // counter after the unit (with a list)
+    // the span replayed: events [from, limit) are staged; with a list, entries [n0, rend) are
+    // the resets it closes, and with `stop` it ends at the last of them.  A whole unit has
+    // from = 0, limit = len, n0 = 0, rend = nres, stop = false.
+    uint32_t from, limit;
+    uint32_t n0, rend;
+    int64_t P0;                  // unit-local prefix sum before `from`
+    bool stop;
 };
 
 struct ExactRun {                // FIRST only: the run's facts, as the sketch records them for a candidate
@@ -43,8 +51,11 @@ struct ExactRun {                // FIRST only: the run's facts, as the sketch r
     int64_t P;                   // unit total
 };
 
-// Replays unit U; writes its records to out[0 .. cap) and returns false if a wait timed
-// out.  n (records taken), enter_hit and the state after the unit are returned.
+// Replays unit U (or one piece of it); writes its records to out[n0 .. cap) and returns false
+// if a wait timed out.  n (records taken up to the span's end), enter_hit and the state after
+// the span are returned; `prior` is 1 + the record of an earlier piece whose block a free of
+// this span hit (0: none), which the caller leaves to a later pass: that record may still be
+// in flight from the warp replaying its piece.
 //
 // The open window's totals are kept warp-uniform.  A step whose deltas all lie in
 // [-2^22, 2^22) has lane sums and a warp sum below 2^30 in magnitude, so its share of a
@@ -55,7 +66,7 @@ struct ExactRun {                // FIRST only: the run's facts, as the sketch r
 template <bool FIRST, class RingT>
 __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const ExactIn &in0, FRec *out, uint32_t cap,
                            int64_t T, unsigned long long spin, ErrWord *err, int lane, uint32_t &n_out,
-                           UnitOut &O, ExactRun *R) {
+                           UnitOut &O, ExactRun *R, uint32_t &prior) {
     constexpr int E = RingT::kE, STEP = 32 * E;
     static_assert(E == 8, "a lane's events fit one byte of bits");
     int64_t accA = warp_sum(in0.wA), accApy = warp_sum(in0.wApy), accSpy = warp_sum(in0.wSpy);
@@ -65,17 +76,20 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
     const int64_t fpb = in0.fpb;
     uint32_t tk = in0.tk;
     uint64_t taddr = in0.taddr;
-    uint32_t tslot = 0;
+    uint32_t tslot = in0.tslot;
     uint32_t enter_hit = 0;
-    uint32_t n = 0;
+    uint32_t n = in0.n0;
+    prior = 0;
     // FIRST: the run's facts (lane-uniform)
     int64_t gmax = INT64_MIN, tmax = INT64_MIN;
     uint32_t garg = 0, targ = 0;
     int32_t last = -1;
 
     auto hit_tracked = [&]() {
-        if (tk == 3) {
+        if (tk == 3 && tslot >= in0.n0) {
             if (lane == 0 && tslot < cap) out[tslot].recl = 1;
+        } else if (tk == 3) {
+            prior = tslot + 1;
         } else {
             enter_hit = 1;
         }
@@ -189,28 +203,33 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         // the list is read 32 entries at a time (lane j holds entry base + j), the next
         // 32 loading while the current ones are used
         const SRes *Ls = in0.list;
-        const uint32_t nres = in0.nres;
+        const uint32_t rend = in0.rend;
         auto fetch = [&](uint32_t base, uint32_t &bp, int64_t &bP) {
             const uint32_t i = base + (uint32_t)lane;
-            if (i < nres) { const SRes q = Ls[i]; bp = q.pos; bP = q.P; } else { bp = 0xffffffffu; bP = 0; }
+            if (i < rend) { const SRes q = Ls[i]; bp = q.pos; bP = q.P; } else { bp = 0xffffffffu; bP = 0; }
         };
+        // lane j holds entry (ri & ~31) + j, the next 32 loading behind them
+        uint32_t ri = in0.n0;
         uint32_t cpos, npos_b;
         int64_t cP, nP_b;
-        fetch(0, cpos, cP);
-        fetch(32, npos_b, nP_b);
-        uint32_t ri = 0;
-        uint32_t npos = __shfl_sync(FULL, cpos, 0);
-        int64_t nP = __shfl_sync(FULL, cP, 0);
-        if (!nres) npos = 0xffffffffu;
-        int64_t cst = c, Pprev = 0;   // counter at the open window's start, prefix there
+        fetch(ri & ~31u, cpos, cP);
+        fetch((ri & ~31u) + 32, npos_b, nP_b);
+        uint32_t npos = __shfl_sync(FULL, cpos, (int)(ri & 31u));
+        int64_t nP = __shfl_sync(FULL, cP, (int)(ri & 31u));
+        if (ri >= rend) npos = 0xffffffffu;
+        int64_t cst = c, Pprev = in0.P0;   // counter at the open window's start, prefix there
+        bool done = false;
+        const uint32_t from = in0.from;
         auto kstep = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
             const bool fits = __all_sync(FULL, step_fits32(in));
-            if (npos >= rel0 + (uint32_t)STEP) {
+            // a piece's first step leaves out the events before it
+            const int a0 = rel0 < from ? (int)(from - rel0) - 1 : -1;
+            if (a0 < 0 && npos >= rel0 + (uint32_t)STEP) {
                 whole_step(in, fits);
                 return false;
             }
             uint32_t fb = free_bits(in);
-            int after = -1;
+            int after = a0;
             while (npos < rel0 + (uint32_t)STEP) {
                 if (npos < rel0 + (uint32_t)(after + 1)) {   // positions must increase
                     if (lane == 0) set_error(err, E_INTERNAL, 12, (unsigned long long)U.gidx0);
@@ -223,7 +242,7 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                 cst = 0;
                 Pprev = nP;
                 after = r;
-                if (++ri < nres) {
+                if (++ri < rend) {
                     if ((ri & 31u) == 0) {
                         cpos = npos_b;
                         cP = nP_b;
@@ -233,13 +252,15 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
                     nP = __shfl_sync(FULL, cP, (int)(ri & 31u));
                 } else {
                     npos = 0xffffffffu;
+                    done = in0.stop;
                 }
             }
+            if (done) return true;   // the piece ends at this reset: the rest is the next piece's
             if (tk && __any_sync(FULL, (fb & range(after, STEP - 1)) != 0)) hit_tracked();
             fold(in, fits, range(after, STEP - 1), std::false_type{});
             return false;
         };
-        ok = ring_walk<true>(sm, U, 0, U.len, phase, spin, err, lane, kstep);
+        ok = ring_walk<true>(sm, U, from / STEP * STEP, in0.limit, phase, spin, err, lane, kstep);
         c = in0.exit_c;
     } else {
         // ---- search for the crossings from the entry counter (in the 32-bit form of a

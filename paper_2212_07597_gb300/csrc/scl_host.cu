@@ -51,7 +51,7 @@ struct scl_ctx {
     uint64_t last_first_events = 0, last_sketch_events = 0;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
-    DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage;
+    DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage, phit;
     DevBuf rate;   // scratch of scl_rate_samples
     DevBuf report; // rows of scl_leak_report
     DevBuf tline;  // scratch and output of scl_line_timeline
@@ -212,9 +212,9 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 struct EnqArgs {
     char *dp;
     const char *hp;
-    size_t blob, o_units, o_bts, o_grp, o_ct, o_ord;
+    size_t blob, o_units, o_bts, o_grp, o_ct, o_ord, o_fit;
     uint32_t nbt;
-    int nunits, ngroups, nctiles;
+    int nunits, ngroups, nctiles, nitems;
 };
 
 // The device work of one replay call, in stream order (captured into a graph when
@@ -266,6 +266,7 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
     a.Tc = (uint64_t)cfg.copy_multiple * (uint64_t)cfg.threshold;
     a.groups = reinterpret_cast<const CompactGroup *>(dp + q.o_grp);
     a.ngroups = q.ngroups;
+    a.phit = static_cast<const uint32_t *>(c->phit.p);
     a.err = c->errw;
     // ---- the copy-volume sampler, on a side stream forked after phase 1 (before the scan when
     // there are no units): beside the chain, the scans and the bandwidth-bound exact replay
@@ -355,6 +356,10 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         LaunchFinal f;
         f.units = d_units;
         f.nunits = nunits;
+        f.items = reinterpret_cast<const FItem *>(dp + q.o_fit);
+        f.nitems = q.nitems;
+        f.phit = static_cast<uint32_t *>(c->phit.p);
+        f.piece = c->tune.piece_events ? c->tune.piece_events : FINAL_PIECE;
         f.utrue = a.utrue;
         f.uplan = a.uplan;
         f.lists = static_cast<const SRes *>(c->lists.p);
@@ -365,12 +370,12 @@ int enqueue_batch(scl_ctx *c, cudaStream_t s, const EnqArgs &q, bool record_plan
         f.err = c->errw;
         f.spin = cfg.spin_limit;
         f.stats = c->stats;
-        f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (nunits + c->num_sms - 1) / c->num_sms));
+        f.warps_per_block = std::max(1, std::min((int)c->tune.final_warps, (q.nitems + c->num_sms - 1) / c->num_sms));
         int bps = 0;
         // fewer warps per block if the requested block does not fit an SM
         while (f.warps_per_block > 1 && (final_occupancy(f.warps_per_block, &bps) || bps < 1)) --f.warps_per_block;
         if (final_occupancy(f.warps_per_block, &bps) || bps < 1) bps = 1;
-        f.blocks = std::max(1, std::min(bps * c->num_sms, (nunits + f.warps_per_block - 1) / f.warps_per_block));
+        f.blocks = std::max(1, std::min(bps * c->num_sms, (q.nitems + f.warps_per_block - 1) / f.warps_per_block));
         Prof p(c, s, "final");
         CK(launch_final(f, s), "launch final");
     }
@@ -457,7 +462,7 @@ void scl_replay_free(scl_ctx *c) {
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->lists, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
-                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report, &c->tline})
+                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report, &c->tline, &c->phit})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
@@ -578,9 +583,10 @@ int scl_tuning_set(scl_ctx *c, const scl_tuning *t) {
     if (!c || !t) return SCL_EINVAL;
     if (t->unit_events % UNIT_ALIGN || t->first_events % UNIT_ALIGN || t->warps_per_block < 1 ||
         t->warps_per_block > 16 || t->final_warps < 1 || t->final_warps > 14 || (t->ext_events % 256) ||
-        t->fixup > 1)
+        t->fixup > 1 || (t->piece_events % 256))
         return fail(c, SCL_EINVAL, "tuning: unit_events and first_events multiples of 1024 (0: default), "
-                                   "warps_per_block 1..16, final_warps 1..14, ext_events multiple of %d, fixup 0/1",
+                                   "warps_per_block 1..16, final_warps 1..14, ext_events and piece_events "
+                                   "multiples of %d, fixup 0/1",
                     256);
     c->tune = *t;
     return SCL_OK;
@@ -716,6 +722,16 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
 
     // ---- phase-1 order: longest work first (a first unit's exact replay costs about twice
     // a sketched unit's events; a sketched unit also streams its warm-up)
+    // ---- k_final's pieces: every unit but a trace's first, cut every piece_events (at the next
+    // listed reset, found on the device)
+    std::vector<FItem> fitems;
+    const uint64_t piece = c->tune.piece_events ? c->tune.piece_events : FINAL_PIECE;
+    for (uint32_t u = 0; u < (uint32_t)units.size(); ++u) {
+        Unit &U = units[u];
+        U.fi0 = (uint32_t)fitems.size();
+        U.fnp = U.first ? 0u : (uint32_t)((U.len + piece - 1) / piece);
+        for (uint32_t p = 0; p < U.fnp; ++p) fitems.push_back({u, p});
+    }
     std::vector<uint32_t> p1order(units.size());
     {
         const uint64_t W = c->tune.ext_events ? c->tune.ext_events : 32768;
@@ -748,7 +764,8 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     const size_t o_grp = al256(o_bts + sizeof(BTrace) * bts.size());
     const size_t o_ct = al256(o_grp + sizeof(CompactGroup) * cgroups.size());
     const size_t o_ord = al256(o_ct + sizeof(CopyTile) * ctiles.size());
-    const size_t blob = al256(o_ord + sizeof(uint32_t) * p1order.size());
+    const size_t o_fit = al256(o_ord + sizeof(uint32_t) * p1order.size());
+    const size_t blob = al256(o_fit + sizeof(FItem) * fitems.size());
     if (c->plan_pending) {
         CK(cudaEventSynchronize(c->plan_done), "wait for previous plan upload");
         c->plan_pending = false;
@@ -766,6 +783,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     memcpy(hp + o_grp, cgroups.data(), sizeof(CompactGroup) * cgroups.size());
     memcpy(hp + o_ct, corder.data(), sizeof(CopyTile) * corder.size());
     memcpy(hp + o_ord, p1order.data(), sizeof(uint32_t) * p1order.size());
+    memcpy(hp + o_fit, fitems.data(), sizeof(FItem) * fitems.size());
 
     int r;
     if ((r = ensure(c, c->plan, blob, s, "plan buffer"))) return r;
@@ -784,6 +802,7 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
     if ((r = ensure(c, c->btres, sizeof(BTraceRes) * nbt, s, "batch trace results"))) return r;
     if ((r = ensure(c, c->ctsum, copy_status_bytes(std::max<size_t>(1, ctiles.size())), s, "copy tile states")))
         return r;
+    if ((r = ensure(c, c->phit, sizeof(uint32_t) * std::max<size_t>(1, fitems.size()), s, "piece reports"))) return r;
 
     char *dp = static_cast<char *>(c->plan.p);
     c->last_units = units.size();
@@ -802,13 +821,14 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
         c->last_sketch_events = se;
     }
     c->last_stream = s;
-    EnqArgs q{dp, hp, blob, o_units, o_bts, o_grp, o_ct, o_ord, nbt, nunits, (int)cgroups.size(), (int)ctiles.size()};
+    EnqArgs q{dp,     hp,    blob,  o_units, o_bts,  o_grp, o_ct, o_ord, o_fit, nbt, nunits, (int)cgroups.size(),
+              (int)ctiles.size(), (int)fitems.size()};
     if (c->graph_on && !c->prof && s != nullptr) {
         // relaunch when the plan bytes, the buffers and the tuning equal the captured batch's:
         // the graph is then exactly this batch's work
         const std::vector<const void *> ptrs = {c->plan.p, c->usum.p, c->cand.p, c->lists.p, c->match.p,
                                                 c->uwalk.p, c->utrue.p, c->umode.p, c->uexp.p, c->uplan.p,
-                                                c->uout.p, c->pref.p, c->recs.p, c->btres.p, c->ctsum.p};
+                                                c->uout.p, c->pref.p, c->recs.p, c->btres.p, c->ctsum.p, c->phit.p};
         const bool same = c->gexec && c->g_blob == blob && c->g_ptrs == ptrs &&
                           memcmp(&c->g_tune, &c->tune, sizeof c->tune) == 0 && memcmp(c->g_plan, hp, blob) == 0;
         if (!same) {
@@ -1324,12 +1344,13 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     };
     // coordinate descent, two passes: each setting in turn takes its best value with the
     // others held at the best found so far
-    const uint32_t units[] = {32768, 65536, 131072, 262144, 524288};
+    const uint32_t units[] = {32768, 65536, 131072, 262144, 524288, 1048576};
     const uint32_t firsts[] = {0, 524288, 1048576, 1310720, 1572864};
     const uint32_t pwarps[] = {8, 12, (uint32_t)PHASE1_MAX_WARPS};
     const uint32_t fwarps[] = {10, 14};
     const uint32_t warm[] = {16384, 32768};
     const uint32_t fixups[] = {0, 1};
+    const uint32_t pieces[] = {32768, 65536, 131072, 1u << 22};   // (the last: no unit is cut)
     scl_tuning start = keep;
     if (start.ext_events == 0) start.ext_events = 32768;
     measure(start);
@@ -1340,6 +1361,7 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
         for (uint32_t v : fwarps) { scl_tuning t = best; t.final_warps = v; if (!rc) measure(t); }
         for (uint32_t v : warm) { scl_tuning t = best; t.ext_events = v; if (!rc) measure(t); }
         for (uint32_t v : fixups) { scl_tuning t = best; t.fixup = v; if (!rc) measure(t); }
+        for (uint32_t v : pieces) { scl_tuning t = best; t.piece_events = v; if (!rc) measure(t); }
     }
     if (copy_state(false) != cudaSuccess && !rc) rc = SCL_ECUDA;
     cudaStreamSynchronize(s);

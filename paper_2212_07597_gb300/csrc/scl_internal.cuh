@@ -19,6 +19,7 @@ constexpr int STEP = 32 * E;       // events per walker step
 constexpr int TILE = 256;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
 constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
+constexpr uint64_t FINAL_PIECE = 65536;   // k_final cuts units into pieces of about this many events
 constexpr int COPY_TILE = 4096;    // memcpy events per block of the copy samplers
 constexpr int SMEM_LINES_MAX = 1024;  // per-line tables kept in shared memory up to this L
 
@@ -66,7 +67,18 @@ struct Unit {
     uint32_t first, last; // first / last unit of its trace in this batch
     uint32_t lst_cap;     // reset-list slots per candidate run of the unit
     uint64_t lst0;        // first reset-list slot of the unit (NL lists of lst_cap)
+    uint32_t fi0, fnp;    // the unit's pieces in k_final: items fi0 .. fi0 + fnp - 1 (none for a first unit)
 };
+
+// A piece of a unit for k_final.  Piece p of a unit whose true run has a reset list covers the
+// events after the first listed reset at or past p * piece_events (the unit start for p = 0)
+// up to and including the first listed reset at or past (p + 1) * piece_events (the unit end
+// if there is none).  After a reset the counter is 0 and the window empty, so a piece's entry
+// state follows from the list alone.  A unit without a list is replayed whole by its piece 0.
+struct FItem {
+    uint32_t u, p;
+};
+constexpr uint32_t PHIT_ENTER = 0xffffffffu;   // a piece freed the block tracked entering its unit
 
 struct BTrace {           // one per trace present in the batch
     uint32_t trace, u0, nu, pad;   // slot, first unit, unit count

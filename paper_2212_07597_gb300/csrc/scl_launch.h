@@ -43,6 +43,10 @@ struct LaunchFinal {
     unsigned long long *stats;   // [5]: units replayed with the crossing search
     const Unit *units;
     int nunits;
+    const FItem *items;          // the pieces, in the order warps take them
+    int nitems;
+    uint32_t *phit;              // per piece: what k_mark applies (0 nothing, PHIT_ENTER, 1 + record)
+    uint64_t piece;              // events per piece (cut at the next listed reset)
     const UnitTrue *utrue;
     const UnitPlan *uplan;
     const SRes *lists;
@@ -95,6 +99,7 @@ struct LaunchPost {
     uint64_t Tc;
     const CompactGroup *groups;
     int ngroups;
+    const uint32_t *phit;  // k_final's per-piece reports (see LaunchFinal)
     ErrWord *err;
 };
 

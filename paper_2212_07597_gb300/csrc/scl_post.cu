@@ -422,11 +422,26 @@ __device__ __forceinline__ uint32_t find_record(const FRec *rec, uint32_t count,
 // ---------------------------------------------------------------- k_mark
 // Section 3.4: the block tracked when a unit starts was freed inside the unit ->
 // mark its crossing's record (or the trace's pre-batch block) reclaimed.
+//
+// The pieces of a unit replayed apart by k_final report here what they could not write
+// themselves: a free of the block an earlier piece's sample tracks (that record is marked
+// now), or of the block tracked entering the unit.
 __global__ void k_mark(LaunchPost a) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= a.nunits) return;
     const UnitOut &O = a.uout[u];
-    if (!O.enter_hit) return;
+    const Unit &U = a.units[u];
+    uint32_t enter = O.enter_hit;
+    if (U.fnp > 1) {
+        const uint32_t cnt = O.count < U.rec_cap ? O.count : U.rec_cap;
+        for (uint32_t i = U.fi0; i < U.fi0 + U.fnp; ++i) {
+            const uint32_t h = a.phit[i];
+            if (h == PHIT_ENTER) enter = 1;
+            else if (h && h - 1 < cnt) a.recs[U.rec0 + h - 1].recl = 1;
+            else if (h) set_error(a.err, E_INTERNAL, 13, (unsigned long long)u);
+        }
+    }
+    if (!enter) return;
     const UnitPlan &Pn = a.uplan[u];
     if (Pn.enter_kind == 1) {
         const Unit &W = a.units[Pn.enter_unit];

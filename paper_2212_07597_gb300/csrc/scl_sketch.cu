@@ -245,14 +245,23 @@ __device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__
     in0.fpb = st.footprint;
     in0.tk = st.tracked_valid ? 2u : 0u;   // as k_scan plans a trace's first unit
     in0.taddr = st.tracked_addr;
+    in0.tslot = 0;
     in0.list = nullptr;
     in0.nres = 0;
     in0.exit_c = 0;
+    in0.from = 0;
+    in0.limit = (uint32_t)U.len;
+    in0.n0 = 0;
+    in0.rend = 0;
+    in0.P0 = 0;
+    in0.stop = false;
     ExactRun R;
     R.C0 = cand + (size_t)u * K;
     UnitOut O;
     uint32_t n = 0;
-    const bool ok = exact_unit<true>(fr, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R);
+    uint32_t prior;   // (a whole unit: no earlier piece)
+    const bool ok = exact_unit<true>(fr, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R,
+                                     prior);
     if (!ok) return false;   // a wait timed out (the ring may not be reusable)
     Cand *C = cand + (size_t)u * K + lane;
     if (lane == 0)

@@ -86,7 +86,7 @@ REQUEST_RESULT_DTYPE = np.dtype([("done_ns", "<u8"), ("latency_ns", "<u8"), ("ba
 class scl_tuning(ctypes.Structure):
     _fields_ = [("unit_events", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
                 ("ext_events", ctypes.c_uint32), ("final_warps", ctypes.c_uint32),
-                ("first_events", ctypes.c_uint32), ("fixup", ctypes.c_uint32)]
+                ("first_events", ctypes.c_uint32), ("fixup", ctypes.c_uint32), ("piece_events", ctypes.c_uint32)]
 
 
 SAMPLE_DTYPE = np.dtype([
@@ -348,8 +348,8 @@ def scl_tuning_get(ctx: Context) -> scl_tuning:
 
 
 def scl_tuning_set(ctx: Context, unit_events: int, warps_per_block: int = 16, ext_events: int = 0,
-                   final_warps: int = 14, first_events: int = 0, fixup: int = 0) -> None:
-    t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps, first_events, fixup)
+                   final_warps: int = 14, first_events: int = 0, fixup: int = 0, piece_events: int = 0) -> None:
+    t = scl_tuning(unit_events, warps_per_block, ext_events, final_warps, first_events, fixup, piece_events)
     _check(ctx, load().scl_tuning_set(ctx.handle, ctypes.byref(t)))
 
 
