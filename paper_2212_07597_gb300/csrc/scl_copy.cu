@@ -103,15 +103,12 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
             }
         }
     };
-    // thread 0 holds the ticket of the tile after the next one, so the ticket's round trip
-    // overlaps a whole tile and only the record's load overlaps the tile's own loads.  (A
-    // block takes tickets in order and works its tiles in that order, and a tile waits only
-    // on tiles of lower tickets: the lowest unfinished ticket can always proceed.)
-    unsigned tk = 0;
-    if (tid == 0) {
-        copy_job(a, atomicAdd(a.queue, 1u), sm.task[0]);
-        tk = atomicAdd(a.queue, 1u);
-    }
+    // A block takes its next ticket once its current tile has found its entering counter,
+    // so the fetch overlaps the tile's samples.  A ticket taken earlier would sit unstarted
+    // while other tiles wait on its sum (in a long trace, consecutive tickets are consecutive
+    // tiles).  A tile waits only on tiles of lower tickets, all of them started, so the
+    // lowest unfinished ticket can always proceed.
+    if (tid == 0) copy_job(a, atomicAdd(a.queue, 1u), sm.task[0]);
     __syncthreads();
     for (int cur = 0;; cur ^= 1) {
         const CopyTask &K = sm.task[cur];
@@ -161,11 +158,6 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
                 for (int b = 0; b < 4; ++b) x |= (e0 + 4 * q + b < len ? (uint32_t)ct.py[e0 + 4 * q + b] : 0u) << (8 * b);
                 pw[q] = x;
             }
-        }
-        // the next tile's ticket and description, while this one's loads are in flight
-        if (tid == 0) {
-            copy_job(a, tk, sm.task[cur ^ 1]);
-            tk = atomicAdd(a.queue, 1u);
         }
         // ---- this thread's bytes, modulo T_c.  When 8 T_c < 2^31 and every size of the thread
         // is below 8 T_c, each residue, sum and remainder below fits 32 bits (the same
@@ -276,6 +268,7 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
         }
         __syncthreads();
         if (!sm.ok) break;   // a wait gave up (uniform over the block)
+        if (tid == 0) copy_job(a, atomicAdd(a.queue, 1u), sm.task[cur ^ 1]);
         // ---- samples at each of this thread's memcpys, from the counter before the first
         unsigned long long rem = madd(madd(sm.base, sm.wsum[w], Tc), x >= ls ? x - ls : x + (Tc - ls), Tc);
         unsigned long long *gc = a.copies + (uint64_t)ct.trace * a.n_lines * 2;
