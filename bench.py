@@ -927,7 +927,10 @@ def run_single(args):
                                          sample_log_capacity=1 << 20))
     stream = torch.cuda.current_stream()
     tuned = None
-    if args.tune:
+    if args.tuning:
+        scl.scl_tuning_set(ctx, *[int(x) for x in args.tuning.split(",")])
+        tuned = dict(tuning_dict(scl.scl_tuning_get(ctx)), fixed=True)
+    elif args.tune:
         best, best_ms = scl.scl_autotune(ctx, [seg], stream)
         tuned = tuning_dict(best, best_ms)
 

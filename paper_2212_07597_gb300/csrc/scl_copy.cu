@@ -9,7 +9,7 @@
 // remainder.  So every sum here is kept modulo T_c (two residues add to less than 2^64, as
 // T_c < 2^63) and no division is needed unless a size is at least 8 T_c.
 //
-// A trace's memcpys are cut into tiles of COPY_TILE, taken by blocks in rounds over the
+// A trace's memcpys are cut into tiles of COPY_PASS_TILE, taken by blocks in rounds over the
 // traces (every trace's first tile, then every second one, ...).  A block loads its tile
 // into registers (each thread CB_PER consecutive memcpys; 13 bytes per memcpy, read once),
 // sums it, publishes the sum, finds the counter entering the tile from its predecessors'
@@ -27,7 +27,9 @@
 namespace scl {
 
 constexpr int CB_THREADS = 256;
-constexpr int CB_PER = COPY_TILE / CB_THREADS;   // memcpys per thread (16)
+constexpr int CB_BLOCKS = 3;                     // resident blocks per SM (the register budget)
+static_assert(COPY_PASS_TILE <= 4096 && COPY_PASS_TILE % (4 * CB_THREADS) == 0, "tile shape");
+constexpr int CB_PER = COPY_PASS_TILE / CB_THREADS;   // memcpys per thread (16)
 constexpr uint32_t CB_HOT = 1024;                // lines counted in shared memory per tile
 constexpr uint32_t CB_FLUSH = 1024;              // tiles of one trace a block counts before a flush
 
@@ -82,7 +84,7 @@ __device__ __forceinline__ void copy_job(const LaunchCopy &a, unsigned it, CopyT
     dst[0] = x; dst[1] = y; dst[2] = z;
 }
 
-__global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
+__global__ void __launch_bounds__(CB_THREADS, CB_BLOCKS) k_copy(const LaunchCopy a) {
     __shared__ CopyBlockSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     unsigned long long *status = static_cast<unsigned long long *>(a.cstatus);
@@ -281,7 +283,8 @@ __global__ void __launch_bounds__(CB_THREADS, 3) k_copy(const LaunchCopy a) {
             }
             const int f = ((pw[k >> 2] >> (8 * (k & 3))) & 0xffu) ? 1 : 0;
             // the shared table takes counts of at most 8 per memcpy, so CB_FLUSH tiles add at most
-            // 1,024 x 4,096 x 8 = 2^25 per entry and the 32-bit counts cannot wrap; larger
+            // 1,024 x 4,096 x 8 = 2^25 per entry (tiles of at most 4,096) and the 32-bit counts
+            // cannot wrap; larger
             // counts go to global memory
             if (l < hot && qn <= 8) atomicAdd(&sm.hot[2 * l + f], qn);
             else atomicAdd(&gc[2 * l + f], (unsigned long long)qn);

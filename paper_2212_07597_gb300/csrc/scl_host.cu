@@ -695,9 +695,9 @@ int scl_replay_batch(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *
                 rec_total += U.rec_cap;
                 lst_total += (uint64_t)NL * U.lst_cap;
             }
-            for (uint64_t off = 0; off < g.cp.n; off += COPY_TILE) {
+            for (uint64_t off = 0; off < g.cp.n; off += COPY_PASS_TILE) {
                 CopyTile T{};
-                T.len = (uint32_t)std::min<uint64_t>(COPY_TILE, g.cp.n - off);
+                T.len = (uint32_t)std::min<uint64_t>(COPY_PASS_TILE, g.cp.n - off);
                 T.size = g.cp.size + off;
                 T.line = g.cp.line + off;
                 T.py = g.cp.is_python + off;

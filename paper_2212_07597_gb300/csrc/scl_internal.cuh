@@ -20,7 +20,8 @@ constexpr int TILE = 256;          // events per shared-memory stage
 constexpr int NST = 4;             // stages per walker warp
 constexpr int UNIT_ALIGN = 1024;   // unit starts are multiples of this within a segment
 constexpr uint64_t FINAL_PIECE = 65536;   // k_final cuts units into pieces of about this many events
-constexpr int COPY_TILE = 4096;    // memcpy events per block of the copy samplers
+constexpr int COPY_TILE = 4096;    // memcpy events per block of the allocation-free copy sampler
+constexpr int COPY_PASS_TILE = 4096;   // memcpy events per tile of the batch's copy pass (k_copy)
 constexpr int SMEM_LINES_MAX = 1024;  // per-line tables kept in shared memory up to this L
 
 // error codes mirrored from scl.h
