@@ -17,7 +17,7 @@ using namespace scl;
 
 namespace {
 
-constexpr uint32_t STATE_MAGIC = 0x53434c32u;   // "SCL2"
+constexpr uint32_t STATE_MAGIC = 0x53434c33u;   // "SCL3"
 
 struct DevBuf {
     void *p = nullptr;
@@ -1019,7 +1019,8 @@ int scl_line_stats(scl_ctx *c, uint32_t trace, scl_line_stat *out, uint32_t cap,
         scl_line_stat &o = out[l];
         const LineRow &x = rows[l];
         o.n_growth = x.n_growth; o.n_shrink = x.n_shrink;
-        o.A = x.A; o.F = x.F; o.A_py = x.A_py; o.F_py = x.F_py; o.net = x.net;
+        o.A = x.A; o.F = x.F; o.A_py = x.A_py; o.F_py = x.F_py;
+        o.net = (int64_t)((uint64_t)x.A - (uint64_t)x.F);   // the sum of A - F over the samples
         o.copy_samples[0] = cps[2 * l]; o.copy_samples[1] = cps[2 * l + 1];
         o.copy_bytes[0] = cps[2 * l] * Tc; o.copy_bytes[1] = cps[2 * l + 1] * Tc;
     }

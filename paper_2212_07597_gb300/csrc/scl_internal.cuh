@@ -39,9 +39,10 @@ struct DevTrace {                   // one per trace slot
 
 struct LineRow {                    // one per (trace, line): sample totals (scl_line_stat order) + leak pair
     unsigned long long n_growth, n_shrink;
-    long long A, F, A_py, F_py, net;
+    long long A, F, A_py, F_py;     // (a line's net total, the sum of A - F, is A - F: formed on query)
     unsigned long long mallocs, frees;
 };
+static_assert(sizeof(LineRow) == 64, "half a 128-byte line per (trace, line)");
 // the copy-volume samples of a (trace, line) live in their own array, [trace][line][flag]
 // (16 bytes per line): the copy sampler's updates then touch a compact per-trace block
 

@@ -12,6 +12,7 @@
 //   k_state    folds the batch into the trace's resident state.
 #include "scl_internal.cuh"
 #include <algorithm>
+#include <cstddef>
 
 #include "scl_launch.h"
 
@@ -317,18 +318,19 @@ __global__ void __launch_bounds__(BT) k_scan_window(LaunchPost a) {
 // ---------------------------------------------------------------- k_compact
 // Section 3.3: each final sample goes to the sample log and to its line's totals;
 // crossings count one tracked malloc for their line (Section 3.4).
-constexpr int HCOLS = 8;   // n_growth, n_shrink, A, F, A_py, F_py, net, mallocs
+constexpr int HCOLS = 7;   // n_growth, n_shrink, A, F, A_py, F_py, mallocs (the LineRow order)
 
+// one sample into a line's totals (row: HCOLS words in LineRow order; zero terms are skipped)
 __device__ __forceinline__ void row_add(unsigned long long *row, bool growth, int64_t A, int64_t F, int64_t Apy,
                                         int64_t Fpy, bool hwm) {
     atomicAdd(&row[growth ? 0 : 1], 1ull);
-    atomicAdd(&row[2], (unsigned long long)A);
-    atomicAdd(&row[3], (unsigned long long)F);
+    if (A) atomicAdd(&row[2], (unsigned long long)A);
+    if (F) atomicAdd(&row[3], (unsigned long long)F);
     if (Apy) atomicAdd(&row[4], (unsigned long long)Apy);
     if (Fpy) atomicAdd(&row[5], (unsigned long long)Fpy);
-    atomicAdd(&row[6], (unsigned long long)(A - F));
-    if (hwm) atomicAdd(&row[7], 1ull);
+    if (hwm) atomicAdd(&row[6], 1ull);
 }
+static_assert(offsetof(LineRow, mallocs) == 6 * 8, "row_add's columns are the LineRow words");
 
 __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
     extern __shared__ __align__(16) unsigned long long hist[];   // [n_lines][HCOLS] when it fits
@@ -376,18 +378,8 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
                 log[log_base + j] = s;
             }
             if (!line_ok) continue;
-            if (use_smem) {
-                row_add(&hist[line * HCOLS], r.kind > 0, r.A, r.F, r.A_py, r.F_py, r.is_hwm);
-            } else {
-                unsigned long long *row = reinterpret_cast<unsigned long long *>(&grow[line]);
-                atomicAdd(&row[r.kind > 0 ? 0 : 1], 1ull);
-                atomicAdd(&row[2], (unsigned long long)r.A);
-                atomicAdd(&row[3], (unsigned long long)r.F);
-                atomicAdd(&row[4], (unsigned long long)r.A_py);
-                atomicAdd(&row[5], (unsigned long long)r.F_py);
-                atomicAdd(&row[6], (unsigned long long)(r.A - r.F));
-                if (r.is_hwm) atomicAdd(&grow[line].mallocs, 1ull);
-            }
+            row_add(use_smem ? &hist[line * HCOLS] : reinterpret_cast<unsigned long long *>(&grow[line]), r.kind > 0,
+                    r.A, r.F, r.A_py, r.F_py, r.is_hwm);
         }
     }
     if (use_smem) {
@@ -403,8 +395,7 @@ __global__ void __launch_bounds__(NT) k_compact(LaunchPost a) {
             atomicAdd(reinterpret_cast<unsigned long long *>(&grow[l].F), h[3]);
             atomicAdd(reinterpret_cast<unsigned long long *>(&grow[l].A_py), h[4]);
             atomicAdd(reinterpret_cast<unsigned long long *>(&grow[l].F_py), h[5]);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&grow[l].net), h[6]);
-            if (h[7]) atomicAdd(&grow[l].mallocs, h[7]);
+            if (h[6]) atomicAdd(&grow[l].mallocs, h[6]);
         }
     }
 }
