@@ -21,8 +21,8 @@
 #include <algorithm>
 #include <cstddef>
 
-#include "scl_internal.cuh"
 #include "scl_launch.h"
+#include "scl_stage.cuh"
 
 namespace scl {
 
@@ -51,6 +51,20 @@ struct alignas(16) CopyBlockSmem {
     CopyTask task[2];             // the current tile and the next
     int ok;
 };
+
+// A warp's 512 memcpys of a tile, staged by coalesced 16-byte asynchronous copies (each
+// lane's own 16 memcpys then read from shared memory).  Sizes sit in the chunk-permuted
+// rows of swz_el<16> (128-byte rows, one per lane); lines in 64-byte rows with chunk c of
+// row r at c ^ ((r >> 1) & 3); flags in 16-byte rows.  A quarter warp reading one chunk per
+// lane then touches eight distinct bank groups in every column.
+struct alignas(16) CopyStage {
+    unsigned long long size[32 * CB_PER];
+    uint32_t line[32 * CB_PER];
+    uint8_t py[32 * CB_PER];
+};
+constexpr size_t COPY_STAGE_BYTES = sizeof(CopyStage) * (CB_THREADS / 32);
+
+__device__ __forceinline__ int line_chunk(int r, int c) { return 4 * r + (c ^ ((r >> 1) & 3)); }
 
 static_assert(offsetof(CopyBlockSmem, task) % 16 == 0 && sizeof(CopyTask) % 16 == 0 && offsetof(CopyTask, ct) == 0,
               "the tile records are copied with 16-byte stores");
@@ -86,7 +100,9 @@ __device__ __forceinline__ void copy_job(const LaunchCopy &a, unsigned it, CopyT
 
 __global__ void __launch_bounds__(CB_THREADS, CB_BLOCKS) k_copy(const LaunchCopy a) {
     __shared__ CopyBlockSmem sm;
+    extern __shared__ __align__(128) unsigned char stage_raw[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    CopyStage &stg = reinterpret_cast<CopyStage *>(stage_raw)[w];
     unsigned long long *status = static_cast<unsigned long long *>(a.cstatus);
     const unsigned long long Tc = a.Tc;
     const bool small = Tc <= (1ull << 60);
@@ -131,21 +147,38 @@ __global__ void __launch_bounds__(CB_THREADS, CB_BLOCKS) k_copy(const LaunchCopy
         unsigned long long v[CB_PER];
         uint32_t ln[CB_PER];
         uint32_t pw[CB_PER / 4];
-        const bool vec = e0 + CB_PER <= len &&
-                         ((reinterpret_cast<uintptr_t>(ct.size) | reinterpret_cast<uintptr_t>(ct.line) |
-                           reinterpret_cast<uintptr_t>(ct.py)) & 15u) == 0;
-        if (vec) {
-            const ulonglong2 *ps = reinterpret_cast<const ulonglong2 *>(ct.size + e0);
+        // the warp's slice is staged whole when it lies inside the tile and the columns are
+        // 16-byte aligned (warp-uniform); otherwise each lane loads its own memcpys
+        const uint32_t w0 = (uint32_t)w * 32 * CB_PER;
+        const bool staged = w0 + 32 * CB_PER <= len &&
+                            ((reinterpret_cast<uintptr_t>(ct.size) | reinterpret_cast<uintptr_t>(ct.line) |
+                              reinterpret_cast<uintptr_t>(ct.py)) & 15u) == 0;
+        if (staged) {
+            const uint64_t *gs = ct.size + w0;
 #pragma unroll
-            for (int q = 0; q < CB_PER / 2; ++q) { const ulonglong2 x = __ldg(ps + q); v[2 * q] = x.x; v[2 * q + 1] = x.y; }
-            const uint4 *pl = reinterpret_cast<const uint4 *>(ct.line + e0);
+            for (int i = 0; i < CB_PER / 2; ++i) {   // chunk j = lane + 32 i: sizes 2j, 2j + 1
+                const int j = lane + 32 * i;
+                cp_async16(&stg.size[swz_el<CB_PER>(2 * j)], gs + 2 * j);
+            }
+            const uint32_t *gl = ct.line + w0;
+#pragma unroll
+            for (int i = 0; i < CB_PER / 4; ++i) {   // chunk j: lines 4j .. 4j + 3 (row j / 4)
+                const int j = lane + 32 * i;
+                cp_async16(&stg.line[4 * line_chunk(j >> 2, j & 3)], gl + 4 * j);
+            }
+            cp_async16(&stg.py[CB_PER * lane], ct.py + w0 + CB_PER * lane);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            load_lane<CB_PER>(stg.size, (uint32_t)(CB_PER * lane), v);
+            const uint4 *sl = reinterpret_cast<const uint4 *>(stg.line);
 #pragma unroll
             for (int q = 0; q < CB_PER / 4; ++q) {
-                const uint4 x = __ldg(pl + q);
+                const uint4 x = sl[line_chunk(lane, q)];
                 ln[4 * q] = x.x; ln[4 * q + 1] = x.y; ln[4 * q + 2] = x.z; ln[4 * q + 3] = x.w;
             }
-            const uint4 y = __ldg(reinterpret_cast<const uint4 *>(ct.py + e0));
+            const uint4 y = reinterpret_cast<const uint4 *>(stg.py)[lane];
             pw[0] = y.x; pw[1] = y.y; pw[2] = y.z; pw[3] = y.w;
+            __syncwarp();   // the warp's stage is rewritten by its next tile only after this
         } else {
 #pragma unroll
             for (int k = 0; k < CB_PER; ++k) {
@@ -345,11 +378,13 @@ size_t copy_status_bytes(size_t ntiles) { return sizeof(unsigned long long) * nt
 
 cudaError_t launch_copy(const LaunchCopy &a, cudaStream_t s) {
     if (!a.nctiles) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_copy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COPY_STAGE_BYTES);
+    if (e != cudaSuccess) return e;
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copy, CB_THREADS, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copy, CB_THREADS, COPY_STAGE_BYTES);
     if (e != cudaSuccess) return e;
     const int blocks = std::max(1, std::min(a.nctiles, std::max(1, bps) * a.num_sms));
-    k_copy<<<blocks, CB_THREADS, 0, s>>>(a);
+    k_copy<<<blocks, CB_THREADS, COPY_STAGE_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
