@@ -194,21 +194,26 @@ class Clocks:
                                                         "than the sampling period)"}
 
 
-KERNEL_SOURCES = ("scl_sketch.cu", "scl_final.cu", "scl_post.cu", "scl_stage.cuh", "scl_internal.cuh",
-                  "scl_exact.cuh", "scl_copy.cu")
+# the sources each replay kernel is built from (its ncu traffic figure holds while they are unchanged)
+KERNEL_SOURCES = {
+    "phase1": ("scl_sketch.cu", "scl_exact.cuh", "scl_stage.cuh", "scl_internal.cuh", "scl_launch.h"),
+    "final": ("scl_final.cu", "scl_exact.cuh", "scl_stage.cuh", "scl_internal.cuh", "scl_launch.h"),
+    "copy": ("scl_copy.cu", "scl_stage.cuh", "scl_internal.cuh", "scl_launch.h"),
+}
 
 
-def source_hash() -> str:
+def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2212_07597_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(kernel: str, units: float):
     """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json), if it
-    was taken on the current kernel sources: the captured bytes per algorithmic byte times
-    this launch's algorithmic bytes (`units`)."""
+    was taken on the current kernel sources: the captured DRAM bytes per streamed byte times
+    this launch's streamed bytes (`units`: the algorithmic bytes, plus, for k_phase1, the
+    warm-up events the sketch re-reads at 8 B each)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -217,9 +222,9 @@ def traffic_for(kernel: str, units: float):
     except Exception:
         return None
     k = d.get("kernels", {}).get(kernel)
-    if not k or d.get("source_hash") != source_hash():
+    if not k or k.get("source_hash") != source_hash(kernel):
         return None
-    return k["dram_bytes_per_alg_byte"] * units
+    return k["dram_bytes_per_streamed_byte"] * units
 
 
 def measured_peak():
@@ -241,10 +246,20 @@ def kernel_bytes(n, m, first_events):
             "copy": COPY_BYTES * m}
 
 
-def roofline_of(ktimes, n, m, first_events, launches_per_step=1, traffic=True):
+def streamed_bytes(n, m, first_events, sketch_streamed=None):
+    """Bytes each replay kernel streams per launch: the algorithmic bytes, with k_phase1's
+    sketch reading `sketch_streamed` events (units plus warm-ups) instead of n - first."""
+    per = kernel_bytes(n, m, first_events)
+    if sketch_streamed is not None:
+        per["phase1"] = EXACT_BYTES * first_events + SKETCH_BYTES * sketch_streamed
+    return per
+
+
+def roofline_of(ktimes, n, m, first_events, launches_per_step=1, traffic=True, sketch_streamed=None):
     """The dominant replay kernel (k_phase1, k_final or k_copy) and its algorithmic GB/s over
     its CUDA-event time per launch, plus the same figures for the others."""
     per = kernel_bytes(n, m, first_events)
+    streamed = streamed_bytes(n, m, first_events, sketch_streamed)
     peak, src = measured_peak()
     ks = {}
     for k in EVENT_KERNELS:
@@ -252,7 +267,7 @@ def roofline_of(ktimes, n, m, first_events, launches_per_step=1, traffic=True):
             ms = ktimes[k][0] / ktimes[k][1]
             a = per[k] / launches_per_step / (ms / 1e3) / 1e9
             ks[k] = {"ms": ms, "alg_bytes": per[k] / launches_per_step, "achieved": a, "frac": a / peak,
-                     "traffic": traffic_for(k, per[k] / launches_per_step) if traffic else None}
+                     "traffic": traffic_for(k, streamed[k] / launches_per_step) if traffic else None}
     # the copy-volume kernel runs on a side stream beside the event path, so its CUDA-event
     # span includes waiting for SMs: the dominant kernel is taken on the event path
     dom = max((k for k in ks if k != "copy"), key=lambda k: ks[k]["ms"])
@@ -564,7 +579,8 @@ def run_batched(args):
 
     # per-kernel times (profiling replaces the graph by plain launches) for the roofline
     ktimes, launches_per_step = profile_steps(scl, ctx, step)
-    roof = roofline_of(ktimes, n_tot, m_tot, bstats["first_events"], traffic=True)
+    roof = roofline_of(ktimes, n_tot, m_tot, bstats["first_events"], traffic=True,
+                       sketch_streamed=bstats["sketch_events"])
     path_gbs = (EVENT_BYTES * n_tot + COPY_BYTES * m_tot) / (tmax / args.steps / 1e3) / 1e9
     peak, peak_src = measured_peak()
 
@@ -626,13 +642,17 @@ def run_batched(args):
         sub_n = int(lens[:len(sub)].sum())
         h2d = sum(int(lens[i]) * 21 + int(mlen[i]) * 13 for i in sub)
         d2h = len(sub) * 4096 * (scl.LINE_STAT_DTYPE.itemsize + scl.LEAK_DTYPE.itemsize)
+        # every trace's rows in two range queries, into pinned host arrays
+        pin = [torch.empty(len(sub) * 4096 * dt.itemsize, dtype=torch.uint8).pin_memory()
+               for dt in (scl.LINE_STAT_DTYPE, scl.LEAK_DTYPE)]
+        stats_out, scores_out = (np.frombuffer(t.numpy(), dtype=dt).reshape(len(sub), 4096)
+                                 for t, dt in zip(pin, (scl.LINE_STAT_DTYPE, scl.LEAK_DTYPE)))
 
         def e2e_step():
             scl.scl_trace_reset(ctx, scl.SCL_ALL_TRACES, stream)
             scl.scl_replay_batch_host(ctx, hsegs, stream)
-            for i in sub:
-                scl.scl_line_stats(ctx, i)
-                scl.scl_leak_scores(ctx, i)
+            scl.scl_line_stats_range(ctx, 0, len(sub), stats_out)
+            scl.scl_leak_scores_range(ctx, 0, len(sub), scores_out)
 
         e2e_step()
         barrier()
@@ -645,7 +665,7 @@ def run_batched(args):
         e2e = {"value": sub_n * ks * ws / el, "unit": "events/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ks,
                "sample": f"first {len(sub)} traces ({sub_n:,} events): host-pinned arrays in, per-line "
-                         f"stats and leak scores of every trace out"}
+                         f"stats and leak scores of every trace out (two range queries)"}
 
     if rank == 0:
         config = dict(batched_config(ntr, lens, mlen, args.stride),
@@ -944,7 +964,7 @@ def run_single(args):
     bstats = scl.scl_batch_stats(ctx)
     value, tmax = job_throughput(ms, n * args.steps, dev)
     ktimes, launches_per_step = profile_steps(scl, ctx, step)
-    roof = roofline_of(ktimes, n, m, bstats["first_events"])
+    roof = roofline_of(ktimes, n, m, bstats["first_events"], sketch_streamed=bstats["sketch_events"])
     peak, peak_src = measured_peak()
     path_gbs = (EVENT_BYTES * n + COPY_BYTES * m) * args.steps / (ms / 1e3) / 1e9
 

@@ -217,6 +217,15 @@ int scl_line_stats(scl_ctx *ctx, uint32_t trace, scl_line_stat *out, uint32_t ca
 int scl_line_timeline(scl_ctx *ctx, uint32_t trace, uint32_t line, uint64_t *idx_out, int64_t *fp_out, uint64_t cap,
                       uint64_t *n_out);
 int scl_leak_scores(scl_ctx *ctx, uint32_t trace, scl_leak_score *out, uint32_t cap, uint32_t *n_out);
+/* The same rows for ntr consecutive traces trace0 .. trace0 + ntr - 1 in one call (one
+ * synchronisation, rows formed on the device, one copy): trace-major, row l of trace
+ * trace0 + i at out[i * n_lines + l]; cap counts rows; *n_out = ntr * n_lines (SCL_ERANGE when
+ * cap is smaller, SCL_EINVAL when the range passes max_traces).  out may be pinned or pageable
+ * host memory.  Grows one device buffer of the context to ntr * n_lines rows. */
+int scl_line_stats_range(scl_ctx *ctx, uint32_t trace0, uint32_t ntr, scl_line_stat *out, uint64_t cap,
+                         uint64_t *n_out);
+int scl_leak_scores_range(scl_ctx *ctx, uint32_t trace0, uint32_t ntr, scl_leak_score *out, uint64_t cap,
+                          uint64_t *n_out);
 int scl_trace_state(scl_ctx *ctx, uint32_t trace, scl_trace_info *out);
 int scl_leak_report(scl_ctx *ctx, uint32_t trace, scl_leak_report_row *out, uint32_t cap, uint32_t *n_out);
 

@@ -51,7 +51,7 @@ struct scl_ctx {
     uint64_t last_first_events = 0, last_sketch_events = 0;
     std::vector<uint64_t> h_events;   // host mirror of each trace's event count
     // batch scratch
-    DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage, phit;
+    DevBuf plan, usum, cand, lists, match, uwalk, utrue, umode, uexp, uplan, uout, pref, recs, btres, ctsum, stage, phit, qrows;
     DevBuf rate;   // scratch of scl_rate_samples
     DevBuf report; // rows of scl_leak_report
     DevBuf tline;  // scratch and output of scl_line_timeline
@@ -462,7 +462,7 @@ void scl_replay_free(scl_ctx *c) {
     for (auto &p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (DevBuf *b : {&c->plan, &c->usum, &c->cand, &c->lists, &c->match, &c->uwalk, &c->utrue, &c->umode, &c->uexp, &c->uplan,
-                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report, &c->tline, &c->phit})
+                      &c->uout, &c->pref, &c->recs, &c->btres, &c->ctsum, &c->stage, &c->rate, &c->report, &c->tline, &c->phit, &c->qrows})
         if (b->p) cudaFree(b->p);
     cudaFree(c->traces);
     cudaFree(c->lines);
@@ -1040,6 +1040,44 @@ int scl_leak_scores(scl_ctx *c, uint32_t trace, scl_leak_score *out, uint32_t ca
        "read scores");
     CK(cudaStreamSynchronize(c->last_stream), "sync");
     return SCL_OK;
+}
+
+// the range queries: rows formed on the device into one buffer, then one copy to the caller
+static int range_rows(scl_ctx *c, uint32_t trace0, uint32_t ntr, void *out, uint64_t cap, uint64_t *n_out, bool stats) {
+    if (!c || !n_out || (ntr && !out)) return SCL_EINVAL;
+    if ((uint64_t)trace0 + ntr > c->cfg.max_traces)
+        return fail(c, SCL_EINVAL, "traces %u .. %u out of range", trace0, trace0 + ntr);
+    int r = sync_and_check(c);
+    if (r) return r;
+    const uint32_t L = c->cfg.n_lines;
+    const uint64_t nrows = (uint64_t)ntr * L;
+    *n_out = nrows;
+    if (cap < nrows) return fail(c, SCL_ERANGE, "output holds %llu rows, %llu needed", (unsigned long long)cap,
+                                 (unsigned long long)nrows);
+    if (!nrows) return SCL_OK;
+    const size_t row = stats ? sizeof(scl_line_stat) : sizeof(scl_leak_score);
+    if ((r = ensure(c, c->qrows, row * nrows, c->last_stream, "query rows"))) return r;
+    if (stats) {
+        const uint64_t Tc = (uint64_t)c->cfg.copy_multiple * (uint64_t)c->cfg.threshold;
+        CK(launch_stat_rows(c->lines, c->copies, trace0, nrows, L, Tc, c->qrows.p, c->num_sms, c->last_stream),
+           "launch line rows");
+    } else {
+        CK(launch_score_rows(c->lines, trace0, nrows, L, c->cfg.leak_rule, c->qrows.p, c->num_sms, c->last_stream),
+           "launch score rows");
+    }
+    CK(cudaMemcpyAsync(out, c->qrows.p, row * nrows, cudaMemcpyDeviceToHost, c->last_stream), "read rows");
+    CK(cudaStreamSynchronize(c->last_stream), "sync");
+    return SCL_OK;
+}
+
+int scl_line_stats_range(scl_ctx *c, uint32_t trace0, uint32_t ntr, scl_line_stat *out, uint64_t cap,
+                         uint64_t *n_out) {
+    return range_rows(c, trace0, ntr, out, cap, n_out, true);
+}
+
+int scl_leak_scores_range(scl_ctx *c, uint32_t trace0, uint32_t ntr, scl_leak_score *out, uint64_t cap,
+                          uint64_t *n_out) {
+    return range_rows(c, trace0, ntr, out, cap, n_out, false);
 }
 
 int scl_leak_report(scl_ctx *c, uint32_t trace, scl_leak_report_row *out, uint32_t cap, uint32_t *n_out) {

@@ -124,6 +124,11 @@ cudaError_t launch_state(const LaunchPost &a, cudaStream_t s);
 
 cudaError_t launch_reset(DevTrace *traces, LineRow *lines, unsigned long long *copies, uint32_t trace0,
                          uint32_t ntr, uint32_t n_lines, int64_t F0, uint64_t phase, cudaStream_t s);
+// the range queries' rows (scl_line_stat / scl_leak_score layouts), trace-major from trace0
+cudaError_t launch_stat_rows(const LineRow *lines, const unsigned long long *copies, uint32_t trace0, uint64_t nrows,
+                             uint32_t n_lines, uint64_t Tc, void *out, int num_sms, cudaStream_t s);
+cudaError_t launch_score_rows(const LineRow *lines, uint32_t trace0, uint64_t nrows, uint32_t n_lines, uint32_t rule,
+                              void *out, int num_sms, cudaStream_t s);
 cudaError_t launch_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines, uint32_t rule, void *out,
                           cudaStream_t s);
 cudaError_t launch_timeline(const Sample *log, uint64_t n, uint32_t line, void *scratch, uint64_t cap,

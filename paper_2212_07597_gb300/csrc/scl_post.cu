@@ -550,6 +550,41 @@ __global__ void k_scores(const LineRow *lines, uint32_t trace, uint32_t n_lines,
     out[l] = s;
 }
 
+struct StatRow {     // layout of scl_line_stat
+    uint64_t n_growth, n_shrink;
+    int64_t A, F, A_py, F_py, net;
+    uint64_t copy_samples[2], copy_bytes[2];
+};
+
+// rows of traces trace0 .. trace0 + ntr - 1, trace-major (the range queries)
+__global__ void k_stat_rows(const LineRow *lines, const unsigned long long *copies, uint32_t trace0, uint64_t nrows,
+                            uint32_t n_lines, uint64_t Tc, StatRow *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrows; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t g = (uint64_t)trace0 * n_lines + i;
+        const LineRow r = lines[g];
+        StatRow o;
+        o.n_growth = r.n_growth; o.n_shrink = r.n_shrink;
+        o.A = r.A; o.F = r.F; o.A_py = r.A_py; o.F_py = r.F_py;
+        o.net = (int64_t)((uint64_t)r.A - (uint64_t)r.F);   // the sum of A - F over the samples
+        o.copy_samples[0] = copies[2 * g]; o.copy_samples[1] = copies[2 * g + 1];
+        o.copy_bytes[0] = o.copy_samples[0] * Tc; o.copy_bytes[1] = o.copy_samples[1] * Tc;   // Section 3.5
+        out[i] = o;
+    }
+}
+
+__global__ void k_score_rows(const LineRow *lines, uint32_t trace0, uint64_t nrows, uint32_t n_lines, uint32_t rule,
+                             ScoreRow *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrows; i += (uint64_t)gridDim.x * blockDim.x) {
+        const LineRow &r = lines[(uint64_t)trace0 * n_lines + i];
+        const int64_t m = (int64_t)r.mallocs, f = (int64_t)r.frees;
+        ScoreRow s;
+        s.line = (uint32_t)(i % n_lines); s.pad = 0; s.mallocs = r.mallocs; s.frees = r.frees;
+        s.den = rule == 0 ? m - f + 2 : m + 2;
+        s.num = s.den - (f + 1);
+        out[i] = s;
+    }
+}
+
 struct ReportRow {   // layout of scl_leak_report_row
     uint32_t line;
     uint8_t reported, likely, growth, pad;
@@ -698,6 +733,20 @@ cudaError_t launch_reset(DevTrace *traces, LineRow *lines, unsigned long long *c
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     k_reset<<<(int)blocks, 256, 0, s>>>(traces, lines, copies, trace0, ntr, n_lines, F0, phase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stat_rows(const LineRow *lines, const unsigned long long *copies, uint32_t trace0, uint64_t nrows,
+                             uint32_t n_lines, uint64_t Tc, void *out, int num_sms, cudaStream_t s) {
+    const int blocks = (int)std::min<uint64_t>((nrows + 255) / 256, (uint64_t)num_sms * 8);
+    if (nrows) k_stat_rows<<<blocks, 256, 0, s>>>(lines, copies, trace0, nrows, n_lines, Tc, static_cast<StatRow *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_rows(const LineRow *lines, uint32_t trace0, uint64_t nrows, uint32_t n_lines, uint32_t rule,
+                              void *out, int num_sms, cudaStream_t s) {
+    const int blocks = (int)std::min<uint64_t>((nrows + 255) / 256, (uint64_t)num_sms * 8);
+    if (nrows) k_score_rows<<<blocks, 256, 0, s>>>(lines, trace0, nrows, n_lines, rule, static_cast<ScoreRow *>(out));
     return cudaGetLastError();
 }
 

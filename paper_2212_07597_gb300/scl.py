@@ -30,6 +30,7 @@ _NAMES = {-1: "SCL_EINVAL", -2: "SCL_ENOMEM", -3: "SCL_ECUDA", -4: "SCL_ETIMEOUT
 # every symbol include/scl.h declares
 EXPORTS = ("scl_config_default", "scl_replay_init", "scl_replay_free", "scl_last_error", "scl_replay_batch",
            "scl_replay_batch_host", "scl_sync", "scl_samples", "scl_line_stats", "scl_leak_scores",
+           "scl_line_stats_range", "scl_leak_scores_range",
            "scl_trace_state", "scl_state_export", "scl_state_import", "scl_trace_reset", "scl_tuning_get",
            "scl_tuning_set", "scl_autotune", "scl_profile_enable", "scl_kernel_times", "scl_profile_reset",
            "scl_selftest_wait", "scl_copy_volume_noalloc", "scl_batch_stats", "scl_graph_enable", "scl_serve", "scl_rate_samples",
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scl_samples": ([P, U32, P, U64, ctypes.POINTER(U64)], I),
             "scl_line_stats": ([P, U32, P, U32, ctypes.POINTER(U32)], I),
             "scl_leak_scores": ([P, U32, P, U32, ctypes.POINTER(U32)], I),
+            "scl_line_stats_range": ([P, U32, U32, P, U64, ctypes.POINTER(U64)], I),
+            "scl_leak_scores_range": ([P, U32, U32, P, U64, ctypes.POINTER(U64)], I),
             "scl_trace_state": ([P, U32, P], I),
             "scl_state_export": ([P, U32, P, U64, ctypes.POINTER(U64)], I),
             "scl_state_import": ([P, U32, P, U64], I),
@@ -293,6 +296,25 @@ def scl_leak_scores(ctx: Context, trace: int) -> np.ndarray:
     out = np.zeros(ctx.cfg.n_lines, LEAK_DTYPE)
     n = ctypes.c_uint32()
     _check(ctx, load().scl_leak_scores(ctx.handle, trace, out.ctypes.data, len(out), ctypes.byref(n)))
+    return out
+
+
+def scl_line_stats_range(ctx: Context, trace0: int, ntr: int, out: np.ndarray | None = None) -> np.ndarray:
+    """Line stats of traces trace0 .. trace0 + ntr - 1 in one call, shape (ntr, n_lines); `out` may be
+    a preallocated (for instance pinned) array of that shape and dtype."""
+    if out is None:
+        out = np.zeros((ntr, ctx.cfg.n_lines), LINE_STAT_DTYPE)
+    n = ctypes.c_uint64()
+    _check(ctx, load().scl_line_stats_range(ctx.handle, trace0, ntr, out.ctypes.data, out.size, ctypes.byref(n)))
+    return out
+
+
+def scl_leak_scores_range(ctx: Context, trace0: int, ntr: int, out: np.ndarray | None = None) -> np.ndarray:
+    """Leak scores of traces trace0 .. trace0 + ntr - 1 in one call, shape (ntr, n_lines)."""
+    if out is None:
+        out = np.zeros((ntr, ctx.cfg.n_lines), LEAK_DTYPE)
+    n = ctypes.c_uint64()
+    _check(ctx, load().scl_leak_scores_range(ctx.handle, trace0, ntr, out.ctypes.data, out.size, ctypes.byref(n)))
     return out
 
 

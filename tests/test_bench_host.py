@@ -33,12 +33,17 @@ def test_traffic_table_matches_the_kernel_sources_or_is_withheld(monkeypatch):
         return
     d = json.load(open(path))
     k = d["kernels"]
-    for name in ("phase1", "final"):
-        assert k[name]["dram_bytes_per_alg_byte"] == pytest.approx(k[name]["dram_bytes"] / k[name]["alg_bytes"])
-    if d["source_hash"] == bench.source_hash():
-        assert bench.traffic_for("final", 1000.0) == pytest.approx(k["final"]["dram_bytes_per_alg_byte"] * 1000.0)
+    for name in ("phase1", "final", "copy"):
+        assert k[name]["dram_bytes_per_streamed_byte"] == pytest.approx(k[name]["dram_bytes"] / k[name]["streamed_bytes"])
+    # the captured case's streamed bytes follow from its event counts
+    c = d["case"]
+    sb = bench.streamed_bytes(c["events"], c["memcpys"], c["first_events"], c["sketch_events"])
+    for name in ("phase1", "final", "copy"):
+        assert k[name]["streamed_bytes"] == pytest.approx(sb[name])
+    if k["final"]["source_hash"] == bench.source_hash("final"):
+        assert bench.traffic_for("final", 1000.0) == pytest.approx(k["final"]["dram_bytes_per_streamed_byte"] * 1000.0)
     # a changed kernel source withholds the figure
-    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "source_hash", lambda kernel: "0" * 16)
     assert bench.traffic_for("final", 1000.0) is None
 
 

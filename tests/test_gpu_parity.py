@@ -376,3 +376,23 @@ def test_line_timeline_matches_oracle_samples():
         sel = w[w["line"] == l]
         assert np.array_equal(idx, sel["idx"]) and np.array_equal(fp, sel["footprint"]), l
         assert len(idx) == len(sel)
+
+
+def test_range_queries_equal_per_trace_queries():
+    # one call for a span of traces returns, trace-major, the rows of the per-trace queries
+    lens = [5000, 1, 77_777, 300_000, 20_000]
+    trs = [tg.plain_trace(n, seed=31, trace=i, n_lines=64) for i, n in enumerate(lens)]
+    ctx = gpu_ctx(1_048_573, n_lines=64, max_traces=8, unit=8192)
+    keep = replay(ctx, [(i + 2, tr) for i, tr in enumerate(trs)])
+    stats = scl.scl_line_stats_range(ctx, 1, 7)
+    scores = scl.scl_leak_scores_range(ctx, 1, 7)
+    assert stats.shape == (7, 64) and scores.shape == (7, 64)
+    for k in range(7):
+        assert stats[k].tobytes() == scl.scl_line_stats(ctx, 1 + k).tobytes()
+        assert scores[k].tobytes() == scl.scl_leak_scores(ctx, 1 + k).tobytes()
+    for i, tr in enumerate(trs):
+        o = oracle_of(tr, 1_048_573, n_lines=64)
+        assert np.array_equal(stats[i + 1]["net"], o.lines()["net"])
+    assert scl.scl_line_stats_range(ctx, 0, 0).shape == (0, 64)
+    with pytest.raises(scl.SclError):
+        scl.scl_line_stats_range(ctx, 5, 4)   # passes max_traces
