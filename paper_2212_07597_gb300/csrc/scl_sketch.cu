@@ -40,13 +40,15 @@ __device__ __forceinline__ int64_t candidate_entry(int k, int64_t T) {
     return -(T - 1) + (int64_t)(span * k / (K - 1));
 }
 
-// Advance this lane's counter c (if `active`) over one step; at each reset of an
-// active lane call on_reset(lane_k, pos, growth, Qr) on all lanes (warp-uniform).
+// Advance this lane's counter c (if `active`) over one step.  Active lanes with equal
+// counters form a group led by its lowest lane (`grp`: this lane's leader); one crossing
+// search runs per group, and at each of its resets on_reset(leader_k, pos, growth, Qr) is
+// called on all lanes (warp-uniform), for every member of group k to record.
 // SP / I: the 64-bit step (StepPrefix, int64_t) or its 32-bit form (StepPrefix32, int32_t).
 template <class SP, class I, class F>
-__device__ __forceinline__ void advance(const SP &sp, const I *xq, I qmax, I qmin, int lane, I T, bool active, I &c,
-                                        F &&on_reset) {
-    unsigned m = __ballot_sync(FULL, active && (c + qmax >= T || c + qmin <= -T));
+__device__ __forceinline__ void advance(const SP &sp, const I *xq, I qmax, I qmin, int lane, I T, bool active, int grp,
+                                        I &c, F &&on_reset) {
+    unsigned m = __ballot_sync(FULL, active && grp == lane && (c + qmax >= T || c + qmin <= -T));
     I cnew = c + sp.tot;
     while (m) {
         const int k = __ffs(m) - 1;
@@ -64,7 +66,7 @@ __device__ __forceinline__ void advance(const SP &sp, const I *xq, I qmax, I qmi
             // prefix moves T away from Q_r
             if (qmax - Qr < T && qmin - Qr > -T) break;
         }
-        if (lane == k) cnew = b + sp.tot;
+        if (active && grp == k) cnew = b + sp.tot;
     }
     c = cnew;
 }
@@ -73,15 +75,15 @@ __device__ __forceinline__ void advance(const SP &sp, const I *xq, I qmax, I qmi
 // (t32: T <= 2^30), else the 64-bit one.  Returns the step total and prefix extremes.
 template <class F>
 __device__ __forceinline__ void sketch_step(const StepIn<8> &in, int64_t *xq, int lane, int64_t T, bool t32,
-                                            bool active, int64_t &c, int64_t &tot, int64_t &qmax, int64_t &qmin,
-                                            F &&on_reset) {
+                                            bool active, int grp, int64_t &c, int64_t &tot, int64_t &qmax,
+                                            int64_t &qmin, F &&on_reset) {
     if (t32 && __all_sync(FULL, step_fits32(in))) {
         StepPrefix32<8> sp;
         int32_t *xq32 = reinterpret_cast<int32_t *>(xq);
         step_prefix32(in, lane, sp, xq32);
         const int32_t mx = __reduce_max_sync(FULL, sp.lmax), mn = __reduce_min_sync(FULL, sp.lmin);
         int32_t c32 = (int32_t)c;
-        advance(sp, (const int32_t *)xq32, mx, mn, lane, (int32_t)T, active, c32, on_reset);
+        advance(sp, (const int32_t *)xq32, mx, mn, lane, (int32_t)T, active, grp, c32, on_reset);
         c = c32;
         tot = sp.tot;
         qmax = mx;
@@ -91,7 +93,7 @@ __device__ __forceinline__ void sketch_step(const StepIn<8> &in, int64_t *xq, in
         step_prefix(in, lane, sp, xq);
         qmax = warp_max(sp.lmax);
         qmin = warp_min(sp.lmin);
-        advance(sp, (const int64_t *)xq, qmax, qmin, lane, T, active, c, on_reset);
+        advance(sp, (const int64_t *)xq, qmax, qmin, lane, T, active, grp, c, on_reset);
         tot = sp.tot;
     }
 }
@@ -139,7 +141,7 @@ __device__ bool sketch_unit(SketchRing &sm, uint32_t &phase, int u, const Unit *
         auto wstep = [&](const StepIn<SE> &in, uint32_t) -> bool {
             const bool act = lead == lane;
             int64_t tot, qmax, qmin;
-            sketch_step(in, sm.xq, lane, T, t32, act, c, tot, qmax, qmin, [](int, int, bool, int64_t) {});
+            sketch_step(in, sm.xq, lane, T, t32, act, lane, c, tot, qmax, qmin, [](int, int, bool, int64_t) {});
             const unsigned same = match_counter(c, t32) & __ballot_sync(FULL, act);
             if (act) lead = __ffs(same) - 1;
             return false;
@@ -164,10 +166,16 @@ __device__ bool sketch_unit(SketchRing &sm, uint32_t &phase, int u, const Unit *
     int64_t gmax = INT64_MIN, tmax = INT64_MIN;
     uint32_t garg = 0, targ = 0;
     int64_t P = 0, umax = INT64_MIN, umin = INT64_MAX;
+    // the distinct runs regroup as they meet: runs whose counters become equal (after both
+    // reset at one event) take the same resets from there on, so one search serves the group
+    // and each member records them in its own lane
+    int grp = lane;
     auto step = [&](const StepIn<SE> &in, uint32_t rel0) -> bool {
         int64_t tot, qmax, qmin;
-        sketch_step(in, sm.xq, lane, T, t32, active, c, tot, qmax, qmin, [&](int k, int r, bool growth, int64_t Qr) {
-            if (lane == k) {
+        bool reset = false;
+        sketch_step(in, sm.xq, lane, T, t32, active, grp, c, tot, qmax, qmin, [&](int k, int r, bool growth, int64_t Qr) {
+            reset = true;
+            if (active && grp == k) {
                 const uint32_t pos = rel0 + (uint32_t)r;
                 const int64_t Pl = P + Qr;
                 if (growth && Pl > gmax) { gmax = Pl; garg = pos; }
@@ -189,6 +197,10 @@ __device__ bool sketch_unit(SketchRing &sm, uint32_t &phase, int u, const Unit *
                 last = (int32_t)pos;
             }
         });
+        if (reset) {
+            const unsigned g = match_counter(c, t32) & __ballot_sync(FULL, active);
+            if (active) grp = __ffs(g) - 1;
+        }
         // the unit's prefix extremes (for the transparency test of k_chain)
         umax = P + qmax > umax ? P + qmax : umax;
         umin = P + qmin < umin ? P + qmin : umin;
