@@ -63,7 +63,14 @@ struct ExactRun {                // FIRST only: the run's facts, as the sketch r
 // other step uses 64-bit lane sums and a shuffle reduction.  The frees of the step that
 // hit the tracked block are found once per step (a bit per event), and re-found only when
 // a sample starts tracking another block.
-template <bool FIRST, class RingT>
+// thresholds at which the exact replay tests each step for the dense form (below); above, a
+// step with every event at least 2T - 1 away from zero is too rare to pay for the test
+constexpr int64_t DENSE_T_MAX = 4096;
+
+// DENSE: the kernel instance for T <= DENSE_T_MAX, which tests each searched step for the
+// dense form; the other instance carries none of that code (its registers and schedule are
+// those of the plain replay).
+template <bool FIRST, bool DENSE, class RingT>
 __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const ExactIn &in0, FRec *out, uint32_t cap,
                            int64_t T, unsigned long long spin, ErrWord *err, int lane, uint32_t &n_out,
                            UnitOut &O, ExactRun *R, uint32_t &prior) {
@@ -191,6 +198,188 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         accA = accApy = accSpy = 0;
         return hwm;
     };
+    // A dense step: every event moves the counter by 0 or by at least 2T - 1.  From |c| < T each
+    // nonzero event then crosses (|c + d| >= |d| - |c| >= T) and leaves the counter at 0, so
+    // every nonzero event is a sample whose window holds just itself (the step's first one
+    // also closes the open window), and the step's samples are formed side by side instead of
+    // one search and close after another.  The marks (a running maximum of the growth
+    // footprints), the tracked block at each free (the last mark-setting sample before it)
+    // and the frees' hits follow by warp scans.  Returns false if the step is not dense.
+    auto dense = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+        const uint64_t lim = 2 * (uint64_t)T - 1;
+        bool is_dense = true;
+        uint32_t nzm = 0;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int64_t d = in.d[k];
+            const uint64_t ad = d < 0 ? 0ull - (uint64_t)d : (uint64_t)d;
+            is_dense &= d == 0 || ad >= lim;
+            nzm |= d != 0 ? 1u << k : 0u;
+        }
+        if (!__all_sync(FULL, is_dense)) return false;
+        const int cnt = __popc(nzm);
+        int rinc = cnt;   // samples up to this lane (inclusive scan)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, rinc, o);
+            if (lane >= o) rinc += y;
+        }
+        const int total = __shfl_sync(FULL, rinc, 31);
+        if (total == 0) return true;   // zero deltas only: nothing moves, no free among them
+        const uint32_t nb = n + (uint32_t)(rinc - cnt);   // this lane's first record
+        // unit-local prefix through each event
+        int64_t lp[E];
+        lp[0] = in.d[0];
+#pragma unroll
+        for (int k = 1; k < E; ++k) lp[k] = lp[k - 1] + in.d[k];
+        const int64_t lin = warp_incl_scan(lp[E - 1], lane);
+        const int64_t stot = __shfl_sync(FULL, lin, 31);
+        const int64_t base = P + lin - lp[E - 1];
+        // the step's first sample closes the open window from counter c (warp-uniform)
+        const int first_lane = __ffs(__ballot_sync(FULL, cnt != 0)) - 1;
+        const int first_k = __ffs(__shfl_sync(FULL, (int)nzm, first_lane)) - 1;
+        // growth footprints and the mark before each event: running maximum within the lane,
+        // then an exclusive maximum over the lanes below
+        int64_t lmx = INT64_MIN;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const bool first = lane == first_lane && k == first_k;
+            const int64_t cr = first ? c + in.d[k] : in.d[k];
+            if (in.d[k] != 0 && cr > 0) lmx = max(lmx, fpb + base + lp[k]);
+        }
+        int64_t mx = lmx;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, mx, o);
+            if (lane >= o && y > mx) mx = y;
+        }
+        int64_t mrun = __shfl_up_sync(FULL, mx, 1);
+        if (lane == 0) mrun = INT64_MIN;
+        mrun = max(mrun, mark);
+        // the last mark-setting sample in each lane (its record and address), then the one
+        // entering each lane from the lanes below (pos: 1 + its step position, 0: none)
+        uint32_t hwm_bits = 0;
+        int64_t mm = mrun;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const bool first = lane == first_lane && k == first_k;
+            const int64_t cr = first ? c + in.d[k] : in.d[k];
+            const int64_t fp = fpb + base + lp[k];
+            if (in.d[k] != 0 && cr > 0 && fp > mm) { hwm_bits |= 1u << k; mm = fp; }
+        }
+        uint32_t hpos = 0, hslot = 0;
+        uint64_t haddr = 0;
+        if (hwm_bits) {
+            const int k = 31 - __clz(hwm_bits);
+            hpos = (uint32_t)(lane * E + k) + 1;
+            hslot = nb + (uint32_t)__popc(nzm & ((1u << k) - 1u));
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+                if (q == k) haddr = in.a[q];
+        }
+        uint32_t epos = hpos, eslot = hslot;
+        uint64_t eaddr = haddr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yp = __shfl_up_sync(FULL, epos, o);
+            const uint32_t ys = __shfl_up_sync(FULL, eslot, o);
+            const uint64_t ya = __shfl_up_sync(FULL, eaddr, o);
+            if (lane >= o && yp > epos) { epos = yp; eslot = ys; eaddr = ya; }
+        }
+        // exclusive: the last mark-setting sample of the lanes below
+        uint32_t cpos = __shfl_up_sync(FULL, epos, 1), cslot = __shfl_up_sync(FULL, eslot, 1);
+        uint64_t caddr = __shfl_up_sync(FULL, eaddr, 1);
+        if (lane == 0) cpos = 0;
+        // records, and each free tested against the block tracked at it
+        uint32_t ctk = cpos ? 3u : tk, cs = cpos ? cslot : tslot;
+        uint64_t ca = cpos ? caddr : taddr;
+        bool own = false;                  // (ctk, cs) is a record this lane wrote in this step
+        uint32_t hit_slot = 0xffffffffu;   // a record a lane below wrote in this step, hit here
+        int64_t gbest = INT64_MIN, tbest = INT64_MIN;
+        uint32_t gpos = 0, tpos = 0;
+        uint32_t r = nb;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int64_t d = in.d[k];
+            if (ctk && d < 0 && in.a[k] == ca) {
+                if (ctk == 3 && own) {
+                    if (cs < cap) out[cs].recl = 1;   // (this thread stored the record above)
+                } else if (ctk == 3 && cs >= n) {
+                    hit_slot = cs;                    // marked once every lane's records are out
+                } else if (ctk == 3 && cs >= in0.n0) {
+                    if (cs < cap) out[cs].recl = 1;   // an earlier step's record
+                } else if (ctk == 3) {
+                    prior = cs + 1;
+                } else {
+                    enter_hit = 1;
+                }
+            }
+            if (d == 0) continue;
+            const bool first = lane == first_lane && k == first_k;
+            const int64_t cr = first ? c + d : d;
+            const int64_t Pr = base + lp[k];
+            const int64_t pos_a = d > 0 ? d : 0;
+            const uint32_t pyk = py_of(in, k) ? 1u : 0u;
+            const int64_t A = (first ? accA : 0) + pos_a;
+            const int64_t Apy = (first ? accApy : 0) + (pyk ? pos_a : 0);
+            const int64_t Spy = (first ? accSpy : 0) + (pyk ? d : 0);
+            const bool growth = cr > 0;
+            const bool hwm = ((hwm_bits >> k) & 1u) != 0;
+            const uint32_t rel = rel0 + (uint32_t)(lane * E + k);
+            if (r < cap) {
+                FRec Rr;
+                Rr.rel = rel;
+                Rr.line = 0;   // filled in by k_compact
+                Rr.kind = growth ? 1 : -1;
+                Rr.is_hwm = hwm ? 1 : 0;
+                Rr.recl = 0;
+                Rr.py = (uint8_t)pyk;
+                Rr.pad = 0;
+                Rr.A = A; Rr.F = A - cr; Rr.A_py = Apy; Rr.F_py = Apy - Spy; Rr.P = Pr;
+                out[r] = Rr;
+            }
+            if (FIRST) {
+                if (r < (uint32_t)RM) { R->C0->pos[r] = rel; R->C0->gp[r] = growth ? Pr : INT64_MIN; }
+                if (growth && Pr > gbest) { gbest = Pr; gpos = rel; }
+                if (growth && r >= (uint32_t)RM && Pr > tbest) { tbest = Pr; tpos = rel; }
+            }
+            if (hwm) { ctk = 3; cs = r; ca = in.a[k]; own = true; }
+            ++r;
+        }
+        __syncwarp();   // the step's records are written before the hits mark them
+        if (hit_slot != 0xffffffffu && hit_slot < cap) out[hit_slot].recl = 1;
+        if (FIRST) {
+            // the largest growth prefix and its first position (positions rise with the lanes)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int64_t yb = __shfl_xor_sync(FULL, gbest, o), zb = __shfl_xor_sync(FULL, tbest, o);
+                const uint32_t yp = __shfl_xor_sync(FULL, gpos, o), zp = __shfl_xor_sync(FULL, tpos, o);
+                if (yb > gbest || (yb == gbest && yp < gpos)) { gbest = yb; gpos = yp; }
+                if (zb > tbest || (zb == tbest && zp < tpos)) { tbest = zb; tpos = zp; }
+            }
+            if (gbest > gmax) { gmax = gbest; garg = gpos; }
+            if (tbest > tmax) { tmax = tbest; targ = tpos; }
+            const int last_lane = 31 - __clz(__ballot_sync(FULL, cnt != 0));
+            const int last_k = 31 - __clz(__shfl_sync(FULL, (int)nzm, last_lane));
+            last = (int32_t)(rel0 + (uint32_t)(last_lane * E + last_k));
+        }
+        // the state after the step: the last sample left the counter at 0 and an empty window
+        enter_hit = __any_sync(FULL, enter_hit != 0) ? 1u : 0u;
+        prior = __reduce_max_sync(FULL, prior);
+        const uint32_t any_hwm = __ballot_sync(FULL, hwm_bits != 0);
+        if (any_hwm) {
+            const int hl = 31 - __clz(any_hwm);
+            tk = 3;
+            tslot = __shfl_sync(FULL, hslot, hl);
+            taddr = __shfl_sync(FULL, haddr, hl);
+            mark = warp_max(lmx);   // every mark-setting sample beat the mark before it
+        }
+        n += (uint32_t)total;
+        c = 0;
+        accA = accApy = accSpy = 0;
+        P += stot;
+        return true;
+    };
     // every event of the step joins the open window (no sample in it)
     auto whole_step = [&](const StepIn<E> &in, bool fits) {
         fold(in, fits, 0xffu, std::true_type{});
@@ -267,6 +456,9 @@ __device__ bool exact_unit(RingT &sm, uint32_t &phase, const Unit &U, const Exac
         // step when T and the step's deltas allow it: the same arithmetic without overflow)
         const bool t32 = T <= FIT32_T;
         auto step = [&](const StepIn<E> &in, uint32_t rel0) -> bool {
+            if constexpr (DENSE) {
+                if (dense(in, rel0)) return false;
+            }
             const bool fits = __all_sync(FULL, step_fits32(in));
             if (t32 && fits) {
                 StepPrefix32<E> sp;

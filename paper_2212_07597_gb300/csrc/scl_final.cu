@@ -38,6 +38,7 @@ __device__ uint32_t list_lower(const SRes *L, uint32_t n, uint32_t x, int lane) 
 
 // 14 warps per block at most (128 registers: a cap of 136 registers left blocks of only 12
 // warps on an SM, and the replay ran 40% longer)
+template <bool DENSE>
 __global__ void __launch_bounds__(32 * 14) k_final(const LaunchFinal a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(32 * 14) k_final(const LaunchFinal a) {
         if (!L && lane == 0) atomicAdd(&a.stats[5], 1ull);
         UnitOut O;
         uint32_t n = 0, prior = 0;
-        const bool ok = exact_unit<false>(sm, phase, U, in0, a.recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O,
+        const bool ok = exact_unit<false, DENSE>(sm, phase, U, in0, a.recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O,
                                           (ExactRun *)nullptr, prior);
         if (lane == 0) {
             // a hit on the entering block of a piece other than the one that ends the unit, and
@@ -191,17 +192,20 @@ cudaError_t launch_wait_selftest(ErrWord *err, unsigned long long limit, cudaStr
 cudaError_t launch_final(const LaunchFinal &a, cudaStream_t s) {
     if (!a.nitems) return cudaSuccess;
     const size_t smem = sizeof(FinalRing) * a.warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the instance with the dense-step test only where a dense step can occur often
+    auto kern = a.T <= DENSE_T_MAX ? k_final<true> : k_final<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_final<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
+    kern<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 int final_occupancy(int warps_per_block, int *blocks_per_sm) {
     const size_t smem = sizeof(FinalRing) * warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // (both instances have the same register cap and shared memory)
+    cudaError_t e = cudaFuncSetAttribute(k_final<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_final, 32 * warps_per_block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_final<false>, 32 * warps_per_block, smem);
     return e == cudaSuccess ? 0 : -1;
 }
 

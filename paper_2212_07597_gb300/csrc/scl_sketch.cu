@@ -243,6 +243,7 @@ __device__ bool sketch_unit(SketchRing &sm, uint32_t &phase, int u, const Unit *
 // The first unit u of a trace in the batch: its entry is the trace's resident state, so it
 // is replayed exactly once (k_final skips it) and the run is recorded as every candidate.
 // Returns false if a wait timed out.
+template <bool DENSE>
 __device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__restrict__ units, UnitSum *usum,
                            Cand *cand, FRec *recs, UnitOut *uout, const DevTrace *traces, int64_t T, ErrWord *err,
                            unsigned long long spin, int lane) {
@@ -272,7 +273,7 @@ __device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__
     UnitOut O;
     uint32_t n = 0;
     uint32_t prior;   // (a whole unit: no earlier piece)
-    const bool ok = exact_unit<true>(fr, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R,
+    const bool ok = exact_unit<true, DENSE>(fr, phase, U, in0, recs + U.rec0, U.rec_cap, T, spin, err, lane, n, O, &R,
                                      prior);
     if (!ok) return false;   // a wait timed out (the ring may not be reusable)
     Cand *C = cand + (size_t)u * K + lane;
@@ -301,6 +302,7 @@ __device__ bool first_unit(FirstRing &fr, uint32_t &phase, int u, const Unit *__
 // work first), replaying a trace's first unit exactly and sketching every other unit, so the
 // latency-bound candidate counters and the exact replays share the SMs and a long first unit
 // starts early.
+template <bool DENSE>
 __global__ void __launch_bounds__(32 * PHASE1_MAX_WARPS, 1) k_phase1(const LaunchSketch a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(32 * PHASE1_MAX_WARPS, 1) k_phase1(const Launc
             cur = want;
             phase = 0;
         }
-        const bool ok = want ? first_unit(sm.f, phase, u, a.units, a.usum, a.cand, a.recs, a.uout, a.traces, a.T,
+        const bool ok = want ? first_unit<DENSE>(sm.f, phase, u, a.units, a.usum, a.cand, a.recs, a.uout, a.traces, a.T,
                                           a.err, a.spin, lane)
                              : sketch_unit(sm.s, phase, u, a.units, a.usum, a.cand, a.lists, a.T, a.warmup, a.err,
                                            a.spin, lane);
@@ -766,9 +768,11 @@ cudaError_t launch_totals(const LaunchSketch &a, cudaStream_t s) {
 cudaError_t launch_phase1(const LaunchSketch &a, cudaStream_t s) {
     if (!a.nitems) return cudaSuccess;
     const size_t smem = PHASE1_WARP_SMEM * a.warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(k_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the instance with the exact replay's dense-step test only where dense steps can be common
+    auto kern = a.T <= DENSE_T_MAX ? k_phase1<true> : k_phase1<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_phase1<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
+    kern<<<a.blocks, 32 * a.warps_per_block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -790,9 +794,10 @@ cudaError_t launch_chain(const LaunchSketch &a, cudaStream_t s) {
 
 int phase1_occupancy(int warps_per_block, int *blocks_per_sm) {
     const size_t smem = PHASE1_WARP_SMEM * warps_per_block;
-    cudaError_t e = cudaFuncSetAttribute(k_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // (both instances have the same register cap and shared memory)
+    cudaError_t e = cudaFuncSetAttribute(k_phase1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_phase1, 32 * warps_per_block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_phase1<false>, 32 * warps_per_block, smem);
     return e == cudaSuccess ? 0 : -1;
 }
 

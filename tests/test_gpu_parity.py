@@ -396,3 +396,14 @@ def test_range_queries_equal_per_trace_queries():
     assert scl.scl_line_stats_range(ctx, 0, 0).shape == (0, 64)
     with pytest.raises(scl.SclError):
         scl.scl_line_stats_range(ctx, 5, 4)   # passes max_traces
+
+
+@pytest.mark.parametrize("T", [1, 7, 100, 4096])
+def test_small_thresholds_dense_steps(T):
+    # at small T most steps are dense (every event 0 or at least 2T - 1 from zero: each nonzero
+    # event is a sample); at T = 100 and 4096 dense and ordinary steps alternate.  Frees with
+    # LIFO address reuse hit tracked blocks inside a step, across lanes and across steps.
+    tr = tg.plain_trace(200_003, seed=41, p_malloc=0.45, addr_reuse=True)
+    ctx = gpu_ctx(T, shift=0, unit=16384, log_cap=tr.n + 1)
+    keep = replay(ctx, [(0, tr)])
+    assert_same(ctx, 0, oracle_of(tr, T))
