@@ -248,8 +248,8 @@ int scl_trace_reset(scl_ctx *ctx, uint32_t trace, void *cuda_stream);
  * segments (a warm-up call, then the mean of three calls issued back to back, so that each
  * call's host-side planning overlaps the previous call's device work as in repeated use;
  * the results of these calls are discarded) and searches one setting at a time,
- * twice over: unit 32k/64k/128k/256k/512k/1M, first unit unit/512k/1M/1.25M/1.5M, phase-1
- * warps 8/12/16, replay warps 10/14, warm-up 16k/32k, fix-up 0/1, replay pieces
+ * twice over: unit 32k/64k/128k/256k/512k/1M/2M, first unit unit/512k/768k/1M/1.25M/1.5M,
+ * phase-1 warps 8/12/16, replay warps 10/12/14, warm-up 16k/32k, fix-up 0/1, replay pieces
  * 32k/64k/128k/4M.  It restores the
  * touched traces' state before every run and at the end, keeps the fastest setting in the
  * context (read it back with scl_tuning_get), and allocates one device buffer for the

@@ -1383,10 +1383,10 @@ int scl_autotune(scl_ctx *c, const scl_segment *segs, uint32_t nsegs, void *stre
     };
     // coordinate descent, two passes: each setting in turn takes its best value with the
     // others held at the best found so far
-    const uint32_t units[] = {32768, 65536, 131072, 262144, 524288, 1048576};
-    const uint32_t firsts[] = {0, 524288, 1048576, 1310720, 1572864};
+    const uint32_t units[] = {32768, 65536, 131072, 262144, 524288, 1048576, 2097152};
+    const uint32_t firsts[] = {0, 524288, 786432, 1048576, 1310720, 1572864};
     const uint32_t pwarps[] = {8, 12, (uint32_t)PHASE1_MAX_WARPS};
-    const uint32_t fwarps[] = {10, 14};
+    const uint32_t fwarps[] = {10, 12, 14};
     const uint32_t warm[] = {16384, 32768};
     const uint32_t fixups[] = {0, 1};
     const uint32_t pieces[] = {32768, 65536, 131072, 1u << 22};   // (the last: no unit is cut)
