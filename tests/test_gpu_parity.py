@@ -274,12 +274,14 @@ def test_autotune_restores_state_and_keeps_results_exact():
     before = scl.scl_state_export(ctx, 0)
     seg, kb = scl.trace_segment(0, b)
     best, ms = scl.scl_autotune(ctx, [seg])
-    assert ms > 0 and best.final_warps in (10, 14) and best.ext_events in (16384, 32768)
-    assert best.unit_events in (0, 32768, 65536, 131072, 262144, 524288) and best.fixup in (0, 1)
-    assert best.first_events in (0, 524288, 1048576, 1310720, 1572864) and best.warps_per_block in (8, 12, 16)
+    # every field within the documented search space (0: the default it starts from)
+    assert ms > 0 and best.final_warps in (10, 12, 14) and best.ext_events in (16384, 32768)
+    assert best.unit_events in (0, 32768, 65536, 131072, 262144, 524288, 1048576, 2097152) and best.fixup in (0, 1)
+    assert best.first_events in (0, 524288, 786432, 1048576, 1310720, 1572864)
+    assert best.warps_per_block in (8, 12, 16) and best.piece_events in (0, 32768, 65536, 131072, 1 << 22)
     assert scl.scl_state_export(ctx, 0) == before
     t = scl.scl_tuning_get(ctx)
-    fields = ("unit_events", "final_warps", "warps_per_block", "ext_events", "first_events", "fixup")
+    fields = ("unit_events", "final_warps", "warps_per_block", "ext_events", "first_events", "fixup", "piece_events")
     assert [getattr(t, f) for f in fields] == [getattr(best, f) for f in fields]
     scl.scl_replay_batch(ctx, [seg])
     scl.scl_sync(ctx)
