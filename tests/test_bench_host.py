@@ -74,3 +74,27 @@ def test_aggregate_is_all_events_over_the_slowest_rank():
 
 def test_default_workload_is_the_batched_configuration():
     assert bench.parse([]).workload == "batched"
+
+
+def test_stride_case_keeps_the_batch_length_mix():
+    ids = bench.batched_ids(256, 16)
+    assert list(ids[:3]) == [0, 16, 32] and len(ids) == 256
+    lens, mlen = bench.batched_spec(256, 0, 0, 16)
+    full, _ = bench.batched_spec(4096)
+    assert np.array_equal(lens, full[ids]) and np.array_equal(mlen, lens // 10)
+    assert "every 16th" in bench.batched_config(256, lens, mlen, 16)["workload"]
+
+
+def test_streamed_bytes_add_the_sketch_warmups_to_phase1_only():
+    n, m, first = 10_000_000, 1_000_000, 4_000_000
+    alg = bench.kernel_bytes(n, m, first)
+    sb = bench.streamed_bytes(n, m, first, sketch_streamed=6_500_000)
+    assert sb["final"] == alg["final"] and sb["copy"] == alg["copy"]
+    assert sb["phase1"] - alg["phase1"] == pytest.approx(8.0 * (6_500_000 - (n - first)))
+    assert bench.streamed_bytes(n, m, first) == alg
+
+
+def test_each_kernel_hashes_its_own_sources():
+    h = {k: bench.source_hash(k) for k in bench.KERNEL_SOURCES}
+    assert len(set(h.values())) == 3 and all(len(v) == 16 for v in h.values())
+    assert all("scl_post.cu" not in files for files in bench.KERNEL_SOURCES.values())
